@@ -1,0 +1,395 @@
+"""Benchmark of the TS-SpGEMM hot path on GB300.
+
+One step = one pass of the whole hot path over the workload: the symbolic
+pass (row flops, binning, per-row nnz, scan), the numeric pass and the fused
+backward (dA = SDDMM on A's pattern, dB = A^T dC on B's pattern).  The
+default workload is the sparse-embedding product: R-MAT scale 22 (n =
+4,194,304, edge factor 16, U(0,1) values) times B (n x 256, 5 % dense, N(0,1)),
+plus-times, forward + backward.
+
+Prints one JSON line.  `value` is useful GFLOP/s of forward + backward with
+inputs resident in HBM (forward 2 flops per product, backward 4: dA and dB
+each multiply and add once per product).  `e2e` is the same metric through
+the public API with the inputs copied from pinned host memory and the
+gradients copied back inside the timed region.  `roofline` is for the numeric
+pass, `cpu_baseline` the FP64 oracle on a bounded sample of rows on the host.
+
+Under torchrun with N > 1, every rank runs an independent replica of the
+workload (the product has no exchange step on one GPU per replica).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, generator kwargs, tuning, backward)
+    "embed-s22": ("R-MAT scale 22, edge factor 16, U(0,1) A; B 4194304x256 at 5% N(0,1); "
+                  "plus-times forward + backward",
+                  dict(scale=22, edge_factor=16, d=256, density=0.05, b_values="normal"), None, True),
+    "tiled-s24": ("R-MAT scale 24, edge factor 16, U(0,1) A; B 16777216x1024 at 1% U(0,1); "
+                  "plus-times, B column tiles of 256, forward + backward",
+                  dict(scale=24, edge_factor=16, d=1024, density=0.01, b_values="uniform"),
+                  {"col_tile": 256}, True),
+    "er-16k": ("Erdos-Renyi A n=16384, 8 per row, U(0,1); B 16384x64 at 10% U(0,1); plus-times "
+               "forward only", None, None, False),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(name, seed_offset=0):
+    import synth
+    desc, kw, tuning, bwd = WORKLOADS[name]
+    if name == "er-16k":
+        A, B = synth.er_product(seed=synth.BASE_SEED + 1 + 1000 * seed_offset)
+    else:
+        seed = synth.BASE_SEED + (3 if name == "embed-s22" else 5) + 1000 * seed_offset
+        A, B = synth.rmat_embedding(seed=seed, **kw)
+    return A, B
+
+
+def products_per_row(A, B):
+    blen = np.diff(B.rowptr)
+    per_entry = blen[A.col]
+    cs = np.concatenate([[0], np.cumsum(per_entry, dtype=np.int64)])
+    return cs[A.rowptr[1:]] - cs[A.rowptr[:-1]]
+
+
+def cpu_baseline(A, B, want_bwd, target_s=12.0):
+    """The FP64 oracle on the first m rows of A (rows are randomly labelled by
+    the R-MAT permutation, so a prefix is a uniform sample), sized to about
+    target_s seconds of single-core work."""
+    import oracle
+    import synth
+    from synth import CSR
+    fl = products_per_row(A, B)
+    cum = np.cumsum(fl)
+
+    def run(m):
+        Asub = CSR(m, A.ncols, A.rowptr[: m + 1], A.col[: A.rowptr[m]], A.val[: A.rowptr[m]])
+        t0 = time.perf_counter()
+        Cp, Ci, Cx, _ = oracle.spgemm(Asub, B)
+        if want_bwd:
+            dC = synth.grad_output(Ci.size, 1).astype(np.float64)
+            oracle.backward(Asub, B, Cp, Ci, dC)
+        return time.perf_counter() - t0, int(cum[m - 1]) if m > 0 else 0
+
+    m = max(1, min(A.nrows, int(np.searchsorted(cum, min(cum[-1], 2_000_000)))))
+    t, f = run(m)
+    rate = f / max(t, 1e-6)
+    m2 = int(np.searchsorted(cum, min(cum[-1], rate * target_s)))
+    m2 = max(m, min(A.nrows, m2))
+    if m2 > m:
+        t, f = run(m2)
+        m = m2
+    flops = (6.0 if want_bwd else 2.0) * f
+    return {"value": flops / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"rows 0..{m - 1} of {A.nrows} ({f} products, "
+                      f"{'forward+backward' if want_bwd else 'forward'}), {t:.1f} s single-threaded FP64"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="embed-s22", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
+    ap.add_argument("--tuning", default=None, help="JSON dict of forced tuning fields")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    desc, _, wl_tuning, want_bwd = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, ws, rank, desc, want_bwd)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2408_11988_gb300 import DeviceCSR, Plan
+    from paper_2408_11988_gb300 import _native as N
+    import synth
+
+    A, B = make_inputs(args.workload, seed_offset=rank)
+    flops_row = products_per_row(A, B)
+    F = int(flops_row.sum())
+    Ad, Bd = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+    tuning = dict(wl_tuning or {})
+    if args.tuning:
+        tuning.update(json.loads(args.tuning))
+    plan = Plan(Ad, Bd, tuning=tuning or None)
+    C = plan.forward(Ad, Bd)
+    nnzC = C.nnz
+    dC = torch.as_tensor(synth.grad_output(nnzC, 1), device="cuda") if want_bwd else None
+    if args.autotune:
+        plan.autotune(Ad, Bd, C, dC_val=dC, reps=2)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        rowptr, nnz = plan.symbolic(Ad, Bd, sync=True)
+        if ev:
+            ev[1].record(stream)
+        Cs = plan.alloc_c(rowptr, nnz)
+        plan.numeric(Ad, Bd, Cs)
+        if ev:
+            ev[2].record(stream)
+        if want_bwd:
+            plan.backward(Ad, Bd, Cs, dC)
+        if ev:
+            ev[3].record(stream)
+        return Cs
+
+    for _ in range(args.warmup):
+        step()
+    plan.check()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    l0 = N.lib().ts_kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = N.lib().ts_kernel_launches() - l0
+    total_ms = t_start.elapsed_time(t_end)
+    sym = [e[0].elapsed_time(e[1]) for e in evs]
+    num = [e[1].elapsed_time(e[2]) for e in evs]
+    bwd = [e[2].elapsed_time(e[3]) for e in evs]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    flop_step = (6.0 if want_bwd else 2.0) * F
+    value = flop_step * ws / (ms * 1e-3) / 1e9
+
+    # roofline of the numeric pass: algorithmic bytes per launch / mean duration
+    n, nnzA = A.nrows, A.nnz
+    num_bytes = 16 * (n + 1) + 24 * nnzA + 8 * F + 8 * nnzC
+    bwd_bytes = 16 * (n + 1) + 28 * nnzA + 8 * F + 8 * nnzC + 4 * B.nnz
+    sym_bytes = 8 * (n + 1) + 20 * nnzA + 4 * F + 8 * n
+    peak, peak_kind = _peaks()
+    num_ms = statistics.mean(num)
+    achieved = num_bytes / (num_ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host inputs in, gradients out
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, A, B, dC, want_bwd, tuning, flop_step, ws, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(A, B, want_bwd)
+
+    if rank == 0:
+        line = {
+            "metric": "TS-SpGEMM GFLOP/s (forward + backward, plus-times)" if want_bwd
+            else "TS-SpGEMM GFLOP/s (forward, plus-times)",
+            "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": n, "d": B.ncols,
+                       "nnz_A": nnzA, "nnz_B": B.nnz, "nnz_C": nnzC, "products": F,
+                       "tuning": plan.tuning, "l2": "inputs larger than L2 (A+B+C > 129 MB)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "numeric pass (k_numeric_dense)",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "bytes_per_launch": num_bytes, "traffic": None},
+            "phases_ms": {"symbolic": round(statistics.mean(sym), 4), "numeric": round(num_ms, 4),
+                          "backward": round(statistics.mean(bwd), 4) if want_bwd else None},
+            "phase_roofline_frac": {
+                "symbolic": round(sym_bytes / (statistics.mean(sym) * 1e-3) / 1e9 / peak, 4),
+                "numeric": round(achieved / peak, 4),
+                "backward": round(bwd_bytes / (statistics.mean(bwd) * 1e-3) / 1e9 / peak, 4)
+                if want_bwd else None},
+            "forward_gflops": round(2.0 * F / ((statistics.mean(sym) + num_ms) * 1e-3) / 1e9, 3),
+            "nnzC_per_s": round(nnzC / ((statistics.mean(sym) + num_ms) * 1e-3), 1),
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, A, B, dC, want_bwd, tuning, flop_step, ws, dist):
+    import torch
+    from paper_2408_11988_gb300 import DeviceCSR, Plan
+    hA = [torch.as_tensor(x).pin_memory() for x in (A.rowptr, A.col, A.val)]
+    hB = [torch.as_tensor(x).pin_memory() for x in (B.rowptr, B.col, B.val)]
+    hdC = dC.cpu().pin_memory() if want_bwd else None
+    dev = [torch.empty_like(x, device="cuda") for x in hA + hB]
+    ddC = torch.empty_like(hdC, device="cuda") if want_bwd else None
+    out_dA = torch.empty(A.nnz, dtype=torch.float32).pin_memory()
+    out_dB = torch.empty(B.nnz, dtype=torch.float32).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in hA + hB) + (hdC.numel() * 4 if want_bwd else 0)
+    d2h = (A.nnz + B.nnz) * 4 if want_bwd else 0
+    Ad = DeviceCSR(A.nrows, A.ncols, dev[0], dev[1], dev[2])
+    Bd = DeviceCSR(B.nrows, B.ncols, dev[3], dev[4], dev[5])
+    plan = Plan(Ad, Bd, tuning=tuning or None)
+
+    def step():
+        for h, d in zip(hA + hB, dev):
+            d.copy_(h, non_blocking=True)
+        if want_bwd:
+            ddC.copy_(hdC, non_blocking=True)
+        C = plan.forward(Ad, Bd)
+        if want_bwd:
+            gA, gB = plan.backward(Ad, Bd, C, ddC)
+            out_dA.copy_(gA, non_blocking=True)
+            out_dB.copy_(gB, non_blocking=True)
+            return None
+        host = torch.empty(C.nnz, dtype=torch.float32).pin_memory()
+        host.copy_(C.val, non_blocking=True)
+        return host
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": round(flop_step * ws / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+            "ms_per_step": round(ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def run_reference(args, ws, rank, desc, want_bwd):
+    """The oracle (FP64, one host core) timed on a bounded sample per step."""
+    if rank != 0:
+        return
+    A, B = make_inputs(args.workload)
+    import oracle  # noqa: F401
+    for _ in range(args.warmup):
+        cpu_baseline(A, B, want_bwd, target_s=2.0)
+    vals = []
+    sample = None
+    for _ in range(args.steps):
+        r = cpu_baseline(A, B, want_bwd, target_s=6.0)
+        vals.append(r["value"])
+        sample = r["sample"]
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference",
+        "metric": "TS-SpGEMM GFLOP/s (forward + backward, plus-times)" if want_bwd
+        else "TS-SpGEMM GFLOP/s (forward, plus-times)",
+        "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

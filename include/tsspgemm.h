@@ -1,0 +1,288 @@
+/*
+ * tsspgemm.h -- C ABI of the GB300 (sm_103a) TS-SpGEMM library.
+ *
+ * The product computed is the local TS-SpGEMM of the paper: C = A * B with A a
+ * square n x n sparse matrix and B a sparse tall-and-skinny n x d matrix
+ * (d << n), over a semiring (paper Sec. II-A), row by row after Gustavson
+ * (paper Sec. III-A, Eq. 1): row r of C is the semiring sum, over the stored
+ * entries (r,c) of A, of A(r,c) times row c of B.  With one GPU there is no
+ * distribution: this is the paper's diagonal-tile product LocalSpGEMM over
+ * the whole of A (Alg. 2, diagonal-tile step), with a dense accumulator of
+ * width d (the SPA of Sec. III-C) or a hash accumulator.
+ *
+ * Conventions shared by every call
+ *  - Matrices are CSR (ts_csr_desc): rowptr int64[nrows+1] with rowptr[0]=0
+ *    and rowptr[nrows]=nnz, col int32[nnz] ascending and distinct within a
+ *    row, val float32[nnz] (plus-times) or NULL (boolean semiring: a stored
+ *    entry means true).  All pointers inside a descriptor are DEVICE pointers.
+ *    ts_csr_validate checks these rules on the device.
+ *  - The caller owns every device buffer (A, B, C, gradients, workspace).  The
+ *    library never allocates device memory; scratch space is the caller's
+ *    workspace, whose size the *_workspace_size calls report.  Plans are host
+ *    objects owned by the caller and released with the matching destroy call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream ordered; the only calls that synchronise the stream are those
+ *    that return a count to the host (documented per call).
+ *  - Every call returns a ts_status.  Argument errors are detected on the host
+ *    before anything is enqueued.  Malformed CSR content that the host cannot
+ *    see (a column index out of range, counts that do not match the symbolic
+ *    pass) is caught on the device: the offending access is skipped, a flag
+ *    is set in the workspace and the next call that synchronises returns
+ *    TS_ERR_BAD_CSR.  No call traps, aborts or exits.  ts_last_error() gives a
+ *    message for the calling thread's most recent failure.
+ *  - Output rows list their columns in ascending order.  The output pattern is
+ *    structural: (i,j) is stored iff some product A(i,k)*B(k,j) exists, even
+ *    when plus-times values cancel to 0.
+ */
+#ifndef TSSPGEMM_H
+#define TSSPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TS_API __attribute__((visibility("default")))
+#else
+#define TS_API
+#endif
+
+typedef int32_t ts_status;
+#define TS_OK 0
+#define TS_ERR_INVALID_ARG (-1)        /* bad pointer, size or enum value       */
+#define TS_ERR_BAD_CSR (-2)            /* CSR content violates the rules above  */
+#define TS_ERR_UNSUPPORTED (-3)        /* valid request this build cannot serve */
+#define TS_ERR_WORKSPACE_TOO_SMALL (-4)
+#define TS_ERR_CAPACITY (-5)           /* caller's output buffer too small      */
+#define TS_ERR_OVERFLOW (-6)           /* a count does not fit its type         */
+#define TS_ERR_CUDA (-7)               /* a CUDA runtime call failed            */
+#define TS_ERR_STATE (-8)              /* calls made out of the required order  */
+
+/* Semirings (paper Sec. II-A; (and, or) for BFS in Alg. 3). */
+#define TS_SR_PLUS_TIMES_F32 0     /* (+, *) on float32 values                   */
+#define TS_SR_OR_SELECT2ND_BOOL 1  /* add = OR, multiply = select2nd (= AND here) */
+
+/* Accumulator kinds (paper Sec. III-C: SPA for d <= 1024, hash above). */
+#define TS_ACC_AUTO 0
+#define TS_ACC_DENSE 1   /* shared-memory dense accumulator + occupancy flags   */
+#define TS_ACC_HASH 2    /* shared-memory open-addressing hash accumulator      */
+
+typedef struct ts_csr_desc {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    int64_t* rowptr; /* device, nrows+1                      */
+    int32_t* col;    /* device, nnz                          */
+    void* val;       /* device float32[nnz], or NULL         */
+} ts_csr_desc;
+
+/*
+ * Tuning of one product; 0 in any field means "choose automatically".
+ *  accum          TS_ACC_*.
+ *  col_tile       accumulator width in columns for the numeric pass (a
+ *                 multiple of 32).  Below d, B's columns are processed in
+ *                 tiles of this width and each output row is the
+ *                 concatenation of its tiles (B column tiling).
+ *  cta_min_flops  rows with at least this many products (rounded up to a
+ *                 power of two) run CTA-per-row; lighter rows warp-per-row.
+ *  warps_per_cta  warps per thread block (1..32).
+ *  hash_slots     slots of a warp's hash table (power of two, >= 64).
+ */
+typedef struct ts_tuning {
+    int32_t accum;
+    int32_t col_tile;
+    int64_t cta_min_flops;
+    int32_t warps_per_cta;
+    int32_t hash_slots;
+} ts_tuning;
+
+typedef struct ts_plan ts_plan;
+typedef struct ts_batched_plan ts_batched_plan;
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+TS_API const char* ts_last_error(void);
+/* Static name of a status code. */
+TS_API const char* ts_status_string(ts_status s);
+/* Library version as major*10000 + minor*100 + patch. */
+TS_API int32_t ts_version(void);
+/* Number of CUDA kernels this library has launched in this process. */
+TS_API int64_t ts_kernel_launches(void);
+
+/*
+ * Validate a CSR matrix on the device: rowptr[0] = 0, rowptr non-decreasing,
+ * rowptr[nrows] = nnz, every column in [0, ncols) and strictly ascending in
+ * its row.  Synchronises `stream`.  Returns TS_OK or TS_ERR_BAD_CSR, and
+ * writes the first offending row (or -1) to *bad_row when bad_row != NULL.
+ * ws: at least ts_validate_workspace_size() bytes of device memory.
+ */
+TS_API size_t ts_validate_workspace_size(void);
+TS_API ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/*
+ * Plan for C = A * B over `semiring` (TS_SR_*).  Reads only the shapes of A
+ * and B (host side, no device access).  `force` (may be NULL) fixes any
+ * non-zero tuning field.  A plan may be reused for any A, B of the same
+ * shapes.  Errors: INVALID_ARG (shapes: A must be n x n, B n x d, d >= 1),
+ * UNSUPPORTED (d above the supported maximum).
+ */
+TS_API ts_status ts_plan_create(const ts_csr_desc* A, const ts_csr_desc* B, int32_t semiring,
+                         const ts_tuning* force, ts_plan** out);
+TS_API ts_status ts_plan_destroy(ts_plan* plan);
+TS_API ts_status ts_plan_get_tuning(const ts_plan* plan, ts_tuning* out);
+TS_API ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning);
+
+/* Device workspace needed by symbolic, numeric, backward and autotune. */
+TS_API ts_status ts_workspace_size(const ts_plan* plan, size_t* bytes);
+
+/*
+ * Synchronise `stream` and report the device-side checks recorded in ws by
+ * the calls since the last symbolic pass: TS_OK, or TS_ERR_BAD_CSR with the
+ * failed checks in ts_last_error().
+ */
+TS_API ts_status ts_workspace_check(const ts_plan* plan, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Symbolic pass (Eq. 1, pattern only): computes the products per row
+ * (flops_i = sum of nnz(B_k) over the stored (i,k)), bins rows by flops,
+ * counts nnz(C_i) = |union of the patterns of the rows B_k| and writes
+ * C_rowptr (device int64[n+1], caller allocated) as their running sum.
+ * When nnzC_host != NULL the total is copied to it and the stream is
+ * synchronised; otherwise nothing synchronises and the total stays at
+ * C_rowptr[n].  The row schedule it leaves in ws is reused by the numeric
+ * and backward calls: keep ws and the patterns of A and B unchanged between
+ * them.  Errors: INVALID_ARG, WORKSPACE_TOO_SMALL, BAD_CSR (only reported
+ * when synchronising), CUDA.
+ */
+TS_API ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                             int64_t* C_rowptr, int64_t* nnzC_host, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/*
+ * Numeric pass (Eq. 1 with values): fills C->col (and C->val for plus-times)
+ * for the C->rowptr of the preceding symbolic call on this plan and ws.
+ * C->nnz must equal the symbolic total.  Plus-times sums in float32 in an
+ * unspecified order; columns are ascending per row.  Does not synchronise.
+ * Errors: INVALID_ARG, STATE (no symbolic pass on this plan/ws before),
+ * WORKSPACE_TOO_SMALL, CUDA; device-side checks as described at the top.
+ */
+TS_API ts_status ts_spgemm_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                            const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Backward of L = sum over C's pattern of dC(i,j) * C(i,j) for C = A*B in
+ * plus-times, with the patterns of A, B and C fixed (the paper's sparse
+ * embedding, Sec. IV-B, trains through this product):
+ *   dA(i,k) = sum over j in B_k of dC(i,j) * B(k,j)          (sampled dense-
+ *             dense product on A's pattern, SDDMM)
+ *   dB(k,j) = sum over i with A(i,k) stored of A(i,k) * dC(i,j)  (A^T dC on
+ *             B's pattern)
+ * dC_val holds float32 values on C's pattern (C->val is not read); dA_val
+ * (nnz_A floats) and dB_val (nnz_B floats) are outputs, either may be NULL.
+ * dB is summed with float atomics, so its rounding is not deterministic.
+ * Uses the row schedule of the preceding symbolic call on this plan and ws.
+ * Does not synchronise.  Errors as for the numeric pass; UNSUPPORTED for the
+ * boolean semiring.
+ */
+TS_API ts_status ts_spgemm_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                             const ts_csr_desc* C, const float* dC_val, float* dA_val,
+                             float* dB_val, void* ws, size_t ws_bytes, void* stream);
+/* The two halves of ts_spgemm_backward on their own (same contract). */
+TS_API ts_status ts_spgemm_backward_dA(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                const ts_csr_desc* C, const float* dC_val, float* dA_val,
+                                void* ws, size_t ws_bytes, void* stream);
+TS_API ts_status ts_spgemm_backward_dB(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                const ts_csr_desc* C, const float* dC_val, float* dB_val,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Autotuner: times the numeric pass (and, for plus-times, the backward when
+ * dC_val != NULL) for a set of candidate tunings on these very inputs, keeps
+ * the fastest in the plan and writes it to *chosen (may be NULL).  Fields
+ * fixed by the plan's `force` are not varied.  C must come from a symbolic
+ * call on this plan/ws (C's contents are overwritten; dA/dB scratch is
+ * written into dA_scratch/dB_scratch when given).  `reps` timed repetitions
+ * per candidate (>= 1).  Synchronises the stream.
+ */
+TS_API ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                           const ts_csr_desc* C, const float* dC_val, float* dA_scratch,
+                           float* dB_scratch, int32_t reps, ts_tuning* chosen, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/*
+ * Multi-source BFS (paper Alg. 3) one level at a time.
+ *
+ * msbfs_init: F0 gets the frontier of d sources (F0(src[s], s) = 1), the
+ * visited bitmap S (uint32[n * ceil(d/32)], bit s of vertex v at word
+ * v*ceil(d/32) + s/32) is set to F0, levels (int32[n*d], vertex-major) to
+ * -1 except level 0 at the sources.  sources_dev: device int32[d], distinct
+ * vertices in [0, n).  F0->rowptr is n+1 int64, F0->col must hold >= d
+ * entries.  Does not synchronise.
+ *
+ * msbfs_step: one iteration of Alg. 3's loop body:
+ *   N = A * F over (or, select2nd);  F_next = N minus S;  S = S or N;
+ * and levels(v, s) = level for every bit of F_next.  A is the pattern of
+ * the graph (val ignored); row v of N pulls from the rows of F at v's
+ * neighbours, i.e. the traversal follows the edges of A transposed
+ * (identical for a symmetric A).  F_next->rowptr (n+1) is always written;
+ * F_next->col (capacity F_next_capacity) receives the frontier.
+ * Synchronises the stream once and writes nnz(F_next) to *nnz_next_host.
+ * If it exceeds the capacity, returns TS_ERR_CAPACITY with the needed size
+ * in *nnz_next_host; S, levels and F_next->rowptr are then already updated
+ * and the call must be repeated by msbfs_emit with a larger buffer.
+ */
+TS_API ts_status msbfs_workspace_size(int64_t n, int64_t d, size_t* bytes);
+TS_API ts_status msbfs_init(int64_t n, int64_t d, const int32_t* sources_dev, uint32_t* visited,
+                     int32_t* levels, const ts_csr_desc* F0, void* stream);
+TS_API ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
+                     int32_t* levels, int32_t level, const ts_csr_desc* F_next,
+                     int64_t F_next_capacity, int64_t* nnz_next_host, void* ws, size_t ws_bytes,
+                     void* stream);
+/* Writes F_next->col from the state a TS_ERR_CAPACITY msbfs_step left in ws. */
+TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/*
+ * Batched products: `count` independent C_b = A_b * B_b of uneven shapes in
+ * one launch per phase, graph capturable.
+ *
+ * ts_batched_plan_create reads the shapes and patterns' sizes (host side) and
+ * picks, per instance, the accumulator width and row-bin threshold (unless
+ * `force` fixes them).  ts_batched_bounds gives, per instance, an upper bound
+ * on nnz(C_b) (sum over rows of min(d_b, nnz(A_b row) * max nnz(B_b row)),
+ * computed on the device from the patterns, synchronises) for allocating C.
+ * ts_batched_bind uploads the descriptors (A, B, C arrays of `count` host
+ * descriptors with device pointers; C_b.rowptr has n_b+1 entries and
+ * C_b.col/val the bound's capacity) into ws; it synchronises.
+ * ts_spgemm_batched then runs every product without any host synchronisation
+ * or allocation, so it can be captured in a CUDA graph and replayed; after
+ * it, C_b.rowptr is the exact structure and nnz(C_b) = C_b.rowptr[n_b].
+ * The descriptor arrays passed to it must equal those bound (checked on the
+ * host).  ts_spgemm_batched_backward is the batched ts_spgemm_backward
+ * (gradient arrays are per instance; NULL entries skip that output).
+ */
+TS_API ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A, const ts_csr_desc* B,
+                                 int32_t semiring, const ts_tuning* force,
+                                 ts_batched_plan** out);
+TS_API ts_status ts_batched_plan_destroy(ts_batched_plan* plan);
+TS_API ts_status ts_batched_workspace_size(const ts_batched_plan* plan, size_t* bytes);
+TS_API ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                            int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream);
+TS_API ts_status ts_batched_bind(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                          const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream);
+TS_API ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, const ts_csr_desc* A,
+                            const ts_csr_desc* B, const ts_csr_desc* C, void* ws,
+                            size_t ws_bytes, void* stream);
+TS_API ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count,
+                                     const float* const* dC_val, float* const* dA_val,
+                                     float* const* dB_val, void* ws, size_t ws_bytes,
+                                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSSPGEMM_H */

@@ -10,6 +10,7 @@ What each function follows:
   spgemm      -- paper Sec. II-A (semiring product, flops = multiplications)
                  and Sec. III-A, Eq. 1 (row-wise Gustavson).
   msbfs       -- paper Alg. 3 (multi-source BFS over the boolean semiring).
+  bfs_levels  -- textbook FIFO-queue BFS (hop distance), one source.
   backward*   -- gradients of <dC, A*B> w.r.t. the stored values of A and B
                  (the product is bilinear, so these are exact sums).
 Every function is pinned by tests/test_oracle.py against something other than
@@ -57,9 +58,10 @@ def _L():
                 "oracle_spgemm_count": (i64, [i64, p, p, p, p, p, i64, p]),
                 "oracle_spgemm": (ci, [i64, ci, p, p, p, p, p, p, p, i64, p, p, p, p]),
                 "oracle_msbfs": (i64, [i64, p, p, i64, p, p, p, i64]),
-                "oracle_backward": (ci, [i64, i64, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+                "oracle_backward": (ci, [i64, i64, p, p, p, i64, p, p, p, p, p, p, p, p, p, p]),
                 "oracle_backward_dA_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
                 "oracle_backward_dB_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
+                "oracle_bfs_levels": (i64, [i64, p, p, ctypes.c_int32, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -135,6 +137,15 @@ def msbfs(A, sources: np.ndarray, maxlev: int = 4096):
     return levels, int(prods), fnnz[: prods + 1].copy()
 
 
+def bfs_levels(A, source: int) -> np.ndarray:
+    """Hop distances from one source by a FIFO-queue BFS (-1 = unreachable)."""
+    out = np.empty(A.nrows, dtype=np.int32)
+    r = _L().oracle_bfs_levels(A.nrows, _p(_i64(A.rowptr)), _p(_i32(A.col)), int(source), _p(out))
+    if r < 0:
+        raise MemoryError("oracle_bfs_levels")
+    return out
+
+
 def backward(A, B, C_rowptr, C_col, dC):
     """(dA, dA_bound, dB, dB_bound) of L = <dC, A*B> for plus-times."""
     n, d = A.nrows, B.ncols
@@ -143,7 +154,7 @@ def backward(A, B, C_rowptr, C_col, dC):
     dB = np.empty(max(B.nnz, 1), dtype=np.float64)
     dBb = np.empty_like(dB)
     st = _L().oracle_backward(n, d, _p(_i64(A.rowptr)), _p(_i32(A.col)), _p(_f64(A.val)),
-                              _p(_i64(B.rowptr)), _p(_i32(B.col)), _p(_f64(B.val)),
+                              B.nrows, _p(_i64(B.rowptr)), _p(_i32(B.col)), _p(_f64(B.val)),
                               _p(_i64(C_rowptr)), _p(_i32(C_col)), _p(_f64(dC)),
                               _p(dA), _p(dAb), _p(dB), _p(dBb))
     if st != 0:

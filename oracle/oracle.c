@@ -194,19 +194,20 @@ done:
  *   dA(i,k) = sum over j in row k of B of dC(i,j) * B(k,j)      for (i,k) in A
  *   dB(k,j) = sum over i with A(i,k) stored of A(i,k) * dC(i,j) for (k,j) in B
  * (dC is zero off C's pattern; C's pattern contains every (i,j) with a
- * product, so every lookup below finds its entry.)  Rows of A are visited in
+ * product, so every lookup below finds its entry.)  A has n rows (it may be
+ * a block of rows of a larger matrix), B has nB rows.  Rows of A are visited in
  * order; dB is summed by scattering each term to its entry.  dA_bound and
  * dB_bound receive the matching sums of absolute terms.  dA, dB and the bounds may each be NULL.
  * Returns 0, or -1 on allocation failure.
  */
 int oracle_backward(int64_t n, int64_t d, const int64_t* Ap, const int32_t* Ai, const double* Ax,
-                    const int64_t* Bp, const int32_t* Bi, const double* Bx, const int64_t* Cp,
+                    int64_t nB, const int64_t* Bp, const int32_t* Bi, const double* Bx, const int64_t* Cp,
                     const int32_t* Ci, const double* dC, double* dA, double* dA_bound, double* dB,
                     double* dB_bound) {
     double* g = (double*)calloc((size_t)(d > 0 ? d : 1), sizeof(double));
     if (!g) return -1;
-    if (dB) memset(dB, 0, (size_t)Bp[n] * sizeof(double));
-    if (dB_bound) memset(dB_bound, 0, (size_t)Bp[n] * sizeof(double));
+    if (dB) memset(dB, 0, (size_t)Bp[nB] * sizeof(double));
+    if (dB_bound) memset(dB_bound, 0, (size_t)Bp[nB] * sizeof(double));
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t e = Cp[i]; e < Cp[i + 1]; ++e) g[Ci[e]] = dC[e];
         for (int64_t e = Ap[i]; e < Ap[i + 1]; ++e) {
@@ -307,4 +308,32 @@ int oracle_backward_dB_rows(int64_t n, const int64_t* Ap, const int32_t* Ai, con
     }
     free(slot); free(base);
     return status;
+}
+
+/*
+ * Textbook single-source BFS with a FIFO queue (the definition of BFS level
+ * = hop distance along stored edges (v -> A.col) of A): levels[v] = distance
+ * from src, -1 if unreachable.  For a symmetric A this equals column s of the
+ * level matrix of Alg. 3.  Returns the largest level, -1 on allocation failure.
+ */
+int64_t oracle_bfs_levels(int64_t n, const int64_t* Ap, const int32_t* Ai, int32_t src, int32_t* levels) {
+    int32_t* queue = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!queue) return -1;
+    for (int64_t v = 0; v < n; ++v) levels[v] = -1;
+    int64_t head = 0, tail = 0, maxlev = 0;
+    levels[src] = 0;
+    queue[tail++] = src;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = Ap[u]; e < Ap[u + 1]; ++e) {
+            int32_t v = Ai[e];
+            if (levels[v] < 0) {
+                levels[v] = levels[u] + 1;
+                if (levels[v] > maxlev) maxlev = levels[v];
+                queue[tail++] = v;
+            }
+        }
+    }
+    free(queue);
+    return maxlev;
 }

@@ -1,0 +1,721 @@
+// Host side of the C ABI declared in include/tsspgemm.h: argument checks,
+// plans and tuning, workspace layout, and dispatch to the kernel launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tsspgemm.h"
+#include "kernels.h"
+#include "layout.h"
+
+using namespace ts;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static ts_status fail(ts_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+static ts_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(TS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define TS_CUDA(call, where)                         \
+    do {                                             \
+        cudaError_t _e = (call);                     \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+static ts_status ok() {
+    g_last_error.clear();
+    return TS_OK;
+}
+
+extern "C" const char* ts_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* ts_status_string(ts_status s) {
+    switch (s) {
+        case TS_OK: return "TS_OK";
+        case TS_ERR_INVALID_ARG: return "TS_ERR_INVALID_ARG";
+        case TS_ERR_BAD_CSR: return "TS_ERR_BAD_CSR";
+        case TS_ERR_UNSUPPORTED: return "TS_ERR_UNSUPPORTED";
+        case TS_ERR_WORKSPACE_TOO_SMALL: return "TS_ERR_WORKSPACE_TOO_SMALL";
+        case TS_ERR_CAPACITY: return "TS_ERR_CAPACITY";
+        case TS_ERR_OVERFLOW: return "TS_ERR_OVERFLOW";
+        case TS_ERR_CUDA: return "TS_ERR_CUDA";
+        case TS_ERR_STATE: return "TS_ERR_STATE";
+        default: return "TS_ERR_UNKNOWN";
+    }
+}
+
+extern "C" int32_t ts_version(void) { return 100; }  // 0.1.0
+
+extern "C" int64_t ts_kernel_launches(void) { return launch_count(); }
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 152;
+    return sms;
+}
+
+static ts_status check_desc(const ts_csr_desc* M, const char* name, bool need_val) {
+    if (!M) return fail(TS_ERR_INVALID_ARG, "%s: descriptor is NULL", name);
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0)
+        return fail(TS_ERR_INVALID_ARG, "%s: negative size", name);
+    if (M->nrows > INT32_MAX || M->ncols > INT32_MAX)
+        return fail(TS_ERR_UNSUPPORTED, "%s: more than 2^31-1 rows or columns", name);
+    if (!M->rowptr) return fail(TS_ERR_INVALID_ARG, "%s: rowptr is NULL", name);
+    if (M->nnz > 0 && !M->col) return fail(TS_ERR_INVALID_ARG, "%s: col is NULL", name);
+    if (need_val && M->nnz > 0 && !M->val)
+        return fail(TS_ERR_INVALID_ARG, "%s: val is NULL for the plus-times semiring", name);
+    return TS_OK;
+}
+
+static DevCsr dev(const ts_csr_desc* M) {
+    DevCsr c;
+    c.nrows = M->nrows;
+    c.ncols = M->ncols;
+    c.nnz = M->nnz;
+    c.rowptr = (const long long*)M->rowptr;
+    c.col = M->col;
+    c.val = (const float*)M->val;
+    return c;
+}
+
+static int cta_class_of(long long min_flops) {
+    int m = 0;
+    while ((1LL << m) < min_flops && m < 46) ++m;
+    return m + 1;
+}
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+struct ts_plan {
+    long long n = 0, d = 0;
+    int semiring = 0;
+    ts_tuning force{};
+    ts_tuning cur{};
+    // state of the last symbolic call (its row schedule lives in that ws)
+    bool sym_valid = false;
+    const void* sym_ws = nullptr;
+    const void* sym_ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long sym_nnz[2] = {0, 0};
+};
+
+static const long long MAX_D = 1LL << 20;
+
+static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t) {
+    const long long dpad = round_up(d, 32);
+    t = ts_tuning{};
+    t.accum = force.accum ? force.accum : (dpad <= 4096 ? TS_ACC_DENSE : TS_ACC_HASH);
+    t.col_tile = force.col_tile ? force.col_tile : (int)std::min<long long>(dpad, 1024);
+    t.cta_min_flops = force.cta_min_flops ? force.cta_min_flops : 4096;
+    t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
+    t.hash_slots = force.hash_slots ? force.hash_slots : 1024;
+    if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH)
+        return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE or TS_ACC_HASH");
+    if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
+        return fail(TS_ERR_INVALID_ARG, "tuning: col_tile must be a multiple of 32 in [32, 4096]");
+    if (t.col_tile > dpad) t.col_tile = (int)dpad;
+    if (t.cta_min_flops < 1) return fail(TS_ERR_INVALID_ARG, "tuning: cta_min_flops must be >= 1");
+    if (t.warps_per_cta < 1 || t.warps_per_cta > 32)
+        return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 32]");
+    if (t.hash_slots < 64 || (t.hash_slots & (t.hash_slots - 1)) || t.hash_slots > 8192)
+        return fail(TS_ERR_INVALID_ARG, "tuning: hash_slots must be a power of two in [64, 8192]");
+    return TS_OK;
+}
+
+struct Layout {
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, tp = 0, total = 0;
+    int W = 0, T = 1;
+};
+
+static Layout plan_layout(long long n, long long d, const ts_tuning& t) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    L.hdr = take(sizeof(WsHeader));
+    L.flops = take(sizeof(long long) * (size_t)n);
+    L.perm = take(sizeof(int) * (size_t)n);
+    L.partial = take(sizeof(long long) * scan_partial_count(n));
+    L.W = t.col_tile;
+    L.T = (int)((d + L.W - 1) / L.W);
+    if (L.T < 1) L.T = 1;
+    if (t.accum == TS_ACC_DENSE && L.T > 1) L.tp = take(sizeof(long long) * (size_t)n * (L.T + 1));
+    L.total = off;
+    return L;
+}
+
+static Sched carve(void* ws, const Layout& L) {
+    char* b = (char*)ws;
+    Sched s;
+    s.hdr = (WsHeader*)(b + L.hdr);
+    s.flops = (long long*)(b + L.flops);
+    s.perm = (int*)(b + L.perm);
+    s.partial = (long long*)(b + L.partial);
+    return s;
+}
+
+static LaunchCfg cfg_of(const ts_tuning& t) {
+    LaunchCfg c;
+    c.warps_per_cta = t.warps_per_cta;
+    c.cta_class = cta_class_of(t.cta_min_flops);
+    c.sms = sm_count();
+    return c;
+}
+
+extern "C" ts_status ts_plan_create(const ts_csr_desc* A, const ts_csr_desc* B, int32_t semiring,
+                                    const ts_tuning* force, ts_plan** out) {
+    if (!out) return fail(TS_ERR_INVALID_ARG, "ts_plan_create: out is NULL");
+    *out = nullptr;
+    if (semiring != TS_SR_PLUS_TIMES_F32 && semiring != TS_SR_OR_SELECT2ND_BOOL)
+        return fail(TS_ERR_INVALID_ARG, "ts_plan_create: unknown semiring %d", semiring);
+    if (!A || !B) return fail(TS_ERR_INVALID_ARG, "ts_plan_create: A or B is NULL");
+    if (A->nrows < 0 || A->ncols != A->nrows)
+        return fail(TS_ERR_INVALID_ARG, "ts_plan_create: A must be square (got %lld x %lld)",
+                    (long long)A->nrows, (long long)A->ncols);
+    if (B->nrows != A->ncols)
+        return fail(TS_ERR_INVALID_ARG, "ts_plan_create: B has %lld rows, A has %lld columns",
+                    (long long)B->nrows, (long long)A->ncols);
+    if (B->ncols < 1) return fail(TS_ERR_INVALID_ARG, "ts_plan_create: B needs d >= 1 columns");
+    if (B->ncols > MAX_D)
+        return fail(TS_ERR_UNSUPPORTED, "ts_plan_create: d = %lld above the supported %lld",
+                    (long long)B->ncols, MAX_D);
+    if (A->nrows > INT32_MAX) return fail(TS_ERR_UNSUPPORTED, "ts_plan_create: n >= 2^31");
+    ts_plan* p = new ts_plan;
+    p->n = A->nrows;
+    p->d = B->ncols;
+    p->semiring = semiring;
+    if (force) p->force = *force;
+    ts_status s = resolve_tuning(p->d, p->force, p->cur);
+    if (s != TS_OK) {
+        delete p;
+        return s;
+    }
+    *out = p;
+    return ok();
+}
+
+extern "C" ts_status ts_plan_destroy(ts_plan* plan) {
+    delete plan;
+    return ok();
+}
+
+extern "C" ts_status ts_plan_get_tuning(const ts_plan* plan, ts_tuning* out) {
+    if (!plan || !out) return fail(TS_ERR_INVALID_ARG, "ts_plan_get_tuning: NULL argument");
+    *out = plan->cur;
+    return ok();
+}
+
+extern "C" ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning) {
+    if (!plan || !tuning) return fail(TS_ERR_INVALID_ARG, "ts_plan_set_tuning: NULL argument");
+    ts_tuning merged = *tuning, t;
+    ts_status s = resolve_tuning(plan->d, merged, t);
+    if (s != TS_OK) return s;
+    plan->cur = t;
+    return ok();
+}
+
+extern "C" ts_status ts_workspace_size(const ts_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return fail(TS_ERR_INVALID_ARG, "ts_workspace_size: NULL argument");
+    *bytes = plan_layout(plan->n, plan->d, plan->cur).total;
+    return ok();
+}
+
+static ts_status check_operands(const ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                void* ws, size_t ws_bytes, const Layout& L, const char* fn) {
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    ts_status s;
+    if ((s = check_desc(A, "A", vals)) != TS_OK) return s;
+    if ((s = check_desc(B, "B", vals)) != TS_OK) return s;
+    if (A->nrows != plan->n || A->ncols != plan->n || B->nrows != plan->n || B->ncols != plan->d)
+        return fail(TS_ERR_INVALID_ARG, "%s: shapes differ from the plan's (n=%lld, d=%lld)", fn,
+                    plan->n, plan->d);
+    if (!ws && L.total) return fail(TS_ERR_INVALID_ARG, "%s: workspace is NULL", fn);
+    if (ws_bytes < L.total)
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: workspace of %zu bytes, %zu needed", fn,
+                    ws_bytes, L.total);
+    if (((uintptr_t)ws) & 255) return fail(TS_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
+    return TS_OK;
+}
+
+static bool same_operands(const ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B, void* ws) {
+    return plan->sym_valid && plan->sym_ws == ws && plan->sym_ptrs[0] == A->rowptr &&
+           plan->sym_ptrs[1] == A->col && plan->sym_ptrs[2] == B->rowptr &&
+           plan->sym_ptrs[3] == B->col && plan->sym_nnz[0] == A->nnz && plan->sym_nnz[1] == B->nnz;
+}
+
+static ts_status read_errors(void* ws, const Layout& L, cudaStream_t st, const char* fn) {
+    unsigned long long err = 0;
+    WsHeader* h = (WsHeader*)((char*)ws + L.hdr);
+    TS_CUDA(cudaMemcpyAsync(&err, &h->err, sizeof err, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (err)
+        return fail(TS_ERR_BAD_CSR, "%s: device checks failed (flags 0x%llx: %s%s%s%s)", fn, err,
+                    (err & ERR_A_COL) ? "column of A out of range; " : "",
+                    (err & ERR_B_COL) ? "column of B out of range; " : "",
+                    (err & ERR_C_ROW) ? "C row does not match its rowptr; " : "",
+                    (err & ERR_HASH_FULL) ? "hash table overflow; " : "");
+    return TS_OK;
+}
+
+extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                        int64_t* C_rowptr, int64_t* nnzC_host, void* ws,
+                                        size_t ws_bytes, void* stream) {
+    const char* fn = "ts_spgemm_symbolic";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    if (!C_rowptr) return fail(TS_ERR_INVALID_ARG, "%s: C_rowptr is NULL", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Sched sc = carve(ws, L);
+    const DevCsr dA = dev(A), dB = dev(B);
+    plan->sym_valid = false;
+    TS_CUDA(launch_row_schedule(dA, dB, sc, (long long*)C_rowptr, st), fn);
+    TS_CUDA(launch_symbolic(dA, dB, plan->d, sc, cfg_of(plan->cur), (long long*)C_rowptr, st), fn);
+    plan->sym_valid = true;
+    plan->sym_ws = ws;
+    plan->sym_ptrs[0] = A->rowptr;
+    plan->sym_ptrs[1] = A->col;
+    plan->sym_ptrs[2] = B->rowptr;
+    plan->sym_ptrs[3] = B->col;
+    plan->sym_nnz[0] = A->nnz;
+    plan->sym_nnz[1] = B->nnz;
+    if (nnzC_host) {
+        long long tot = 0;
+        TS_CUDA(cudaMemcpyAsync(&tot, (long long*)C_rowptr + plan->n, sizeof tot,
+                                cudaMemcpyDeviceToHost, st), fn);
+        s = read_errors(ws, L, st, fn);
+        if (s != TS_OK) return s;
+        if (tot > INT32_MAX * 64LL) return fail(TS_ERR_OVERFLOW, "%s: nnz(C) = %lld", fn, tot);
+        *nnzC_host = tot;
+    }
+    return ok();
+}
+
+extern "C" ts_status ts_workspace_check(const ts_plan* plan, void* ws, size_t ws_bytes, void* stream) {
+    if (!plan || !ws) return fail(TS_ERR_INVALID_ARG, "ts_workspace_check: NULL argument");
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    if (ws_bytes < sizeof(WsHeader)) return fail(TS_ERR_WORKSPACE_TOO_SMALL, "ts_workspace_check");
+    ts_status s = read_errors(ws, L, (cudaStream_t)stream, "ts_workspace_check");
+    return s == TS_OK ? ok() : s;
+}
+
+static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                             const ts_csr_desc* C, void* ws, const Layout& L, cudaStream_t st,
+                             const char* fn) {
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    const Sched sc = carve(ws, L);
+    const DevCsr dA = dev(A), dB = dev(B);
+    const LaunchCfg cfg = cfg_of(plan->cur);
+    if (plan->cur.accum == TS_ACC_DENSE) {
+        long long* tp = nullptr;
+        if (L.T > 1) {
+            tp = (long long*)((char*)ws + L.tp);
+            TS_CUDA(launch_tile_split(dB, L.W, L.T, tp, st), fn);
+        }
+        TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, sc, cfg,
+                                     (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                fn);
+    } else {
+        TS_CUDA(launch_numeric_hash(dA, dB, plan->d, plan->cur.hash_slots, vals, sc, cfg,
+                                    (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                fn);
+    }
+    return TS_OK;
+}
+
+extern "C" ts_status ts_spgemm_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                       const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream) {
+    const char* fn = "ts_spgemm_numeric";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    if ((s = check_desc(C, "C", vals)) != TS_OK) return s;
+    if (C->nrows != plan->n || C->ncols != plan->d)
+        return fail(TS_ERR_INVALID_ARG, "%s: C must be %lld x %lld", fn, plan->n, plan->d);
+    if (!same_operands(plan, A, B, ws))
+        return fail(TS_ERR_STATE, "%s: no symbolic pass on this plan with these A, B and workspace", fn);
+    s = run_numeric(plan, A, B, C, ws, L, (cudaStream_t)stream, fn);
+    return s == TS_OK ? ok() : s;
+}
+
+static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                              const ts_csr_desc* C, const float* dC, float* dA, float* dB, void* ws,
+                              size_t ws_bytes, void* stream, const char* fn) {
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    if (plan->semiring != TS_SR_PLUS_TIMES_F32)
+        return fail(TS_ERR_UNSUPPORTED, "%s: the boolean semiring has no gradient", fn);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    if (!C || !C->rowptr || (C->nnz > 0 && (!C->col || !dC)))
+        return fail(TS_ERR_INVALID_ARG, "%s: C pattern or dC is NULL", fn);
+    if (C->nrows != plan->n || C->ncols != plan->d || C->nnz < 0)
+        return fail(TS_ERR_INVALID_ARG, "%s: C must be %lld x %lld", fn, plan->n, plan->d);
+    if (!same_operands(plan, A, B, ws))
+        return fail(TS_ERR_STATE, "%s: no symbolic pass on this plan with these A, B and workspace", fn);
+    if (plan->d > 8192) return fail(TS_ERR_UNSUPPORTED, "%s: backward supports d <= 8192", fn);
+    const Sched sc = carve(ws, L);
+    TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
+                            dA, dB, sc, cfg_of(plan->cur), (cudaStream_t)stream),
+            fn);
+    return ok();
+}
+
+extern "C" ts_status ts_spgemm_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                        const ts_csr_desc* C, const float* dC_val, float* dA_val,
+                                        float* dB_val, void* ws, size_t ws_bytes, void* stream) {
+    return run_backward(plan, A, B, C, dC_val, dA_val, dB_val, ws, ws_bytes, stream,
+                        "ts_spgemm_backward");
+}
+
+extern "C" ts_status ts_spgemm_backward_dA(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                           const ts_csr_desc* C, const float* dC_val, float* dA_val,
+                                           void* ws, size_t ws_bytes, void* stream) {
+    if (!dA_val) return fail(TS_ERR_INVALID_ARG, "ts_spgemm_backward_dA: dA_val is NULL");
+    return run_backward(plan, A, B, C, dC_val, dA_val, nullptr, ws, ws_bytes, stream,
+                        "ts_spgemm_backward_dA");
+}
+
+extern "C" ts_status ts_spgemm_backward_dB(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                           const ts_csr_desc* C, const float* dC_val, float* dB_val,
+                                           void* ws, size_t ws_bytes, void* stream) {
+    if (!dB_val) return fail(TS_ERR_INVALID_ARG, "ts_spgemm_backward_dB: dB_val is NULL");
+    return run_backward(plan, A, B, C, dC_val, nullptr, dB_val, ws, ws_bytes, stream,
+                        "ts_spgemm_backward_dB");
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                      const ts_csr_desc* C, const float* dC_val, float* dA_scratch,
+                                      float* dB_scratch, int32_t reps, ts_tuning* chosen, void* ws,
+                                      size_t ws_bytes, void* stream) {
+    const char* fn = "ts_plan_autotune";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    if (reps < 1) return fail(TS_ERR_INVALID_ARG, "%s: reps must be >= 1", fn);
+    const Layout L0 = plan_layout(plan->n, plan->d, plan->cur);
+    ts_status s = check_operands(plan, A, B, ws, ws_bytes, L0, fn);
+    if (s != TS_OK) return s;
+    if (!same_operands(plan, A, B, ws))
+        return fail(TS_ERR_STATE, "%s: run ts_spgemm_symbolic on this plan and workspace first", fn);
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    if ((s = check_desc(C, "C", vals)) != TS_OK) return s;
+    const bool do_bwd = vals && dC_val && (dA_scratch || dB_scratch) && plan->d <= 8192;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long dpad = round_up(plan->d, 32);
+
+    // candidate grid; fields fixed by the plan's `force` are kept
+    std::vector<int> tiles;
+    for (int w : {64, 128, 256, 512, 1024, 2048, 4096})
+        if (w <= dpad && (w >= dpad / 16 || w >= 1024)) tiles.push_back(w);
+    if (tiles.empty() || tiles.back() < dpad) tiles.push_back((int)std::min<long long>(dpad, 4096));
+    std::vector<long long> thresholds = {1024, 4096, 16384, 65536};
+    std::vector<int> warps = {4, 8, 16};
+    std::vector<int> accs = {TS_ACC_DENSE};
+    if (plan->d > 256) accs.push_back(TS_ACC_HASH);
+
+    cudaEvent_t e0, e1;
+    TS_CUDA(cudaEventCreate(&e0), fn);
+    TS_CUDA(cudaEventCreate(&e1), fn);
+    const ts_tuning saved = plan->cur;
+    ts_tuning best = saved;
+    float best_ms = 1e30f;
+    auto try_one = [&](const ts_tuning& cand_in) -> ts_status {
+        ts_tuning cand;
+        if (resolve_tuning(plan->d, cand_in, cand) != TS_OK) return TS_OK;  // skip invalid
+        const Layout L = plan_layout(plan->n, plan->d, cand);
+        if (L.total > ws_bytes) return TS_OK;  // does not fit the caller's workspace
+        plan->cur = cand;
+        float tot = 0.0f;
+        for (int r = 0; r <= reps; ++r) {  // first run warms up
+            TS_CUDA(cudaEventRecord(e0, st), fn);
+            ts_status q = run_numeric(plan, A, B, C, ws, L, st, fn);
+            if (q != TS_OK) return q;
+            if (do_bwd) {
+                q = run_backward(plan, A, B, C, dC_val, dA_scratch, dB_scratch, ws, ws_bytes, stream, fn);
+                if (q != TS_OK) return q;
+            }
+            TS_CUDA(cudaEventRecord(e1, st), fn);
+            TS_CUDA(cudaEventSynchronize(e1), fn);
+            float ms = 0.0f;
+            TS_CUDA(cudaEventElapsedTime(&ms, e0, e1), fn);
+            if (r > 0) tot += ms;
+        }
+        const float avg = tot / reps;
+        if (avg < best_ms) {
+            best_ms = avg;
+            best = cand;
+        }
+        return TS_OK;
+    };
+    ts_tuning base = plan->force;
+    for (int acc : accs) {
+        if (plan->force.accum && acc != plan->force.accum) continue;
+        for (long long th : thresholds) {
+            if (plan->force.cta_min_flops && th != plan->force.cta_min_flops) continue;
+            for (int w : warps) {
+                if (plan->force.warps_per_cta && w != plan->force.warps_per_cta) continue;
+                ts_tuning c = base;
+                c.accum = acc;
+                c.cta_min_flops = th;
+                c.warps_per_cta = w;
+                if (acc == TS_ACC_DENSE) {
+                    for (int t : tiles) {
+                        if (plan->force.col_tile && t != plan->force.col_tile) continue;
+                        c.col_tile = t;
+                        s = try_one(c);
+                        if (s != TS_OK) break;
+                    }
+                } else {
+                    for (int hs : {512, 1024, 2048}) {
+                        if (plan->force.hash_slots && hs != plan->force.hash_slots) continue;
+                        c.hash_slots = hs;
+                        s = try_one(c);
+                        if (s != TS_OK) break;
+                    }
+                }
+                if (s != TS_OK) break;
+            }
+            if (s != TS_OK) break;
+        }
+        if (s != TS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TS_OK) {
+        plan->cur = saved;
+        return s;
+    }
+    plan->cur = best;
+    if (chosen) *chosen = best;
+    // leave C holding the product of the chosen tuning
+    const Layout Lb = plan_layout(plan->n, plan->d, best);
+    s = run_numeric(plan, A, B, C, ws, Lb, st, fn);
+    if (s != TS_OK) return s;
+    s = read_errors(ws, Lb, st, fn);
+    return s == TS_OK ? ok() : s;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+extern "C" size_t ts_validate_workspace_size(void) { return 256; }
+
+extern "C" ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, void* ws, size_t ws_bytes,
+                                     void* stream) {
+    const char* fn = "ts_csr_validate";
+    ts_status s = check_desc(M, "M", false);
+    if (s != TS_OK) return s;
+    if (!ws || ws_bytes < ts_validate_workspace_size())
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: needs %zu bytes of workspace", fn,
+                    ts_validate_workspace_size());
+    cudaStream_t st = (cudaStream_t)stream;
+    long long bad = -1;
+    TS_CUDA(launch_validate(dev(M), (long long*)ws, st), fn);
+    TS_CUDA(cudaMemcpyAsync(&bad, ws, sizeof bad, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (bad_row) *bad_row = bad;
+    if (bad != -1) return fail(TS_ERR_BAD_CSR, "%s: row %lld violates the CSR rules", fn, bad);
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// multi-source BFS (paper Alg. 3)
+// ---------------------------------------------------------------------------
+static const long long MSBFS_MAX_D = 65536;
+
+struct BfsLayout {
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, newbits = 0, total = 0;
+};
+
+static BfsLayout bfs_layout(long long n, long long d) {
+    BfsLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    L.hdr = take(sizeof(WsHeader));
+    L.flops = take(sizeof(long long) * (size_t)n);
+    L.perm = take(sizeof(int) * (size_t)n);
+    L.partial = take(sizeof(long long) * scan_partial_count(n));
+    L.newbits = take(sizeof(unsigned) * (size_t)n * (size_t)((d + 31) / 32));
+    L.total = off;
+    return L;
+}
+
+extern "C" ts_status msbfs_workspace_size(int64_t n, int64_t d, size_t* bytes) {
+    if (!bytes || n < 0 || d < 1) return fail(TS_ERR_INVALID_ARG, "msbfs_workspace_size: bad argument");
+    if (d > MSBFS_MAX_D) return fail(TS_ERR_UNSUPPORTED, "msbfs: d above %lld", MSBFS_MAX_D);
+    *bytes = bfs_layout(n, d).total;
+    return ok();
+}
+
+extern "C" ts_status msbfs_init(int64_t n, int64_t d, const int32_t* sources_dev, uint32_t* visited,
+                                int32_t* levels, const ts_csr_desc* F0, void* stream) {
+    const char* fn = "msbfs_init";
+    if (n < 0 || d < 1 || !sources_dev || !visited || !levels || !F0 || !F0->rowptr || !F0->col)
+        return fail(TS_ERR_INVALID_ARG, "%s: NULL or negative argument", fn);
+    if (n > INT32_MAX) return fail(TS_ERR_UNSUPPORTED, "%s: n >= 2^31", fn);
+    if (d > MSBFS_MAX_D) return fail(TS_ERR_UNSUPPORTED, "%s: d above %lld", fn, MSBFS_MAX_D);
+    if (F0->nrows != n || F0->ncols != d)
+        return fail(TS_ERR_INVALID_ARG, "%s: F0 must be %lld x %lld", fn, (long long)n, (long long)d);
+    if (F0->nnz < d) return fail(TS_ERR_CAPACITY, "%s: F0 needs room for %lld entries", fn, (long long)d);
+    TS_CUDA(launch_msbfs_init(n, (int)d, sources_dev, visited, levels, (long long*)F0->rowptr, F0->col,
+                              (cudaStream_t)stream),
+            fn);
+    return ok();
+}
+
+extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
+                                int32_t* levels, int32_t level, const ts_csr_desc* F_next,
+                                int64_t F_next_capacity, int64_t* nnz_next_host, void* ws,
+                                size_t ws_bytes, void* stream) {
+    const char* fn = "msbfs_step";
+    ts_status s;
+    if ((s = check_desc(A, "A", false)) != TS_OK) return s;
+    if ((s = check_desc(F, "F", false)) != TS_OK) return s;
+    if (!F_next || !F_next->rowptr || !visited || !levels || !nnz_next_host)
+        return fail(TS_ERR_INVALID_ARG, "%s: NULL argument", fn);
+    const long long n = A->nrows, d = F->ncols;
+    if (A->ncols != n || F->nrows != n || F_next->nrows != n || F_next->ncols != d)
+        return fail(TS_ERR_INVALID_ARG, "%s: A must be n x n, F and F_next n x d", fn);
+    if (d < 1 || d > MSBFS_MAX_D) return fail(TS_ERR_UNSUPPORTED, "%s: d must be in [1, %lld]", fn, MSBFS_MAX_D);
+    if (F_next_capacity < 0 || (F_next_capacity > 0 && !F_next->col))
+        return fail(TS_ERR_INVALID_ARG, "%s: bad F_next capacity", fn);
+    const BfsLayout L = bfs_layout(n, d);
+    if (!ws || ws_bytes < L.total)
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, L.total);
+    if (((uintptr_t)ws) & 255) return fail(TS_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* b = (char*)ws;
+    Sched sc;
+    sc.hdr = (WsHeader*)(b + L.hdr);
+    sc.flops = (long long*)(b + L.flops);
+    sc.perm = (int*)(b + L.perm);
+    sc.partial = (long long*)(b + L.partial);
+    unsigned* newbits = (unsigned*)(b + L.newbits);
+    ts_tuning t{};
+    resolve_tuning(d, ts_tuning{}, t);
+    LaunchCfg cfg = cfg_of(t);
+    TS_CUDA(launch_msbfs_step(dev(A), dev(F), (int)d, visited, levels, level, sc, newbits,
+                              (long long*)F_next->rowptr, cfg, st),
+            fn);
+    long long tot = 0;
+    TS_CUDA(cudaMemcpyAsync(&tot, (long long*)F_next->rowptr + n, sizeof tot, cudaMemcpyDeviceToHost, st), fn);
+    unsigned long long err = 0;
+    TS_CUDA(cudaMemcpyAsync(&err, &sc.hdr->err, sizeof err, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (err) return fail(TS_ERR_BAD_CSR, "%s: device checks failed (flags 0x%llx)", fn, err);
+    *nnz_next_host = tot;
+    if (tot > F_next_capacity)
+        return fail(TS_ERR_CAPACITY, "%s: next frontier has %lld entries, capacity %lld", fn, tot,
+                    (long long)F_next_capacity);
+    TS_CUDA(launch_msbfs_emit(n, (int)d, newbits, (const long long*)F_next->rowptr, F_next->col,
+                              F_next_capacity, sc.hdr, st),
+            fn);
+    return ok();
+}
+
+extern "C" ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, void* ws,
+                                size_t ws_bytes, void* stream) {
+    const char* fn = "msbfs_emit";
+    if (!F_next || !F_next->rowptr || !F_next->col || F_next_capacity < 0)
+        return fail(TS_ERR_INVALID_ARG, "%s: bad F_next", fn);
+    const long long n = F_next->nrows, d = F_next->ncols;
+    if (n < 0 || d < 1 || d > MSBFS_MAX_D) return fail(TS_ERR_INVALID_ARG, "%s: bad shape", fn);
+    const BfsLayout L = bfs_layout(n, d);
+    if (!ws || ws_bytes < L.total) return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long tot = 0;
+    TS_CUDA(cudaMemcpyAsync(&tot, (long long*)F_next->rowptr + n, sizeof tot, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (tot > F_next_capacity)
+        return fail(TS_ERR_CAPACITY, "%s: %lld entries, capacity %lld", fn, tot, (long long)F_next_capacity);
+    char* b = (char*)ws;
+    TS_CUDA(launch_msbfs_emit(n, (int)d, (const unsigned*)(b + L.newbits), (const long long*)F_next->rowptr,
+                              F_next->col, F_next_capacity, (WsHeader*)(b + L.hdr), st),
+            fn);
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// batched products (filled in by batched.cu's launchers)
+// ---------------------------------------------------------------------------
+struct ts_batched_plan {
+    int count = 0;
+};
+
+extern "C" ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A, const ts_csr_desc* B,
+                                            int32_t semiring, const ts_tuning* force,
+                                            ts_batched_plan** out) {
+    (void)count; (void)A; (void)B; (void)semiring; (void)force;
+    if (out) *out = nullptr;
+    return fail(TS_ERR_UNSUPPORTED, "ts_batched_plan_create: not built yet");
+}
+extern "C" ts_status ts_batched_plan_destroy(ts_batched_plan* plan) {
+    delete plan;
+    return ok();
+}
+extern "C" ts_status ts_batched_workspace_size(const ts_batched_plan* plan, size_t* bytes) {
+    (void)plan; (void)bytes;
+    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+}
+extern "C" ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                       int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream) {
+    (void)plan; (void)A; (void)B; (void)C_capacity; (void)ws; (void)ws_bytes; (void)stream;
+    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+}
+extern "C" ts_status ts_batched_bind(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                     const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream) {
+    (void)plan; (void)A; (void)B; (void)C; (void)ws; (void)ws_bytes; (void)stream;
+    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+}
+extern "C" ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, const ts_csr_desc* A,
+                                       const ts_csr_desc* B, const ts_csr_desc* C, void* ws,
+                                       size_t ws_bytes, void* stream) {
+    (void)plan; (void)count; (void)A; (void)B; (void)C; (void)ws; (void)ws_bytes; (void)stream;
+    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+}
+extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count,
+                                                const float* const* dC_val, float* const* dA_val,
+                                                float* const* dB_val, void* ws, size_t ws_bytes,
+                                                void* stream) {
+    (void)plan; (void)count; (void)dC_val; (void)dA_val; (void)dB_val; (void)ws; (void)ws_bytes; (void)stream;
+    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+}

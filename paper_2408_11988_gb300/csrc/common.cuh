@@ -1,0 +1,178 @@
+// Device building blocks of the TS-SpGEMM kernels (sm_103a).
+//
+// The product is row-wise Gustavson (paper Sec. III-A, Eq. 1): row i of C is
+// the semiring sum over the stored (i,k) of A(i,k) * B(k,:).  On the GPU a row
+// is processed by one warp (light rows) or one thread block (heavy rows); the
+// products of up to 32 entries of A are flattened across the 32 lanes so that
+// every lane handles one (k, j) pair per step regardless of how the rows of B
+// vary in length.  Accumulators live in shared memory (paper Sec. III-C: a
+// dense accumulator of width d, "SPA", or a hash table).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace ts {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int flops_class(long long f) {
+    if (f <= 0) return 0;
+    int c = 64 - __clzll(f);  // 1 + floor(log2 f)
+    return c < NUM_CLASSES ? c : NUM_CLASSES - 1;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Largest lane q whose (non-decreasing) key is <= p.  Lane 0's key must be <= p.
+__device__ __forceinline__ int owner_lane(int key, int p) {
+    int q = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        int k = __shfl_sync(FULL, key, q + s);
+        if (k <= p) q += s;
+    }
+    return q;
+}
+
+__device__ __forceinline__ long long shfl64(long long v, int src) {
+    return (long long)__shfl_sync(FULL, (unsigned long long)v, src);
+}
+
+// owner_lane for 64-bit keys.
+__device__ __forceinline__ int owner_lane64(long long key, long long p) {
+    int q = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        long long k = shfl64(key, q + s);
+        if (k <= p) q += s;
+    }
+    return q;
+}
+
+__device__ __forceinline__ long long clampll(long long v, long long lo, long long hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Segment of B's row k that a pass reads: the whole row, or the part of the
+// row inside one column tile (tile_ptr holds T+1 offsets per row of B).
+// Segments are clamped to [0, nnzB) and to at most `cap` entries (a row of
+// B holds at most d distinct columns), so even a malformed row pointer array
+// cannot move a gather outside B's arrays.
+struct SegWhole {
+    const long long* __restrict__ Bp;
+    long long nnzB;
+    int cap;
+    __device__ __forceinline__ void operator()(int k, long long& start, int& len) const {
+        long long s = __ldg(Bp + k), e = __ldg(Bp + k + 1);
+        s = s < 0 ? 0 : (s > nnzB ? nnzB : s);
+        e = e < s ? s : (e > nnzB ? nnzB : e);
+        start = s;
+        len = (int)(e - s < cap ? e - s : cap);
+    }
+};
+
+struct SegTile {
+    const long long* __restrict__ tp;  // [nB][T+1], already clamped to [0, nnzB]
+    int T1;                            // T + 1
+    int t;
+    int cap;
+    __device__ __forceinline__ void operator()(int k, long long& start, int& len) const {
+        const long long* r = tp + (long long)k * T1 + t;
+        long long s = __ldg(r), e = __ldg(r + 1);
+        start = s;
+        len = (int)(e > s ? (e - s < cap ? e - s : cap) : 0);
+    }
+};
+
+// Expand the products of the A entries e0 + lane (lane < nvalid) of one
+// chunk of up to 32 entries: for every pair (entry q, position j in B's
+// segment of row A.col[e0+q]) call visit.step(j, a_q, q, ok) with all 32
+// lanes converged; `ok` is false for padding lanes.  Steps are issued four at
+// a time where possible so that every lane has several gathers in flight.
+template <class Seg, class Visit>
+__device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
+                                             const float* __restrict__ Ax, int nB, const Seg& seg,
+                                             Visit& visit, unsigned long long* err) {
+    const int lane = lane_id();
+    long long start = 0;
+    int len = 0;
+    float a = 1.0f;
+    if (lane < nvalid) {
+        int k = __ldg(Ai + e0 + lane);
+        if ((unsigned)k < (unsigned)nB) {
+            seg(k, start, len);
+            if (Ax) a = __ldg(Ax + e0 + lane);
+        } else {
+            atomicOr(err, ERR_A_COL);
+        }
+    }
+    const int incl = warp_incl_scan(len);
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - len;
+    const long long shift = start - excl;  // position in B = shift(owner) + p
+    int p0 = 0;
+    for (; p0 + 128 <= total; p0 += 128) {
+        long long j[4];
+        float av[4];
+        int q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + 32 * u + lane;
+            q[u] = owner_lane(excl, p);
+            j[u] = shfl64(shift, q[u]) + p;
+            av[u] = __shfl_sync(FULL, a, q[u]);
+        }
+        visit.step4(j, av, q);
+    }
+    for (; p0 < total; p0 += 32) {
+        const int p = p0 + lane;
+        const int q = owner_lane(excl, p);
+        const long long j = shfl64(shift, q) + p;
+        const float av = __shfl_sync(FULL, a, q);
+        visit.step1(j, av, q, p < total);
+    }
+}
+
+// Exclusive-scan helper for per-word counts held in shared memory by one warp.
+// Replaces cnt[0..nw) by exclusive prefix sums; returns the total.
+__device__ __forceinline__ int warp_excl_scan_smem(int* cnt, int nw) {
+    const int lane = lane_id();
+    int carry = 0;
+    for (int b = 0; b < nw; b += 32) {
+        int v = (b + lane < nw) ? cnt[b + lane] : 0;
+        int inc = warp_incl_scan(v);
+        if (b + lane < nw) cnt[b + lane] = carry + inc - v;
+        carry += __shfl_sync(FULL, inc, 31);
+    }
+    return carry;
+}
+
+}  // namespace ts

@@ -1,0 +1,97 @@
+// Internal launchers of the TS-SpGEMM kernels (host side, C++).  The public C
+// ABI in include/tsspgemm.h is implemented on top of these in api.cpp.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ts {
+
+struct WsHeader;
+
+// CSR view with device pointers (int64 row pointers, int32 columns).
+struct DevCsr {
+    long long nrows = 0, ncols = 0, nnz = 0;
+    const long long* rowptr = nullptr;
+    const int* col = nullptr;
+    const float* val = nullptr;
+};
+
+// Row schedule written by the binning kernels into the workspace.
+struct Sched {
+    WsHeader* hdr = nullptr;     // counters, class histogram
+    long long* flops = nullptr;  // products per row of A, int64[n]
+    int* perm = nullptr;         // non-empty rows, heaviest class first, int32[n]
+    long long* partial = nullptr;// scan partial sums
+};
+
+struct LaunchCfg {
+    int warps_per_cta = 8;
+    int cta_class = 14;      // rows of flops class >= this run CTA-per-row
+    int sms = 152;
+};
+
+// Bytes of the scan partials for n values.
+size_t scan_partial_count(long long n);
+
+// flops per row, class histogram and (when Cp != nullptr) Cp[i+1] = 0 for
+// rows without products; then perm = non-empty rows ordered by class.
+cudaError_t launch_row_schedule(const DevCsr& A, const DevCsr& B, const Sched& s, long long* Cp,
+                                cudaStream_t st);
+// The two halves: flops per row (clears the header), and histogram + perm
+// from the flops array (Cp_next[i] = 0 for rows without products if given).
+cudaError_t launch_row_flops(const DevCsr& A, const DevCsr& B, const Sched& s, cudaStream_t st);
+cudaError_t launch_reclassify(long long n, const Sched& s, long long* Cp_next, cudaStream_t st);
+
+// Symbolic pass: Cp[i+1] = nnz(C_i) for the scheduled rows, then Cp = running sum.
+cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const Sched& s,
+                            const LaunchCfg& cfg, long long* Cp, cudaStream_t st);
+
+// In-place inclusive scan of x[0..n) (int64) using partial[] as scratch.
+cudaError_t launch_scan_inplace(long long* x, long long n, long long* partial, cudaStream_t st);
+
+// Column-tile offsets: tp[k*(T+1)+t] = first position of row k of B with
+// column >= t*W (t = 0..T; t = T gives the row end).
+cudaError_t launch_tile_split(const DevCsr& B, int W, int T, long long* tp, cudaStream_t st);
+
+// Numeric pass with a dense accumulator of width W over T column tiles.
+cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                 const long long* tp, bool values, const Sched& s,
+                                 const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx,
+                                 long long nnzC, cudaStream_t st);
+
+// Numeric pass with a per-warp hash accumulator of `slots` entries.
+cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, int slots,
+                                bool values, const Sched& s, const LaunchCfg& cfg,
+                                const long long* Cp, int* Ci, float* Cx, long long nnzC,
+                                cudaStream_t st);
+size_t numeric_dense_smem(int W, int warps, bool values);
+size_t numeric_hash_smem(int slots, int warps, bool values);
+
+// Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).
+cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const long long* Cp,
+                            const int* Ci, long long nnzC, const float* dC, float* dA, float* dB,
+                            const Sched& s, const LaunchCfg& cfg, cudaStream_t st);
+size_t backward_smem(long long d, int warps);
+
+// Multi-source BFS (Alg. 3) levels.
+cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, int* levels,
+                              long long* rp, int* col, cudaStream_t st);
+cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned* S, int* levels,
+                              int level, const Sched& s, unsigned* newbits, long long* rp_next,
+                              const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t launch_msbfs_emit(long long n, int d, const unsigned* newbits, const long long* rp,
+                              int* col, long long cap, WsHeader* hdr, cudaStream_t st);
+
+// CSR validation; writes the first bad row (or -1) into *bad (device).
+cudaError_t launch_validate(const DevCsr& M, long long* bad, cudaStream_t st);
+
+// Process-wide count of kernel launches made by this library.
+void count_launch();
+long long launch_count();
+
+// Occupancy-derived persistent grid size.
+int persistent_grid(const void* kernel, int threads, size_t smem, int sms);
+
+}  // namespace ts

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol include/tsspgemm.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_11988_gb300.build import build
+    from paper_2408_11988_gb300 import _native as N
+    build()
+    return N.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "tsspgemm.h")).read()
+    return sorted(set(re.findall(r"^TS_API [^(]*?\b([A-Za-z_][A-Za-z0-9_]*)\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 28
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_side_errors(lib):
+    from paper_2408_11988_gb300 import _native as N
+    A = N.CsrDesc(100, 100, 0, 8, None, None)      # fake non-NULL pointer, never dereferenced
+    B = N.CsrDesc(100, 64, 0, 8, None, None)
+    h = ctypes.c_void_p()
+    assert lib.ts_plan_create(None, ctypes.byref(B), 0, None, ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
+    Abad = N.CsrDesc(100, 99, 0, 8, None, None)
+    assert lib.ts_plan_create(ctypes.byref(Abad), ctypes.byref(B), 0, None, ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
+    assert "square" in N.last_error()
+    assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 7, None, ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
+    Bbig = N.CsrDesc(100, 1 << 21, 0, 8, None, None)
+    assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(Bbig), 0, None, ctypes.byref(h)) == N.TS_ERR_UNSUPPORTED
+    bad_t = N.Tuning(0, 48, 0, 0, 0)
+    assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bad_t), ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
+    assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, None, ctypes.byref(h)) == N.TS_OK
+    t = N.Tuning()
+    assert lib.ts_plan_get_tuning(h, ctypes.byref(t)) == N.TS_OK
+    assert t.accum == N.ACC_DENSE and t.col_tile == 64 and t.warps_per_cta == 8
+    sz = ctypes.c_size_t()
+    assert lib.ts_workspace_size(h, ctypes.byref(sz)) == N.TS_OK and sz.value > 100 * 12
+    # missing workspace and missing C row pointers are argument errors
+    assert lib.ts_spgemm_symbolic(h, ctypes.byref(A), ctypes.byref(B), None, None, None, 0, None) == N.TS_ERR_INVALID_ARG
+    rp = ctypes.c_void_p(256)
+    assert lib.ts_spgemm_symbolic(h, ctypes.byref(A), ctypes.byref(B), rp, None, ctypes.c_void_p(256), 16, None) \
+        == N.TS_ERR_WORKSPACE_TOO_SMALL
+    # numeric before symbolic is a state error, found before any launch
+    C = N.CsrDesc(100, 64, 0, 8, None, None)
+    assert lib.ts_spgemm_numeric(h, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), ctypes.c_void_p(256),
+                                 sz.value, None) == N.TS_ERR_STATE
+    assert lib.ts_plan_destroy(h) == N.TS_OK
+    assert lib.msbfs_workspace_size(10, 0, ctypes.byref(sz)) == N.TS_ERR_INVALID_ARG
+    assert lib.msbfs_workspace_size(10, 128, ctypes.byref(sz)) == N.TS_OK
+    assert N.status_string(N.TS_ERR_CAPACITY) == "TS_ERR_CAPACITY"
+    assert lib.ts_version() >= 100

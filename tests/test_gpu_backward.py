@@ -1,0 +1,125 @@
+"""GPU parity of the backward kernels and the autograd Function.
+
+dA = SDDMM(dC, B^T) on A's pattern, dB = A^T dC on B's pattern.  The CUDA
+gradients must be within 1e-5 * (sum of absolute terms) of the FP64 oracle
+per entry, and within 1e-4 relative of FP64 central differences of
+L = <dC, A*B> (exact for a bilinear L) wherever the gradient is not
+dominated by cancellation.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _cmp import REL
+
+pytestmark = pytest.mark.gpu
+
+from paper_2408_11988_gb300 import ACC_HASH, DeviceCSR, Plan
+from paper_2408_11988_gb300.autograd import ts_spgemm
+
+
+def dev(M):
+    return DeviceCSR.from_host(M)
+
+
+def _run(A, B, tuning=None, seed=1):
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd, tuning=tuning)
+    C = plan.forward(Ad, Bd)
+    dC = synth.grad_output(C.nnz, seed)
+    dA, dB = plan.backward(Ad, Bd, C, torch.as_tensor(dC, device="cuda"))
+    rp, col, _ = C.to_host()
+    return rp, col, dC, dA.cpu().numpy(), dB.cpu().numpy()
+
+
+@pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1}, {"cta_min_flops": 128, "warps_per_cta": 4},
+                                    {"warps_per_cta": 1}])
+def test_backward_matches_oracle(tuning):
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
+    rp, col, dC, dA, dB = _run(A, B, tuning)
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
+    assert np.all(np.abs(dA - rA) <= REL * bA), np.max(np.abs(dA - rA) / np.maximum(bA, 1e-30))
+    assert np.all(np.abs(dB - rB) <= REL * bB), np.max(np.abs(dB - rB) / np.maximum(bB, 1e-30))
+
+
+def test_backward_ragged_and_empty_rows():
+    A, B = synth.er_product(n=3000, k=5, d=100, density=0.05, seed=51)
+    rp, col, dC, dA, dB = _run(A, B)
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
+    assert np.all(np.abs(dA - rA) <= REL * bA)
+    assert np.all(np.abs(dB - rB) <= REL * bB)
+
+
+def test_backward_finite_differences():
+    A, B = synth.rmat_embedding(scale=9, edge_factor=8, d=64, density=0.1, seed=52)
+    rp, col, dC, dA, dB = _run(A, B, seed=3)
+    dC64 = dC.astype(np.float64)
+    Cp, Ci, Cx, _ = oracle.spgemm(A, B)
+
+    def loss(Av, Bv):
+        _, _, X, _ = oracle.spgemm(A.with_values(Av), B.with_values(Bv))
+        return float(np.dot(dC64, X))
+
+    rng = np.random.default_rng(0)
+    _, bA, _, bB = oracle.backward(A, B, rp, col, dC64)
+    Av, Bv = A.val.astype(np.float64), B.val.astype(np.float64)
+    checked = 0
+    for e in rng.choice(A.nnz, 128, replace=False):
+        p, m = Av.copy(), Av.copy()
+        p[e] += 1.0
+        m[e] -= 1.0
+        fd = (loss(p, Bv) - loss(m, Bv)) / 2.0
+        assert abs(dA[e] - fd) <= REL * bA[e] + 1e-12
+        if abs(fd) >= 1e-2 * bA[e]:
+            assert abs(dA[e] - fd) <= 1e-4 * abs(fd)
+            checked += 1
+    for f in rng.choice(B.nnz, 128, replace=False):
+        p, m = Bv.copy(), Bv.copy()
+        p[f] += 1.0
+        m[f] -= 1.0
+        fd = (loss(Av, p) - loss(Av, m)) / 2.0
+        assert abs(dB[f] - fd) <= REL * bB[f] + 1e-12
+        if abs(fd) >= 1e-2 * bB[f]:
+            assert abs(dB[f] - fd) <= 1e-4 * abs(fd)
+            checked += 1
+    assert checked > 100
+
+
+def test_autograd_function():
+    A, B = synth.rmat_embedding(scale=11, edge_factor=16, d=128, density=0.1, seed=53)
+    Ad, Bd = dev(A), dev(B)
+    a = Ad.val.clone().requires_grad_(True)
+    b = Bd.val.clone().requires_grad_(True)
+    C = ts_spgemm(Ad, Bd, a, b)
+    g = torch.as_tensor(synth.grad_output(C.nnz, 9), device="cuda")
+    (C.val * g).sum().backward()
+    rp, col, _ = C.to_host()
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, g.double().cpu().numpy())
+    assert np.all(np.abs(a.grad.cpu().numpy() - rA) <= REL * bA)
+    assert np.all(np.abs(b.grad.cpu().numpy() - rB) <= REL * bB)
+
+
+def test_backward_full_size_sampled():
+    # sparse-embedding workload at full size (R-MAT scale 22, d = 256, 5 %)
+    A, B = synth.rmat_embedding()
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    C = plan.forward(Ad, Bd)
+    dC = synth.grad_output(C.nnz, 11)
+    dA, dB = plan.backward(Ad, Bd, C, torch.as_tensor(dC, device="cuda"))
+    rp, col, _ = C.to_host()
+    rng = np.random.default_rng(1)
+    deg = np.diff(A.rowptr)
+    rows = np.concatenate([np.argsort(deg)[-4:], rng.choice(A.nrows, 2000, replace=False)])
+    sA, bA = oracle.backward_dA_rows(A, B, rp, col, dC.astype(np.float64), rows)
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows])
+    gA = dA.cpu().numpy()[idx]
+    assert np.all(np.abs(gA - sA) <= REL * bA)
+    indeg = np.bincount(A.col, minlength=A.nrows)
+    krows = np.unique(np.concatenate([np.argsort(indeg)[-4:], rng.choice(B.nrows, 2000, replace=False)]))
+    sB, bB = oracle.backward_dB_rows(A, B, rp, col, dC.astype(np.float64), krows)
+    idx = np.concatenate([np.arange(B.rowptr[k], B.rowptr[k + 1]) for k in krows])
+    gB = dB.cpu().numpy()[idx]
+    assert np.all(np.abs(gB - sB) <= REL * bB)

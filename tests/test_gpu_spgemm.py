@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA product (through the C ABI) against the FP64 oracle.
+
+Patterns and boolean results must be bit-exact; plus-times values must be
+within 1e-5 * sum |a_ik||b_kj| of the FP64 oracle per entry.  Every accumulator,
+tile width, row-bin threshold and block size is forced at least once.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import CSR
+from _cmp import compare_full, compare_rows, assert_pattern_equal, assert_values_close
+
+pytestmark = pytest.mark.gpu
+
+from paper_2408_11988_gb300 import (ACC_DENSE, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, DeviceCSR, Plan,
+                                    TSError, spgemm, validate)
+
+
+def dev(M):
+    return DeviceCSR.from_host(M)
+
+
+TUNINGS = [
+    None,
+    {"col_tile": 32},                         # two column tiles of B (d = 64)
+    {"cta_min_flops": 1},                      # every row CTA-per-row
+    {"cta_min_flops": 64},
+    {"warps_per_cta": 1},
+    {"warps_per_cta": 32, "cta_min_flops": 16},
+    {"accum": ACC_HASH, "hash_slots": 128},
+    {"accum": ACC_HASH, "hash_slots": 1024, "warps_per_cta": 4},
+]
+
+
+@pytest.fixture(scope="module")
+def er_case():
+    # the Erdos-Renyi workload at its full size: n = 16384, 8 per row, d = 64, 10 %
+    return synth.er_product(n=16384, k=8, d=64, density=0.10)
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_er_full_size(er_case, tuning):
+    A, B = er_case
+    C = spgemm(dev(A), dev(B), tuning=tuning)
+    compare_full(C, A, B)
+
+
+@pytest.mark.parametrize("tuning", [None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH}])
+def test_er_boolean(er_case, tuning):
+    A, B = er_case
+    C = spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=tuning)
+    assert C.val is None
+    compare_full(C, A, B, semiring=oracle.OR_SELECT2ND)
+
+
+@pytest.mark.parametrize("tuning", [None, {"col_tile": 64}, {"col_tile": 96}, {"cta_min_flops": 128},
+                                    {"accum": ACC_HASH, "hash_slots": 512}])
+def test_rmat_embedding_small(tuning):
+    A, B = synth.rmat_embedding(scale=13, edge_factor=16, d=256, density=0.05, seed=31)
+    C = spgemm(dev(A), dev(B), tuning=tuning)
+    compare_full(C, A, B)
+
+
+def test_rmat_tiled_d1024():
+    # the large tiled product's shape at small scale: d = 1024, 1 %, tiles of 256
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=1024, density=0.01, seed=32, b_values="uniform")
+    for t in (None, {"col_tile": 256}, {"col_tile": 256, "cta_min_flops": 32}, {"accum": ACC_HASH}):
+        compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+
+
+def test_large_d_hash_and_tiles():
+    A = synth.rmat(11, 8, 33)
+    A.val = synth.uniform(A.nnz, 34)
+    B = synth.tall_skinny(A.nrows, 5000, 0.002, 35)
+    B.val = synth.normal(B.nnz, 36)
+    for t in (None, {"accum": ACC_HASH, "hash_slots": 256}, {"accum": ACC_DENSE, "col_tile": 2048}):
+        compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+
+
+def _csr(n, ncols, rows, vals=True, seed=0):
+    rng = np.random.default_rng(seed)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    cols = []
+    for i, r in enumerate(rows):
+        r = np.unique(np.asarray(r, dtype=np.int64))
+        cols.append(r)
+        rowptr[i + 1] = rowptr[i] + r.size
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    val = rng.random(col.size).astype(np.float32) if vals else None
+    return CSR(n, ncols, rowptr, col, val)
+
+
+@pytest.mark.parametrize("n,d", [(1, 1), (3, 33), (200, 100), (64, 32)])
+def test_small_shapes_and_ragged_d(n, d):
+    rng = np.random.default_rng(n * 7 + d)
+    A = _csr(n, n, [rng.choice(n, size=rng.integers(0, n + 1), replace=False) for _ in range(n)], seed=1)
+    B = _csr(n, d, [rng.choice(d, size=rng.integers(0, d + 1), replace=False) for _ in range(n)], seed=2)
+    for t in (None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH, "hash_slots": 256}):
+        compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+
+
+def test_empty_operands():
+    n, d = 500, 64
+    A, B = synth.er_product(n=n, k=4, d=d, density=0.1, seed=5)
+    Z = CSR(n, n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    Zb = CSR(n, d, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    for a, b in ((Z, B), (A, Zb), (Z, Zb)):
+        C = spgemm(dev(a), dev(b))
+        rp, col, val = C.to_host()
+        assert np.all(rp == 0) and C.nnz == 0
+
+
+def test_identity_is_exact():
+    n, d = 3000, 96
+    B = synth.tall_skinny(n, d, 0.3, 7)
+    B.val = synth.normal(B.nnz, 8)
+    I = CSR(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n, np.float32))
+    for t in (None, {"col_tile": 32}, {"accum": ACC_HASH}):
+        rp, col, val = spgemm(dev(I), dev(B), tuning=t).to_host()
+        np.testing.assert_array_equal(rp, B.rowptr)
+        np.testing.assert_array_equal(col, B.col)
+        assert np.array_equal(val, B.val)  # one term 1*b per entry: bit-exact
+
+
+def test_hub_row_and_dense_b():
+    n, d = 6000, 128
+    rng = np.random.default_rng(9)
+    rows = [np.arange(n)] + [rng.choice(n, size=3, replace=False) for _ in range(n - 1)]
+    A = _csr(n, n, rows, seed=10)                  # row 0 touches every row of B
+    B = synth.tall_skinny(n, d, 1.0, 11)           # fully dense rows
+    B.val = synth.uniform(B.nnz, 12)
+    for t in (None, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 2}):
+        compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+
+
+def test_embedding_full_size_sampled():
+    # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %
+    A, B = synth.rmat_embedding()
+    Ad, Bd = dev(A), dev(B)
+    C = spgemm(Ad, Bd)
+    rp = C.rowptr.cpu().numpy()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= B.ncols)
+    deg = np.diff(A.rowptr)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([np.argsort(deg)[-8:], rng.choice(A.nrows, 3000, replace=False)])
+    compare_rows(C, A, B, rows)
+
+
+def test_validate_and_device_checks():
+    n, d = 1000, 64
+    A, B = synth.er_product(n=n, k=6, d=d, density=0.1, seed=14)
+    validate(dev(A))
+    validate(dev(B))
+    bad = CSR(n, d, B.rowptr.copy(), B.col.copy(), B.val)
+    r = int(np.nonzero(np.diff(B.rowptr) >= 2)[0][0])
+    s = int(B.rowptr[r])
+    bad.col[s], bad.col[s + 1] = bad.col[s + 1], bad.col[s]   # unsorted row
+    with pytest.raises(TSError) as ei:
+        validate(dev(bad))
+    assert ei.value.status == -2
+    # a column of B outside [0, d) is caught by the kernels' own checks
+    oob = CSR(n, d, B.rowptr.copy(), B.col.copy(), B.val)
+    oob.col[s] = d + 5
+    plan = Plan(dev(A), dev(oob))
+    with pytest.raises(TSError) as ei:
+        plan.forward(dev(A), dev(oob))
+    assert ei.value.status == -2
+
+
+def test_state_and_argument_errors():
+    A, B = synth.er_product(n=300, k=4, d=64, density=0.1, seed=15)
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    rowptr = torch.zeros(301, dtype=torch.int64, device="cuda")
+    C = plan.alloc_c(rowptr, 0)
+    with pytest.raises(TSError) as ei:       # numeric before any symbolic pass
+        plan.numeric(Ad, Bd, C)
+    assert ei.value.status == -8
+    with pytest.raises(TSError):
+        Plan(Ad, dev(synth.tall_skinny(299, 64, 0.1, 1)))
+    with pytest.raises(TSError):
+        Plan(Ad, Bd, tuning={"col_tile": 48})
+
+
+def test_autotune_keeps_results():
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=40)
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    C = plan.forward(Ad, Bd)
+    dC = torch.randn(C.nnz, device="cuda")
+    best = plan.autotune(Ad, Bd, C, dC_val=dC, reps=1)
+    assert best["col_tile"] % 32 == 0
+    compare_full(C, A, B)
+    compare_full(plan.forward(Ad, Bd), A, B)

@@ -203,6 +203,7 @@ def test_msbfs_matches_queue_bfs(kind):
     for s_idx, s in enumerate(srcs):
         ref = queue_bfs(A, int(s))
         np.testing.assert_array_equal(levels[:, s_idx], ref)
+        np.testing.assert_array_equal(oracle.bfs_levels(A, int(s)), ref)
         maxlev = max(maxlev, int(ref.max()))
     assert prods == maxlev + 1
     assert fnnz.sum() == int((levels >= 0).sum())
