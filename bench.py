@@ -116,9 +116,11 @@ def dist_env():
     return ws, rank, local
 
 
-def make_inputs(name, seed_offset=0):
+def make_inputs(name, seed_offset=0, scale=None):
     import synth
     desc, kw, tuning, bwd = WORKLOADS[name]
+    if scale is not None and kw is not None:
+        kw = dict(kw, scale=scale)
     if name == "er-16k":
         A, B = synth.er_product(seed=synth.BASE_SEED + 1 + 1000 * seed_offset)
     else:
@@ -178,6 +180,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
     ap.add_argument("--tuning", default=None, help="JSON dict of forced tuning fields")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="R-MAT scale override (smaller copies of a workload for profiling)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     desc, _, wl_tuning, want_bwd = WORKLOADS[args.workload]
@@ -194,7 +198,7 @@ def main():
     from paper_2408_11988_gb300 import _native as N
     import synth
 
-    A, B = make_inputs(args.workload, seed_offset=rank)
+    A, B = make_inputs(args.workload, seed_offset=rank, scale=args.scale)
     flops_row = products_per_row(A, B)
     F = int(flops_row.sum())
     Ad, Bd = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
@@ -282,7 +286,8 @@ def main():
             "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "n": n, "d": B.ncols,
+            "config": {"workload": args.workload + (f"@scale{args.scale}" if args.scale else ""),
+                       "description": desc, "n": n, "d": B.ncols,
                        "nnz_A": nnzA, "nnz_B": B.nnz, "nnz_C": nnzC, "products": F,
                        "tuning": plan.tuning, "l2": "inputs larger than L2 (A+B+C > 129 MB)",
                        "parallelism": f"replicas x{ws}"},

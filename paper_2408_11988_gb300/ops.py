@@ -65,7 +65,7 @@ class DeviceCSR:
         rp = self.rowptr.cpu().numpy()
         n = int(rp[-1])
         col = self.col[:n].cpu().numpy()
-        val = None if self.val is None else self.val[:n].cpu().numpy()
+        val = None if self.val is None else self.val[:n].detach().cpu().numpy()
         return rp, col, val
 
 
