@@ -88,8 +88,14 @@ typedef struct ts_csr_desc {
  *                 concatenation of its tiles (B column tiling).
  *  cta_min_flops  rows with at least this many products (rounded up to a
  *                 power of two) run CTA-per-row; lighter rows warp-per-row.
- *  warps_per_cta  warps per thread block (1..32).
+ *  warps_per_cta  warps per thread block (1..8).
  *  hash_slots     slots of a warp's hash table (power of two, >= 64).
+ *  group          how a warp spreads the products of 32 entries of A over its
+ *                 lanes: 1 = one product per lane across entries (any mix of
+ *                 B row lengths); 4, 8, 16 or 32 = that many lanes walk one
+ *                 entry's row of B (best for rows of about that length).
+ *  pack_b         1 = gather B from a packed (column, value) copy built in the
+ *                 workspace at each call, 2 = from B's own arrays.
  */
 typedef struct ts_tuning {
     int32_t accum;
@@ -97,6 +103,8 @@ typedef struct ts_tuning {
     int64_t cta_min_flops;
     int32_t warps_per_cta;
     int32_t hash_slots;
+    int32_t group;
+    int32_t pack_b;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;
@@ -135,7 +143,8 @@ TS_API ts_status ts_plan_destroy(ts_plan* plan);
 TS_API ts_status ts_plan_get_tuning(const ts_plan* plan, ts_tuning* out);
 TS_API ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning);
 
-/* Device workspace needed by symbolic, numeric, backward and autotune. */
+/* Device workspace needed by symbolic, numeric, backward and autotune (for
+ * plus-times it covers every tuning the autotuner may choose). */
 TS_API ts_status ts_workspace_size(const ts_plan* plan, size_t* bytes);
 
 /*
@@ -215,6 +224,9 @@ TS_API ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const ts_
 /*
  * Multi-source BFS (paper Alg. 3) one level at a time.
  *
+ * msbfs_workspace_size: device workspace for a graph of n vertices and nnz_A
+ * stored edges with d sources.
+ *
  * msbfs_init: F0 gets the frontier of d sources (F0(src[s], s) = 1), the
  * visited bitmap S (uint32[n * ceil(d/32)], bit s of vertex v at word
  * v*ceil(d/32) + s/32) is set to F0, levels (int32[n*d], vertex-major) to
@@ -234,7 +246,7 @@ TS_API ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const ts_
  * in *nnz_next_host; S, levels and F_next->rowptr are then already updated
  * and the call must be repeated by msbfs_emit with a larger buffer.
  */
-TS_API ts_status msbfs_workspace_size(int64_t n, int64_t d, size_t* bytes);
+TS_API ts_status msbfs_workspace_size(int64_t n, int64_t nnz_A, int64_t d, size_t* bytes);
 TS_API ts_status msbfs_init(int64_t n, int64_t d, const int32_t* sources_dev, uint32_t* visited,
                      int32_t* levels, const ts_csr_desc* F0, void* stream);
 TS_API ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,

@@ -38,7 +38,8 @@ class CsrDesc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("accum", c_int32), ("col_tile", c_int32), ("cta_min_flops", c_int64),
-                ("warps_per_cta", c_int32), ("hash_slots", c_int32)]
+                ("warps_per_cta", c_int32), ("hash_slots", c_int32), ("group", c_int32),
+                ("pack_b", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,7 +84,7 @@ _SIGS = {
                                         c_void_p, c_void_p, c_size_t, c_void_p]),
     "ts_plan_autotune": (c_int32, [c_void_p, P(CsrDesc), P(CsrDesc), P(CsrDesc), c_void_p, c_void_p,
                                    c_void_p, c_int32, P(Tuning), c_void_p, c_size_t, c_void_p]),
-    "msbfs_workspace_size": (c_int32, [c_int64, c_int64, P(c_size_t)]),
+    "msbfs_workspace_size": (c_int32, [c_int64, c_int64, c_int64, P(c_size_t)]),
     "msbfs_init": (c_int32, [c_int64, c_int64, c_void_p, c_void_p, c_void_p, P(CsrDesc), c_void_p]),
     "msbfs_step": (c_int32, [P(CsrDesc), P(CsrDesc), c_void_p, c_void_p, c_int32, P(CsrDesc),
                              c_int64, P(c_int64), c_void_p, c_size_t, c_void_p]),

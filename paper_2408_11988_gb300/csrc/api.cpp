@@ -115,6 +115,7 @@ static int cta_class_of(long long min_flops) {
 // ---------------------------------------------------------------------------
 struct ts_plan {
     long long n = 0, d = 0;
+    long long nnzA = 0, nnzB = 0;
     int semiring = 0;
     ts_tuning force{};
     ts_tuning cur{};
@@ -127,7 +128,18 @@ struct ts_plan {
 
 static const long long MAX_D = 1LL << 20;
 
-static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t) {
+// Lanes per A entry: the power of two at or above the mean row length of B,
+// in [4, 32]; rows of fewer than 3 entries on average use the flattened mode.
+static int auto_group(long long nB, long long nnzB) {
+    const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
+    if (avg < 3.0) return 1;
+    int g = 4;
+    while (g < 32 && g < avg) g *= 2;
+    return g;
+}
+
+static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t,
+                                long long nB = 0, long long nnzB = 0) {
     const long long dpad = round_up(d, 32);
     t = ts_tuning{};
     t.accum = force.accum ? force.accum : (dpad <= 4096 ? TS_ACC_DENSE : TS_ACC_HASH);
@@ -135,25 +147,35 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.cta_min_flops = force.cta_min_flops ? force.cta_min_flops : 4096;
     t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
     t.hash_slots = force.hash_slots ? force.hash_slots : 1024;
+    t.group = force.group ? force.group : auto_group(nB, nnzB);
+    t.pack_b = force.pack_b ? force.pack_b : 2;
+    if (t.group != 1 && t.group != 4 && t.group != 8 && t.group != 16 && t.group != 32)
+        return fail(TS_ERR_INVALID_ARG, "tuning: group must be 1, 4, 8, 16 or 32");
+    if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
     if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH)
         return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE or TS_ACC_HASH");
     if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
         return fail(TS_ERR_INVALID_ARG, "tuning: col_tile must be a multiple of 32 in [32, 4096]");
     if (t.col_tile > dpad) t.col_tile = (int)dpad;
     if (t.cta_min_flops < 1) return fail(TS_ERR_INVALID_ARG, "tuning: cta_min_flops must be >= 1");
-    if (t.warps_per_cta < 1 || t.warps_per_cta > 32)
-        return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 32]");
+    if (t.warps_per_cta < 1 || t.warps_per_cta > 8)
+        return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 8]");
     if (t.hash_slots < 64 || (t.hash_slots & (t.hash_slots - 1)) || t.hash_slots > 8192)
         return fail(TS_ERR_INVALID_ARG, "tuning: hash_slots must be a power of two in [64, 8192]");
     return TS_OK;
 }
 
 struct Layout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, tp = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, tp = 0, bpk = 0, total = 0;
     int W = 0, T = 1;
 };
 
-static Layout plan_layout(long long n, long long d, const ts_tuning& t) {
+// Workspace layout for tuning t.  With `cover_autotune`, the column-tile and
+// packed-B regions are sized for every tuning the autotuner may try (tiles
+// of at least max(64, d/8) columns, packing on), so that one workspace
+// serves the whole search.
+static Layout plan_layout(long long n, long long d, const ts_tuning& t, long long nnzA, long long nnzB,
+                          bool cover_autotune = false) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -165,10 +187,18 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t) {
     L.flops = take(sizeof(long long) * (size_t)n);
     L.perm = take(sizeof(int) * (size_t)n);
     L.partial = take(sizeof(long long) * scan_partial_count(n));
+    L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
     L.W = t.col_tile;
     L.T = (int)((d + L.W - 1) / L.W);
     if (L.T < 1) L.T = 1;
-    if (t.accum == TS_ACC_DENSE && L.T > 1) L.tp = take(sizeof(long long) * (size_t)n * (L.T + 1));
+    int Tmax = (t.accum == TS_ACC_DENSE) ? L.T : 1;
+    if (cover_autotune) {
+        const long long dpad = round_up(d, 32);
+        const long long wmin = std::max<long long>(64, round_up(dpad / 8, 32));
+        Tmax = std::max<int>(Tmax, (int)((d + wmin - 1) / wmin));
+    }
+    if (Tmax > 1) L.tp = take(sizeof(long long) * (size_t)n * (Tmax + 1));
+    if (t.pack_b == 1 || cover_autotune) L.bpk = take(8 * (size_t)nnzB);
     L.total = off;
     return L;
 }
@@ -180,6 +210,7 @@ static Sched carve(void* ws, const Layout& L) {
     s.flops = (long long*)(b + L.flops);
     s.perm = (int*)(b + L.perm);
     s.partial = (long long*)(b + L.partial);
+    s.items = (long long*)(b + L.items);
     return s;
 }
 
@@ -188,6 +219,7 @@ static LaunchCfg cfg_of(const ts_tuning& t) {
     c.warps_per_cta = t.warps_per_cta;
     c.cta_class = cta_class_of(t.cta_min_flops);
     c.sms = sm_count();
+    c.group = t.group;
     return c;
 }
 
@@ -212,9 +244,11 @@ extern "C" ts_status ts_plan_create(const ts_csr_desc* A, const ts_csr_desc* B, 
     ts_plan* p = new ts_plan;
     p->n = A->nrows;
     p->d = B->ncols;
+    p->nnzA = A->nnz;
+    p->nnzB = B->nnz;
     p->semiring = semiring;
     if (force) p->force = *force;
-    ts_status s = resolve_tuning(p->d, p->force, p->cur);
+    ts_status s = resolve_tuning(p->d, p->force, p->cur, p->n, p->nnzB);
     if (s != TS_OK) {
         delete p;
         return s;
@@ -237,7 +271,7 @@ extern "C" ts_status ts_plan_get_tuning(const ts_plan* plan, ts_tuning* out) {
 extern "C" ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning) {
     if (!plan || !tuning) return fail(TS_ERR_INVALID_ARG, "ts_plan_set_tuning: NULL argument");
     ts_tuning merged = *tuning, t;
-    ts_status s = resolve_tuning(plan->d, merged, t);
+    ts_status s = resolve_tuning(plan->d, merged, t, plan->n, plan->nnzB);
     if (s != TS_OK) return s;
     plan->cur = t;
     return ok();
@@ -245,7 +279,8 @@ extern "C" ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning) 
 
 extern "C" ts_status ts_workspace_size(const ts_plan* plan, size_t* bytes) {
     if (!plan || !bytes) return fail(TS_ERR_INVALID_ARG, "ts_workspace_size: NULL argument");
-    *bytes = plan_layout(plan->n, plan->d, plan->cur).total;
+    *bytes = plan_layout(plan->n, plan->d, plan->cur, plan->nnzA, plan->nnzB,
+                         plan->semiring == TS_SR_PLUS_TIMES_F32).total;
     return ok();
 }
 
@@ -292,7 +327,7 @@ extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, con
                                         size_t ws_bytes, void* stream) {
     const char* fn = "ts_spgemm_symbolic";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
-    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
     ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
     if (!C_rowptr) return fail(TS_ERR_INVALID_ARG, "%s: C_rowptr is NULL", fn);
@@ -324,7 +359,7 @@ extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, con
 
 extern "C" ts_status ts_workspace_check(const ts_plan* plan, void* ws, size_t ws_bytes, void* stream) {
     if (!plan || !ws) return fail(TS_ERR_INVALID_ARG, "ts_workspace_check: NULL argument");
-    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur, plan->nnzA, plan->nnzB);
     if (ws_bytes < sizeof(WsHeader)) return fail(TS_ERR_WORKSPACE_TOO_SMALL, "ts_workspace_check");
     ts_status s = read_errors(ws, L, (cudaStream_t)stream, "ts_workspace_check");
     return s == TS_OK ? ok() : s;
@@ -343,7 +378,12 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
             tp = (long long*)((char*)ws + L.tp);
             TS_CUDA(launch_tile_split(dB, L.W, L.T, tp, st), fn);
         }
-        TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, sc, cfg,
+        int2* bpk = nullptr;
+        if (vals && plan->cur.pack_b == 1 && B->nnz > 0) {
+            bpk = (int2*)((char*)ws + L.bpk);
+            TS_CUDA(launch_pack_b(dB, bpk, st), fn);
+        }
+        TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, cfg,
                                      (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                 fn);
     } else {
@@ -358,7 +398,7 @@ extern "C" ts_status ts_spgemm_numeric(ts_plan* plan, const ts_csr_desc* A, cons
                                        const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream) {
     const char* fn = "ts_spgemm_numeric";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
-    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
     ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
     const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
@@ -377,7 +417,7 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (plan->semiring != TS_SR_PLUS_TIMES_F32)
         return fail(TS_ERR_UNSUPPORTED, "%s: the boolean semiring has no gradient", fn);
-    const Layout L = plan_layout(plan->n, plan->d, plan->cur);
+    const Layout L = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
     ts_status s = check_operands(plan, A, B, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
     if (!C || !C->rowptr || (C->nnz > 0 && (!C->col || !dC)))
@@ -388,8 +428,13 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
         return fail(TS_ERR_STATE, "%s: no symbolic pass on this plan with these A, B and workspace", fn);
     if (plan->d > 8192) return fail(TS_ERR_UNSUPPORTED, "%s: backward supports d <= 8192", fn);
     const Sched sc = carve(ws, L);
+    int2* bpk = nullptr;
+    if (plan->cur.pack_b == 1 && B->nnz > 0) {
+        bpk = (int2*)((char*)ws + L.bpk);
+        TS_CUDA(launch_pack_b(dev(B), bpk, (cudaStream_t)stream), fn);
+    }
     TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
-                            dA, dB, sc, cfg_of(plan->cur), (cudaStream_t)stream),
+                            dA, dB, bpk, sc, cfg_of(plan->cur), (cudaStream_t)stream),
             fn);
     return ok();
 }
@@ -427,7 +472,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     const char* fn = "ts_plan_autotune";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (reps < 1) return fail(TS_ERR_INVALID_ARG, "%s: reps must be >= 1", fn);
-    const Layout L0 = plan_layout(plan->n, plan->d, plan->cur);
+    const Layout L0 = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
     ts_status s = check_operands(plan, A, B, ws, ws_bytes, L0, fn);
     if (s != TS_OK) return s;
     if (!same_operands(plan, A, B, ws))
@@ -438,16 +483,9 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     cudaStream_t st = (cudaStream_t)stream;
     const long long dpad = round_up(plan->d, 32);
 
-    // candidate grid; fields fixed by the plan's `force` are kept
-    std::vector<int> tiles;
-    for (int w : {64, 128, 256, 512, 1024, 2048, 4096})
-        if (w <= dpad && (w >= dpad / 16 || w >= 1024)) tiles.push_back(w);
-    if (tiles.empty() || tiles.back() < dpad) tiles.push_back((int)std::min<long long>(dpad, 4096));
-    std::vector<long long> thresholds = {1024, 4096, 16384, 65536};
-    std::vector<int> warps = {4, 8, 16};
-    std::vector<int> accs = {TS_ACC_DENSE};
-    if (plan->d > 256) accs.push_back(TS_ACC_HASH);
-
+    // coordinate descent from the heuristic default: each field in turn takes
+    // the value that times fastest with the others fixed; fields fixed by the
+    // plan's `force` are not varied
     cudaEvent_t e0, e1;
     TS_CUDA(cudaEventCreate(&e0), fn);
     TS_CUDA(cudaEventCreate(&e1), fn);
@@ -456,12 +494,12 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     float best_ms = 1e30f;
     auto try_one = [&](const ts_tuning& cand_in) -> ts_status {
         ts_tuning cand;
-        if (resolve_tuning(plan->d, cand_in, cand) != TS_OK) return TS_OK;  // skip invalid
-        const Layout L = plan_layout(plan->n, plan->d, cand);
+        if (resolve_tuning(plan->d, cand_in, cand, plan->n, B->nnz) != TS_OK) return TS_OK;  // skip
+        const Layout L = plan_layout(plan->n, plan->d, cand, A->nnz, B->nnz);
         if (L.total > ws_bytes) return TS_OK;  // does not fit the caller's workspace
         plan->cur = cand;
         float tot = 0.0f;
-        for (int r = 0; r <= reps; ++r) {  // first run warms up
+        for (int r = 0; r <= reps; ++r) {  // the first run warms up
             TS_CUDA(cudaEventRecord(e0, st), fn);
             ts_status q = run_numeric(plan, A, B, C, ws, L, st, fn);
             if (q != TS_OK) return q;
@@ -482,37 +520,45 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         }
         return TS_OK;
     };
-    ts_tuning base = plan->force;
-    for (int acc : accs) {
-        if (plan->force.accum && acc != plan->force.accum) continue;
-        for (long long th : thresholds) {
-            if (plan->force.cta_min_flops && th != plan->force.cta_min_flops) continue;
-            for (int w : warps) {
-                if (plan->force.warps_per_cta && w != plan->force.warps_per_cta) continue;
-                ts_tuning c = base;
-                c.accum = acc;
-                c.cta_min_flops = th;
-                c.warps_per_cta = w;
-                if (acc == TS_ACC_DENSE) {
-                    for (int t : tiles) {
-                        if (plan->force.col_tile && t != plan->force.col_tile) continue;
-                        c.col_tile = t;
-                        s = try_one(c);
-                        if (s != TS_OK) break;
-                    }
-                } else {
-                    for (int hs : {512, 1024, 2048}) {
-                        if (plan->force.hash_slots && hs != plan->force.hash_slots) continue;
-                        c.hash_slots = hs;
-                        s = try_one(c);
-                        if (s != TS_OK) break;
-                    }
-                }
-                if (s != TS_OK) break;
-            }
+    s = try_one(best);
+    std::vector<int> tiles;
+    for (int w : {64, 128, 256, 512, 1024, 2048, 4096})
+        if (w <= dpad && w >= std::max<long long>(64, round_up(dpad / 8, 32))) tiles.push_back(w);
+    if (tiles.empty() || tiles.back() < std::min<long long>(dpad, 4096))
+        tiles.push_back((int)std::min<long long>(dpad, 4096));
+    for (int field = 0; field < 6 && s == TS_OK; ++field) {
+        std::vector<ts_tuning> cands;
+        ts_tuning c = best;
+        switch (field) {
+            case 0:
+                if (plan->force.group) break;
+                for (int g : {1, 4, 8, 16, 32}) { c.group = g; cands.push_back(c); }
+                break;
+            case 1:
+                if (plan->force.pack_b || !vals) break;
+                for (int pk : {1, 2}) { c.pack_b = pk; cands.push_back(c); }
+                break;
+            case 2:
+                if (plan->force.accum || plan->d <= 256) break;
+                for (int acc : {TS_ACC_DENSE, TS_ACC_HASH}) { c.accum = acc; cands.push_back(c); }
+                break;
+            case 3:
+                if (plan->force.col_tile || best.accum != TS_ACC_DENSE) break;
+                for (int w : tiles) { c.col_tile = w; cands.push_back(c); }
+                break;
+            case 4:
+                if (plan->force.cta_min_flops) break;
+                for (long long th : {1024LL, 4096LL, 16384LL, 65536LL}) { c.cta_min_flops = th; cands.push_back(c); }
+                break;
+            case 5:
+                if (plan->force.warps_per_cta) break;
+                for (int w : {2, 4, 8}) { c.warps_per_cta = w; cands.push_back(c); }
+                break;
+        }
+        for (const ts_tuning& cand : cands) {
+            s = try_one(cand);
             if (s != TS_OK) break;
         }
-        if (s != TS_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -523,7 +569,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     plan->cur = best;
     if (chosen) *chosen = best;
     // leave C holding the product of the chosen tuning
-    const Layout Lb = plan_layout(plan->n, plan->d, best);
+    const Layout Lb = plan_layout(plan->n, plan->d, best, A->nnz, B->nnz);
     s = run_numeric(plan, A, B, C, ws, Lb, st, fn);
     if (s != TS_OK) return s;
     s = read_errors(ws, Lb, st, fn);
@@ -559,10 +605,10 @@ extern "C" ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, voi
 static const long long MSBFS_MAX_D = 65536;
 
 struct BfsLayout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, newbits = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, newbits = 0, total = 0;
 };
 
-static BfsLayout bfs_layout(long long n, long long d) {
+static BfsLayout bfs_layout(long long n, long long d, long long nnzA) {
     BfsLayout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -574,15 +620,18 @@ static BfsLayout bfs_layout(long long n, long long d) {
     L.flops = take(sizeof(long long) * (size_t)n);
     L.perm = take(sizeof(int) * (size_t)n);
     L.partial = take(sizeof(long long) * scan_partial_count(n));
+    // newbits before items: msbfs_emit finds it without knowing nnz(A)
     L.newbits = take(sizeof(unsigned) * (size_t)n * (size_t)((d + 31) / 32));
+    L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
     L.total = off;
     return L;
 }
 
-extern "C" ts_status msbfs_workspace_size(int64_t n, int64_t d, size_t* bytes) {
-    if (!bytes || n < 0 || d < 1) return fail(TS_ERR_INVALID_ARG, "msbfs_workspace_size: bad argument");
+extern "C" ts_status msbfs_workspace_size(int64_t n, int64_t nnz_A, int64_t d, size_t* bytes) {
+    if (!bytes || n < 0 || nnz_A < 0 || d < 1)
+        return fail(TS_ERR_INVALID_ARG, "msbfs_workspace_size: bad argument");
     if (d > MSBFS_MAX_D) return fail(TS_ERR_UNSUPPORTED, "msbfs: d above %lld", MSBFS_MAX_D);
-    *bytes = bfs_layout(n, d).total;
+    *bytes = bfs_layout(n, d, nnz_A).total;
     return ok();
 }
 
@@ -618,7 +667,7 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     if (d < 1 || d > MSBFS_MAX_D) return fail(TS_ERR_UNSUPPORTED, "%s: d must be in [1, %lld]", fn, MSBFS_MAX_D);
     if (F_next_capacity < 0 || (F_next_capacity > 0 && !F_next->col))
         return fail(TS_ERR_INVALID_ARG, "%s: bad F_next capacity", fn);
-    const BfsLayout L = bfs_layout(n, d);
+    const BfsLayout L = bfs_layout(n, d, A->nnz);
     if (!ws || ws_bytes < L.total)
         return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, L.total);
     if (((uintptr_t)ws) & 255) return fail(TS_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
@@ -629,6 +678,7 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     sc.flops = (long long*)(b + L.flops);
     sc.perm = (int*)(b + L.perm);
     sc.partial = (long long*)(b + L.partial);
+    sc.items = (long long*)(b + L.items);
     unsigned* newbits = (unsigned*)(b + L.newbits);
     ts_tuning t{};
     resolve_tuning(d, ts_tuning{}, t);
@@ -659,8 +709,9 @@ extern "C" ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capaci
         return fail(TS_ERR_INVALID_ARG, "%s: bad F_next", fn);
     const long long n = F_next->nrows, d = F_next->ncols;
     if (n < 0 || d < 1 || d > MSBFS_MAX_D) return fail(TS_ERR_INVALID_ARG, "%s: bad shape", fn);
-    const BfsLayout L = bfs_layout(n, d);
-    if (!ws || ws_bytes < L.total) return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s", fn);
+    const BfsLayout L = bfs_layout(n, d, 0);
+    if (!ws || ws_bytes < L.newbits + sizeof(unsigned) * (size_t)n * (size_t)((d + 31) / 32))
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s", fn);
     cudaStream_t st = (cudaStream_t)stream;
     long long tot = 0;
     TS_CUDA(cudaMemcpyAsync(&tot, (long long*)F_next->rowptr + n, sizeof tot, cudaMemcpyDeviceToHost, st), fn);

@@ -20,6 +20,7 @@ struct BwdParams {
     const long long* Bp;
     const int* Bi;
     const float* Bx;
+    const int2* Bpk;
     long long nnzB;
     int nB;
     int d;
@@ -48,63 +49,76 @@ __device__ __forceinline__ float seg_sum_down(float v, int key) {
     return v;
 }
 
-struct BwdVisit {
-    const int* __restrict__ Bi;
-    const float* __restrict__ Bx;
+template <class BA>
+struct BwdOp {
+    BA ba;
     const float* g;
-    float* sdA;  // 32 partial dot products of this warp's chunk
+    float* sdA;  // flattened mode: 32 partial dot products of this warp's chunk
+    float* dA;   // grouped mode: written directly
     float* dB;
     bool want_dA;
     int d;
     unsigned long long* err;
-    __device__ __forceinline__ void one(long long j, float a, int q, bool ok) {
-        float contrib = 0.0f;
-        if (ok) {
-            const int c = __ldg(Bi + j);
-            if ((unsigned)c < (unsigned)d) {
-                const float gj = g[c];
-                contrib = __ldg(Bx + j) * gj;
-                if (dB) atomicAdd(dB + j, a * gj);
-            } else {
-                atomicOr(err, ERR_B_COL);
-            }
+    float part[2];  // grouped mode: this lane's share of the two entries in flight
+    struct Item {
+        int c;
+        float b;
+    };
+    __device__ __forceinline__ Item fetch(long long j) const {
+        Item it;
+        ba.get(j, it.c, it.b);
+        return it;
+    }
+    // dB(k,j) += A(i,k) * dC(i,j); returns B(k,j) * dC(i,j) for dA(i,k)
+    __device__ __forceinline__ float term(const Item& it, float a, long long j) {
+        if ((unsigned)it.c < (unsigned)d) {
+            const float gj = g[it.c];
+            if (dB) atomicAdd(dB + j, a * gj);
+            return it.b * gj;
         }
-        if (want_dA) {
-            const float s = seg_sum_down(contrib, q);
-            const int prevq = __shfl_up_sync(FULL, q, 1);
-            if (ok && (lane_id() == 0 || prevq != q)) atomicAdd(sdA + q, s);
+        atomicOr(err, ERR_B_COL);
+        return 0.0f;
+    }
+    __device__ __forceinline__ void apply(const Item& it, float a, long long j, int slot) {
+        part[slot] += term(it, a, j);
+    }
+    template <int G>
+    __device__ __forceinline__ void done(int q0, int q1, int nvalid, long long e0) {
+        float t0 = part[0], t1 = part[1];
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) {
+            t0 += __shfl_xor_sync(FULL, t0, o);
+            t1 += __shfl_xor_sync(FULL, t1, o);
         }
+        if (want_dA && (lane_id() % G) == 0) {
+            if (q0 < nvalid) dA[e0 + q0] = t0;
+            if (q1 < nvalid) dA[e0 + q1] = t1;
+        }
+        part[0] = part[1] = 0.0f;
+    }
+    // flattened mode (expand_chunk): segmented lane reduction into sdA
+    __device__ __forceinline__ void reduce_into(float contrib, int q, bool ok) {
+        if (!want_dA) return;
+        const float s = seg_sum_down(contrib, q);
+        const int prevq = __shfl_up_sync(FULL, q, 1);
+        if (ok && (lane_id() == 0 || prevq != q)) atomicAdd(sdA + q, s);
     }
     __device__ __forceinline__ void step4(const long long* j, const float* a, const int* q) {
-        int c[4];
-        float b[4];
+        Item it[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            c[u] = __ldg(Bi + j[u]);
-            b[u] = __ldg(Bx + j[u]);
-        }
+        for (int u = 0; u < 4; ++u) it[u] = fetch(j[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float contrib = 0.0f;
-            if ((unsigned)c[u] < (unsigned)d) {
-                const float gj = g[c[u]];
-                contrib = b[u] * gj;
-                if (dB) atomicAdd(dB + j[u], a[u] * gj);
-            } else {
-                atomicOr(err, ERR_B_COL);
-            }
-            if (want_dA) {
-                const float s = seg_sum_down(contrib, q[u]);
-                const int prevq = __shfl_up_sync(FULL, q[u], 1);
-                if (lane_id() == 0 || prevq != q[u]) atomicAdd(sdA + q[u], s);
-            }
-        }
+        for (int u = 0; u < 4; ++u) reduce_into(term(it[u], a[u], j[u]), q[u], true);
     }
-    __device__ __forceinline__ void step1(long long j, float a, int q, bool ok) { one(j, a, q, ok); }
+    __device__ __forceinline__ void step1(long long j, float a, int q, bool ok) {
+        float c = 0.0f;
+        if (ok) c = term(fetch(j), a, j);
+        reduce_into(c, q, ok);
+    }
 };
 
-template <bool CTA>
-__device__ __forceinline__ void backward_row(const BwdParams& p, int row, float* g, float* sdA) {
+template <int G, class BA, bool CTA>
+__device__ __forceinline__ void backward_row(const BwdParams& p, const BA& ba, int row, float* g, float* sdA) {
     unsigned long long* err = &p.hdr->err;
     const int lane = lane_id();
     const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
@@ -124,15 +138,19 @@ __device__ __forceinline__ void backward_row(const BwdParams& p, int row, float*
     const long long first = CTA ? a0 + 32LL * warp_id() : a0;
     const long long stride = CTA ? 32LL * nw : 32LL;
     const SegWhole seg{p.Bp, p.nnzB, p.d};
-    BwdVisit vis{p.Bi, p.Bx, g, sdA, p.dB, p.dA != nullptr, p.d, err};
+    BwdOp<BA> op{ba, g, sdA, p.dA, p.dB, p.dA != nullptr, p.d, err, {0.0f, 0.0f}};
     for (long long e0 = first; e0 < a1; e0 += stride) {
         const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
-        expand_chunk(e0, nv, p.Ai, p.Ax, p.nB, seg, vis, err);
-        __syncwarp();
-        if (p.dA) {
-            if (lane < nv) p.dA[e0 + lane] = sdA[lane];
-            sdA[lane] = 0.0f;
+        if constexpr (G == 1) {
+            expand_chunk(e0, nv, p.Ai, p.Ax, p.nB, seg, op, err);
             __syncwarp();
+            if (p.dA) {
+                if (lane < nv) p.dA[e0 + lane] = sdA[lane];
+                sdA[lane] = 0.0f;
+                __syncwarp();
+            }
+        } else {
+            grouped_chunk<G>(e0, nv, p.Ai, p.Ax, p.nB, seg, op, err);
         }
     }
     if (CTA) __syncthreads();
@@ -145,7 +163,8 @@ __device__ __forceinline__ void backward_row(const BwdParams& p, int row, float*
     else __syncwarp();
 }
 
-__global__ void __launch_bounds__(1024) k_backward(BwdParams p) {
+template <int G, bool PACKED>
+__global__ void __launch_bounds__(256, 6) k_backward(BwdParams p) {
     extern __shared__ __align__(16) float fsm[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
@@ -163,18 +182,22 @@ __global__ void __launch_bounds__(1024) k_backward(BwdParams p) {
     __syncthreads();
     const long long nheavy = s_nheavy, nrows = s_nrows;
     float* sdA = fsm + (size_t)nw * p.dpad + 32 * warp;
+    using BA = typename std::conditional<PACKED, BPacked, BSep>::type;
+    BA ba;
+    if constexpr (PACKED) ba = BPacked{p.Bpk};
+    else ba = BSep{p.Bi, p.Bx};
     for (;;) {
         if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
         __syncthreads();
         const long long h = s_item;
         __syncthreads();
         if (h >= nheavy) break;
-        backward_row<true>(p, p.perm[h], fsm, sdA);
+        backward_row<G, BA, true>(p, ba, p.perm[h], fsm, sdA);
     }
     float* g = fsm + (size_t)warp * p.dpad;
     for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
          idx += (long long)gridDim.x * nw)
-        backward_row<false>(p, p.perm[idx], g, sdA);
+        backward_row<G, BA, false>(p, ba, p.perm[idx], g, sdA);
 }
 
 size_t backward_smem(long long d, int warps) {
@@ -182,9 +205,14 @@ size_t backward_smem(long long d, int warps) {
     return sizeof(float) * (size_t)warps * (size_t)(dpad + 32);
 }
 
+template <int G, bool PACKED>
+static const void* bwd_kernel() {
+    return (const void*)k_backward<G, PACKED>;
+}
+
 cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const long long* Cp,
                             const int* Ci, long long nnzC, const float* dC, float* dA, float* dB,
-                            const Sched& s, const LaunchCfg& cfg, cudaStream_t st) {
+                            const int2* Bpk, const Sched& s, const LaunchCfg& cfg, cudaStream_t st) {
     cudaError_t e;
     if (d > MAX_BWD_D) return cudaErrorInvalidValue;
     if (dA && A.nnz && (e = cudaMemsetAsync(dA, 0, sizeof(float) * A.nnz, st))) return e;
@@ -199,6 +227,7 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     p.Bp = B.rowptr;
     p.Bi = B.col;
     p.Bx = B.val;
+    p.Bpk = Bpk;
     p.nnzB = B.nnz;
     p.nB = (int)B.nrows;
     p.d = (int)d;
@@ -213,19 +242,29 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
     int warps = cfg.warps_per_cta;
+    if (warps > 8) return cudaErrorInvalidValue;
     size_t smem = backward_smem(d, warps);
     while (smem > 200 * 1024 && warps > 1) {
         warps /= 2;
         smem = backward_smem(d, warps);
     }
+    const void* k;
+    const bool pk = Bpk != nullptr;
+    switch (cfg.group) {
+        case 1: k = pk ? bwd_kernel<1, true>() : bwd_kernel<1, false>(); break;
+        case 4: k = pk ? bwd_kernel<4, true>() : bwd_kernel<4, false>(); break;
+        case 8: k = pk ? bwd_kernel<8, true>() : bwd_kernel<8, false>(); break;
+        case 16: k = pk ? bwd_kernel<16, true>() : bwd_kernel<16, false>(); break;
+        case 32: k = pk ? bwd_kernel<32, true>() : bwd_kernel<32, false>(); break;
+        default: return cudaErrorInvalidValue;
+    }
     if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute((const void*)k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)))
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
-    const int grid = persistent_grid((const void*)k_backward, 32 * warps, smem, cfg.sms);
+    const int grid = persistent_grid(k, 32 * warps, smem, cfg.sms);
+    void* args[] = {&p};
     count_launch();
-    k_backward<<<grid, 32 * warps, smem, st>>>(p);
-    return cudaGetLastError();
+    return cudaLaunchKernel(k, dim3(grid), dim3(32 * warps), args, smem, st);
 }
 
 }  // namespace ts

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "layout.h"
@@ -159,6 +160,86 @@ __device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int
         const float av = __shfl_sync(FULL, a, q);
         visit.step1(j, av, q, p < total);
     }
+}
+
+// B's entries either as the caller's two arrays or as (column, value bits)
+// pairs packed into 8 bytes (one load per product).
+struct BSep {
+    const int* __restrict__ Bi;
+    const float* __restrict__ Bx;
+    __device__ __forceinline__ int col(long long j) const { return __ldg(Bi + j); }
+    __device__ __forceinline__ void get(long long j, int& c, float& b) const {
+        c = __ldg(Bi + j);
+        b = Bx ? __ldg(Bx + j) : 0.0f;
+    }
+};
+
+struct BPacked {
+    const int2* __restrict__ P;
+    __device__ __forceinline__ int col(long long j) const { return __ldg(&P[j].x); }
+    __device__ __forceinline__ void get(long long j, int& c, float& b) const {
+        const int2 v = __ldg(P + j);
+        c = v.x;
+        b = __int_as_float(v.y);
+    }
+};
+
+// Group distribution of the products of one chunk of up to 32 A entries:
+// lanes form 32/G groups of G lanes; a group takes one A entry q and walks
+// its segment of B with stride G.  Two entries per group are in flight per
+// pass (slots 0 and 1) so that each lane has two independent gathers
+// outstanding.  `op` provides fetch(j) -> Item, apply(item, a_q, j, slot) and
+// done<G>(q0, q1, nvalid, e0), called once per pass with all 32 lanes
+// converged after both entries' segments are complete.
+template <int G, class Seg, class Op>
+__device__ __forceinline__ void grouped_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
+                                              const float* __restrict__ Ax, int nB, const Seg& seg,
+                                              Op& op, unsigned long long* err) {
+    static_assert(G >= 2 && G <= 32 && (32 % G) == 0, "group size");
+    constexpr int NG = 32 / G;
+    const int lane = lane_id();
+    long long start = 0;
+    int len = 0;
+    float a = 1.0f;
+    if (lane < nvalid) {
+        const int k = __ldg(Ai + e0 + lane);
+        if ((unsigned)k < (unsigned)nB) {
+            seg(k, start, len);
+            if (Ax) a = __ldg(Ax + e0 + lane);
+        } else {
+            atomicOr(err, ERR_A_COL);
+        }
+    }
+    const int gi = lane / G, gl = lane % G;
+    for (int t = 0; t < nvalid; t += 2 * NG) {
+        const int q0 = t + gi, q1 = t + NG + gi;  // both <= 31 because 2*NG divides 32
+        const long long s0 = shfl64(start, q0), s1 = shfl64(start, q1);
+        const int l0 = __shfl_sync(FULL, len, q0), l1 = __shfl_sync(FULL, len, q1);
+        const float a0 = __shfl_sync(FULL, a, q0), a1 = __shfl_sync(FULL, a, q1);
+        const int lm = l0 > l1 ? l0 : l1;
+        for (int r = gl; r < lm; r += G) {
+            const bool v0 = r < l0, v1 = r < l1;
+            typename Op::Item i0, i1;
+            if (v0) i0 = op.fetch(s0 + r);
+            if (v1) i1 = op.fetch(s1 + r);
+            if (v0) op.apply(i0, a0, s0 + r, 0);
+            if (v1) op.apply(i1, a1, s1 + r, 1);
+        }
+        op.template done<G>(q0, q1, nvalid, e0);
+    }
+}
+
+// Rows with products: all classes >= 1; heavy: classes >= cta_class.
+__device__ __forceinline__ void sched_counts(const WsHeader* hdr, int cta_class, long long& nheavy,
+                                             long long& nrows) {
+    long long nh = 0, nr = 0;
+    for (int c = 1; c < NUM_CLASSES; ++c) {
+        const long long h = hdr->hist[c];
+        nr += h;
+        if (c >= cta_class) nh += h;
+    }
+    nheavy = nh;
+    nrows = nr;
 }
 
 // Exclusive-scan helper for per-word counts held in shared memory by one warp.

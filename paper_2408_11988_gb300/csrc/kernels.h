@@ -24,12 +24,17 @@ struct Sched {
     long long* flops = nullptr;  // products per row of A, int64[n]
     int* perm = nullptr;         // non-empty rows, heaviest class first, int32[n]
     long long* partial = nullptr;// scan partial sums
+    long long* items = nullptr;  // (row, chunk) work items of long rows for the flops pass
 };
+
+// Capacity (entries) of Sched::items for a matrix with n rows and nnzA entries.
+long long flops_item_capacity(long long n, long long nnzA);
 
 struct LaunchCfg {
     int warps_per_cta = 8;
     int cta_class = 14;      // rows of flops class >= this run CTA-per-row
     int sms = 152;
+    int group = 1;           // lanes per A entry (1 = flattened products)
 };
 
 // Bytes of the scan partials for n values.
@@ -56,10 +61,14 @@ cudaError_t launch_scan_inplace(long long* x, long long n, long long* partial, c
 cudaError_t launch_tile_split(const DevCsr& B, int W, int T, long long* tp, cudaStream_t st);
 
 // Numeric pass with a dense accumulator of width W over T column tiles.
+// Bpk: packed (column, value) copy of B or nullptr; G: lanes per A entry
+// (1 = flattened products).
 cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
-                                 const long long* tp, bool values, const Sched& s,
-                                 const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx,
-                                 long long nnzC, cudaStream_t st);
+                                 const long long* tp, bool values, const int2* Bpk, int G,
+                                 const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,
+                                 float* Cx, long long nnzC, cudaStream_t st);
+// Packed (column, value bits) copy of B's entries.
+cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st);
 
 // Numeric pass with a per-warp hash accumulator of `slots` entries.
 cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, int slots,
@@ -72,7 +81,7 @@ size_t numeric_hash_smem(int slots, int warps, bool values);
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).
 cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const long long* Cp,
                             const int* Ci, long long nnzC, const float* dC, float* dA, float* dB,
-                            const Sched& s, const LaunchCfg& cfg, cudaStream_t st);
+                            const int2* Bpk, const Sched& s, const LaunchCfg& cfg, cudaStream_t st);
 size_t backward_smem(long long d, int warps);
 
 // Multi-source BFS (Alg. 3) levels.

@@ -1,0 +1,333 @@
+// Numeric pass with a dense accumulator (the paper's SPA, Sec. III-C) of
+// width W in shared memory plus one occupancy byte per column.  Row i of C
+// (Eq. 1) is produced tile by tile (W columns of B each); inside a tile the
+// occupied columns are read out in ascending order, four per lane, which
+// also restores the accumulator to zero for the next row.
+//
+// Products are spread over the lanes in one of two ways (template G):
+//   G = 1      flattened: the products of 32 A entries are numbered and lane l
+//              takes numbers l, l+32, ... (any mix of B row lengths);
+//   G = 4..32  grouped: a group of G lanes takes one A entry and walks its B
+//              row with stride G (no per-product owner search; best when B's
+//              rows have nearly equal lengths close to G).
+// B is read from its two arrays or from a packed (column, value) copy.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ts {
+
+constexpr int MAX_DENSE_W = 4096;
+
+struct NumParams {
+    const long long* Ap;
+    const int* Ai;
+    const float* Ax;
+    long long nnzA;
+    const long long* Bp;
+    const int* Bi;
+    const float* Bx;
+    const int2* Bpk;
+    long long nnzB;
+    int nB;
+    int d;
+    int W;
+    int T;
+    const long long* tp;
+    const int* perm;
+    WsHeader* hdr;
+    int cta_class;
+    const long long* Cp;
+    int* Ci;
+    float* Cx;
+    long long nnzC;
+};
+
+template <bool VALUES, class BA>
+struct DenseOp {
+    BA ba;
+    float* acc;
+    unsigned char* flg;
+    int d;
+    int c0;
+    int W;
+    unsigned long long* err;
+    struct Item {
+        int c;
+        float b;
+    };
+    __device__ __forceinline__ Item fetch(long long j) const {
+        Item it;
+        if (VALUES) ba.get(j, it.c, it.b);
+        else {
+            it.c = ba.col(j);
+            it.b = 0.0f;
+        }
+        return it;
+    }
+    __device__ __forceinline__ void add(int c, float v) {
+        const int lc = c - c0;
+        if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
+            flg[lc] = 1;
+            if (VALUES) atomicAdd(acc + lc, v);
+        } else {
+            atomicOr(err, ERR_B_COL);
+        }
+    }
+    __device__ __forceinline__ void apply(const Item& it, float a, long long, int) { add(it.c, a * it.b); }
+    template <int G>
+    __device__ __forceinline__ void done(int, int, int, long long) {}
+    // flattened-mode interface (expand_chunk)
+    __device__ __forceinline__ void step4(const long long* j, const float* a, const int*) {
+        Item it[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) it[u] = fetch(j[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add(it[u].c, a[u] * it[u].b);
+    }
+    __device__ __forceinline__ void step1(long long j, float a, int, bool ok) {
+        if (ok) {
+            const Item it = fetch(j);
+            add(it.c, a * it.b);
+        }
+    }
+};
+
+// Warp read-out: lane l looks at columns 4l..4l+3 of each 128-column block.
+template <bool VALUES>
+__device__ __forceinline__ void warp_emit4(float* acc, unsigned char* flg, int W, int c0, long long& out,
+                                           long long out_end, int* Ci, float* Cx,
+                                           unsigned long long* err) {
+    const int lane = lane_id();
+    for (int base = 0; base < W; base += 128) {
+        const int cb = base + 4 * lane;
+        unsigned f = 0;
+        if (cb < W) f = *reinterpret_cast<const unsigned*>(flg + cb) & 0x01010101u;
+        const int cnt = __popc(f);
+        const int incl = warp_incl_scan(cnt);
+        long long pos = out + incl - cnt;
+        out += __shfl_sync(FULL, incl, 31);
+        if (f) {
+            *reinterpret_cast<unsigned*>(flg + cb) = 0u;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (VALUES) {
+                v = *reinterpret_cast<const float4*>(acc + cb);
+                *reinterpret_cast<float4*>(acc + cb) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (f & (1u << (8 * u))) {
+                    if (pos < out_end) {
+                        Ci[pos] = c0 + cb + u;
+                        if (VALUES) Cx[pos] = vv[u];
+                    } else {
+                        atomicOr(err, ERR_C_ROW);
+                    }
+                    ++pos;
+                }
+            }
+        }
+    }
+}
+
+// Block-wide read-out for a heavy row; wcnt has W/32 + 1 entries.
+template <bool VALUES>
+__device__ __forceinline__ void cta_emit(float* acc, unsigned char* flg, int W, int c0, long long& out,
+                                         long long out_end, int* Ci, float* Cx, int* wcnt,
+                                         unsigned long long* err) {
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    const int words = W >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int w = warp; w < words; w += nw) {
+        const unsigned bal = __ballot_sync(FULL, flg[w * 32 + lane] != 0);
+        if (lane == 0) wcnt[w] = __popc(bal);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int tot = warp_excl_scan_smem(wcnt, words);
+        if (lane == 0) wcnt[words] = tot;
+    }
+    __syncthreads();
+    for (int w = warp; w < words; w += nw) {
+        const int c = w * 32 + lane;
+        const bool f = flg[c] != 0;
+        const unsigned bal = __ballot_sync(FULL, f);
+        if (f) {
+            const long long pos = out + wcnt[w] + __popc(bal & lt);
+            if (pos < out_end) {
+                Ci[pos] = c0 + c;
+                if (VALUES) Cx[pos] = acc[c];
+            } else {
+                atomicOr(err, ERR_C_ROW);
+            }
+            flg[c] = 0;
+            if (VALUES) acc[c] = 0.0f;
+        }
+    }
+    out += wcnt[words];
+    __syncthreads();
+}
+
+template <bool VALUES, int G, class BA, bool CTA, class Seg>
+__device__ __forceinline__ void numeric_tile(const NumParams& p, const BA& ba, const Seg& seg, long long a0,
+                                             long long a1, DenseOp<VALUES, BA>& op) {
+    unsigned long long* err = &p.hdr->err;
+    const int nw = blockDim.x >> 5;
+    const long long first = CTA ? a0 + 32LL * warp_id() : a0;
+    const long long stride = CTA ? 32LL * nw : 32LL;
+    const float* Ax = VALUES ? p.Ax : nullptr;
+    for (long long e0 = first; e0 < a1; e0 += stride) {
+        const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
+        if constexpr (G == 1) expand_chunk(e0, nv, p.Ai, Ax, p.nB, seg, op, err);
+        else grouped_chunk<G>(e0, nv, p.Ai, Ax, p.nB, seg, op, err);
+    }
+}
+
+template <bool VALUES, int G, class BA, bool CTA>
+__device__ __forceinline__ void numeric_row(const NumParams& p, const BA& ba, int row, float* acc,
+                                            unsigned char* flg, int* wcnt) {
+    unsigned long long* err = &p.hdr->err;
+    const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+    const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+    long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+    const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+    for (int t = 0; t < p.T; ++t) {
+        DenseOp<VALUES, BA> op{ba, acc, flg, p.d, t * p.W, p.W, err};
+        if (p.T == 1) numeric_tile<VALUES, G, BA, CTA>(p, ba, SegWhole{p.Bp, p.nnzB, p.d}, a0, a1, op);
+        else numeric_tile<VALUES, G, BA, CTA>(p, ba, SegTile{p.tp, p.T + 1, t, p.W}, a0, a1, op);
+        if (CTA) {
+            __syncthreads();
+            cta_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, wcnt, err);
+        } else {
+            __syncwarp();
+            warp_emit4<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, err);
+            __syncwarp();
+        }
+    }
+    if (out != out_end && (CTA ? threadIdx.x == 0 : lane_id() == 0)) atomicOr(err, ERR_C_ROW);
+}
+
+template <bool VALUES, int G, bool PACKED>
+__global__ void __launch_bounds__(256, 6) k_numeric(NumParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
+    __shared__ long long s_item, s_nheavy, s_nrows;
+    const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
+    const int slot = VALUES ? 5 * p.W : p.W;  // bytes per warp: W floats + W flags
+    for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    const long long nheavy = s_nheavy, nrows = s_nrows;
+    using BA = typename std::conditional<PACKED, BPacked, BSep>::type;
+    BA ba;
+    if constexpr (PACKED) ba = BPacked{p.Bpk};
+    else ba = BSep{p.Bi, VALUES ? p.Bx : nullptr};
+    {
+        float* acc = reinterpret_cast<float*>(smem);
+        unsigned char* flg = smem + (VALUES ? 4 * p.W : 0);
+        for (;;) {
+            if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
+            __syncthreads();
+            const long long h = s_item;
+            __syncthreads();
+            if (h >= nheavy) break;
+            numeric_row<VALUES, G, BA, true>(p, ba, p.perm[h], acc, flg, s_wcnt);
+        }
+    }
+    float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
+    unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
+    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
+         idx += (long long)gridDim.x * nw)
+        numeric_row<VALUES, G, BA, false>(p, ba, p.perm[idx], acc, flg, nullptr);
+}
+
+__global__ void k_pack_b(long long nnz, const int* __restrict__ Bi, const float* __restrict__ Bx,
+                         int2* __restrict__ P) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+         j += (long long)gridDim.x * blockDim.x)
+        P[j] = make_int2(__ldg(Bi + j), __float_as_int(__ldg(Bx + j)));
+}
+
+cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st) {
+    if (B.nnz == 0) return cudaSuccess;
+    long long blocks = (B.nnz + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    count_launch();
+    k_pack_b<<<(unsigned)blocks, 256, 0, st>>>(B.nnz, B.col, B.val, P);
+    return cudaGetLastError();
+}
+
+size_t numeric_dense_smem(int W, int warps, bool values) {
+    return (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
+}
+
+template <bool VALUES, int G, bool PACKED>
+static cudaError_t launch_one(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    const void* k = (const void*)k_numeric<VALUES, G, PACKED>;
+    const size_t smem = numeric_dense_smem(p.W, warps, VALUES);
+    cudaError_t e;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid(k, 32 * warps, smem, sms);
+    count_launch();
+    k_numeric<VALUES, G, PACKED><<<grid, 32 * warps, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <bool VALUES, bool PACKED>
+static cudaError_t launch_g(const NumParams& p, int G, int warps, int sms, cudaStream_t st) {
+    switch (G) {
+        case 1: return launch_one<VALUES, 1, PACKED>(p, warps, sms, st);
+        case 4: return launch_one<VALUES, 4, PACKED>(p, warps, sms, st);
+        case 8: return launch_one<VALUES, 8, PACKED>(p, warps, sms, st);
+        case 16: return launch_one<VALUES, 16, PACKED>(p, warps, sms, st);
+        case 32: return launch_one<VALUES, 32, PACKED>(p, warps, sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                 const long long* tp, bool values, const int2* Bpk, int G,
+                                 const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,
+                                 float* Cx, long long nnzC, cudaStream_t st) {
+    cudaError_t e;
+    if (A.nrows == 0) return cudaSuccess;
+    if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
+    if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
+    NumParams p;
+    p.Ap = A.rowptr;
+    p.Ai = A.col;
+    p.Ax = A.val;
+    p.nnzA = A.nnz;
+    p.Bp = B.rowptr;
+    p.Bi = B.col;
+    p.Bx = B.val;
+    p.Bpk = Bpk;
+    p.nnzB = B.nnz;
+    p.nB = (int)B.nrows;
+    p.d = (int)d;
+    p.W = W;
+    p.T = T;
+    p.tp = tp;
+    p.perm = s.perm;
+    p.hdr = s.hdr;
+    p.cta_class = cfg.cta_class;
+    p.Cp = Cp;
+    p.Ci = Ci;
+    p.Cx = Cx;
+    p.nnzC = nnzC;
+    if (values) {
+        if (Bpk) return launch_g<true, true>(p, G, cfg.warps_per_cta, cfg.sms, st);
+        return launch_g<true, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
+    }
+    return launch_g<false, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
+}
+
+}  // namespace ts

@@ -11,82 +11,108 @@ namespace ts {
 
 // ---------------------------------------------------------------------------
 // Row flops: flops_i = sum over stored (i,k) of nnz(B_k) (paper Sec. II-A:
-// flops = number of multiplications).  Entry parallel: every warp takes a
-// fixed slice of A's entries, so rows with very many entries are spread over
-// many warps.  Partial row sums are added with atomics into a zeroed array.
+// flops = number of multiplications).  Rows of at most SHORT_ROW entries are
+// summed by one thread each.  Longer rows are cut into chunks of LONG_CHUNK
+// entries, queued as (row, chunk) items, and each chunk is summed by one
+// warp and added to its row with an atomic, so a row with very many entries
+// is spread over many warps.
 // ---------------------------------------------------------------------------
-constexpr int FLOPS_CHUNK = 256;  // entries of A per warp
+constexpr int SHORT_ROW = 32;
+constexpr int LONG_CHUNK = 256;
 
-__global__ void __launch_bounds__(256) k_flops_entries(long long n, const long long* __restrict__ Ap,
-                                                       const int* __restrict__ Ai, long long nnzA,
-                                                       SegWhole segB, int nB,
-                                                       long long* __restrict__ flops,
-                                                       WsHeader* hdr) {
-    __shared__ unsigned long long s_sum[8][32];
-    const int warp = warp_id(), lane = lane_id();
-    const long long E0 = ((long long)blockIdx.x * 8 + warp) * FLOPS_CHUNK;
-    if (E0 >= nnzA || n <= 0) return;
-    const long long E1 = E0 + FLOPS_CHUNK < nnzA ? E0 + FLOPS_CHUNK : nnzA;
-
-    // r = the row holding entry E0: the largest r in [0, n) with Ap[r] <= E0,
-    // found by a 32-way search (the answer stays in [lo, hi)).
-    auto find_row = [&](long long lo, long long hi, long long e) {
-        while (hi - lo > 1) {
-            const long long step = (hi - lo + 31) / 32;
-            const long long cand = lo + (long long)lane * step;
-            const bool le = cand < hi && __ldg(Ap + cand) <= e;
-            const unsigned m = __ballot_sync(FULL, le) | 1u;
-            const int q = 31 - __clz(m);
-            lo = lo + (long long)q * step;
-            const long long nh = lo + step;
-            hi = nh < hi ? nh : hi;
-        }
-        return lo;
-    };
-    long long r = find_row(0, n, E0);
-    long long e = E0;
+__global__ void __launch_bounds__(256) k_flops_rows(long long n, const long long* __restrict__ Ap,
+                                                    const int* __restrict__ Ai, long long nnzA,
+                                                    SegWhole segB, int nB, long long* __restrict__ flops,
+                                                    long long* __restrict__ items, long long item_cap,
+                                                    WsHeader* hdr) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long* err = &hdr->err;
-    // every pass either consumes an entry or re-locates r once, so a well
-    // formed A needs at most 2*FLOPS_CHUNK passes; the guard only ends the
-    // loop on a row pointer array that is not monotone
-    for (int guard = 0; e < E1; ++guard) {
-        if (guard > 4 * FLOPS_CHUNK) {
-            if (lane == 0) atomicOr(err, ERR_A_COL);
-            break;
-        }
-        // skip a window of rows that ends before e (only with long empty runs)
-        const long long nxt = (r + 32 <= n) ? __ldg(Ap + r + 32) : LLONG_MAX;
-        if (nxt <= e) {
-            r = find_row(r, n, e);
-            continue;
-        }
-        const long long rr = r + lane;
-        const long long st = rr < n ? __ldg(Ap + rr) : LLONG_MAX;
-        s_sum[warp][lane] = 0;
-        __syncwarp();
-        const long long stop = nxt < E1 ? nxt : E1;
-        for (long long base = e; base < stop; base += 32) {
-            const long long ee = base + lane;
-            const int q = owner_lane64(st, ee);
-            if (ee < stop) {
-                const int k = __ldg(Ai + ee);
+    long long nchunks = 0;
+    long long a0 = 0, a1 = 0;
+    if (i < n) {
+        a0 = clampll(__ldg(Ap + i), 0, nnzA);
+        a1 = clampll(__ldg(Ap + i + 1), a0, nnzA);
+        if (a1 - a0 <= SHORT_ROW) {
+            long long f = 0;
+#pragma unroll 4
+            for (long long e = a0; e < a1; ++e) {
+                const int k = __ldg(Ai + e);
                 if ((unsigned)k < (unsigned)nB) {
                     long long s0;
                     int len;
                     segB(k, s0, len);
-                    if (len) atomicAdd(&s_sum[warp][q], (unsigned long long)len);
+                    f += len;
+                } else {
+                    atomicOr(err, ERR_A_COL);
+                }
+            }
+            flops[i] = f;
+        } else {
+            flops[i] = 0;
+            nchunks = (a1 - a0 + LONG_CHUNK - 1) / LONG_CHUNK;
+        }
+    }
+    // reserve item slots: one atomic per warp
+    const int lane = lane_id();
+    long long incl = warp_incl_scan(nchunks);
+    const long long tot = __shfl_sync(FULL, incl, 31);
+    long long base = 0;
+    if (tot > 0) {
+        if (lane == 31) base = (long long)atomicAdd((unsigned long long*)&hdr->scratch[0], (unsigned long long)tot);
+        base = __shfl_sync(FULL, base, 31);
+    }
+    for (long long c = 0; c < nchunks; ++c) {
+        const long long slot = base + incl - nchunks + c;
+        if (slot < item_cap) items[slot] = (i << 24) | c;
+        else atomicOr(err, ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_flops_chunks(const long long* __restrict__ Ap,
+                                                      const int* __restrict__ Ai, long long nnzA,
+                                                      SegWhole segB, int nB, long long* flops,
+                                                      const long long* __restrict__ items,
+                                                      long long item_cap, WsHeader* hdr) {
+    const long long nitems_raw = *(volatile long long*)&hdr->scratch[0];
+    const long long nitems = nitems_raw < item_cap ? nitems_raw : item_cap;
+    const int lane = lane_id();
+    unsigned long long* err = &hdr->err;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long it = gw; it < nitems; it += nwarps) {
+        const long long item = items[it];
+        const long long row = item >> 24, c = item & 0xFFFFFF;
+        const long long a0 = clampll(__ldg(Ap + row), 0, nnzA);
+        const long long a1 = clampll(__ldg(Ap + row + 1), a0, nnzA);
+        const long long e0 = a0 + c * LONG_CHUNK;
+        const long long e1 = e0 + LONG_CHUNK < a1 ? e0 + LONG_CHUNK : a1;
+        long long f = 0;
+#pragma unroll
+        for (int u = 0; u < LONG_CHUNK / 32; ++u) {
+            const long long e = e0 + u * 32 + lane;
+            if (e < e1) {
+                const int k = __ldg(Ai + e);
+                if ((unsigned)k < (unsigned)nB) {
+                    long long s0;
+                    int len;
+                    segB(k, s0, len);
+                    f += len;
                 } else {
                     atomicOr(err, ERR_A_COL);
                 }
             }
         }
-        __syncwarp();
-        const unsigned long long v = s_sum[warp][lane];
-        if (v && rr < n) atomicAdd((unsigned long long*)(flops + rr), v);
-        __syncwarp();
-        e = stop;
-        r += 32;
+        f = warp_sum(f);
+        if (lane == 0 && f) atomicAdd((unsigned long long*)(flops + row), (unsigned long long)f);
     }
+}
+
+// Room for the (row, chunk) items: rows longer than SHORT_ROW are at most
+// nnzA / (SHORT_ROW + 1), and their chunks add at most nnzA / LONG_CHUNK.
+long long flops_item_capacity(long long n, long long nnzA) {
+    long long rows = nnzA / (SHORT_ROW + 1) + 1;
+    if (rows > n) rows = n;
+    return rows + nnzA / LONG_CHUNK + 1;
 }
 
 // Class histogram of the rows (class 0 = no products); rows without products
@@ -157,15 +183,14 @@ cudaError_t launch_row_flops(const DevCsr& A, const DevCsr& B, const Sched& s, c
     cudaError_t e;
     if ((e = cudaMemsetAsync(s.hdr, 0, sizeof(WsHeader), st))) return e;
     if (n == 0) return cudaSuccess;
-    if ((e = cudaMemsetAsync(s.flops, 0, sizeof(long long) * n, st))) return e;
-    if (A.nnz > 0) {
-        const SegWhole segB{B.rowptr, B.nnz, (int)B.ncols};
-        const long long warps = (A.nnz + FLOPS_CHUNK - 1) / FLOPS_CHUNK;
-        const long long blocks = (warps + 7) / 8;
-        count_launch();
-        k_flops_entries<<<(unsigned)blocks, 256, 0, st>>>(n, A.rowptr, A.col, A.nnz, segB,
-                                                          (int)B.nrows, s.flops, s.hdr);
-    }
+    const SegWhole segB{B.rowptr, B.nnz, (int)B.ncols};
+    const long long cap = flops_item_capacity(n, A.nnz);
+    count_launch();
+    k_flops_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A.rowptr, A.col, A.nnz, segB,
+                                                             (int)B.nrows, s.flops, s.items, cap, s.hdr);
+    count_launch();
+    k_flops_chunks<<<152 * 8, 256, 0, st>>>(A.rowptr, A.col, A.nnz, segB, (int)B.nrows, s.flops, s.items,
+                                            cap, s.hdr);
     return cudaGetLastError();
 }
 
@@ -200,6 +225,13 @@ struct SymVisit {
     unsigned* bm;
     int d;
     unsigned long long* err;
+    struct Item {
+        int c;
+    };
+    __device__ __forceinline__ Item fetch(long long j) const { return Item{__ldg(Bi + j)}; }
+    __device__ __forceinline__ void apply(const Item& it, float, long long, int) { mark(it.c); }
+    template <int G>
+    __device__ __forceinline__ void done(int, int, int, long long) {}
     __device__ __forceinline__ void mark(int c) {
         if ((unsigned)c < (unsigned)d) atomicOr(bm + (c >> 5), 1u << (c & 31));
         else atomicOr(err, ERR_B_COL);
@@ -231,20 +263,15 @@ struct SymParams {
     long long* Cp_next;
 };
 
-// Rows with products: all classes >= 1; heavy: classes >= cta_class.
-__device__ __forceinline__ void sched_counts(const WsHeader* hdr, int cta_class, long long& nheavy,
-                                             long long& nrows) {
-    long long nh = 0, nr = 0;
-    for (int c = 1; c < NUM_CLASSES; ++c) {
-        const long long h = hdr->hist[c];
-        nr += h;
-        if (c >= cta_class) nh += h;
-    }
-    nheavy = nh;
-    nrows = nr;
+template <int G, class Seg>
+__device__ __forceinline__ void sym_chunk(const SymParams& p, long long e0, int nv, SymVisit& vis,
+                                          unsigned long long* err) {
+    if constexpr (G == 1) expand_chunk(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
+    else grouped_chunk<G>(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
 }
 
-__global__ void __launch_bounds__(1024) k_symbolic(SymParams p) {
+template <int G>
+__global__ void __launch_bounds__(256, 6) k_symbolic(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];
@@ -272,8 +299,7 @@ __global__ void __launch_bounds__(1024) k_symbolic(SymParams p) {
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
         SymVisit vis{p.Bi, smem_u, p.d, err};
         for (long long e0 = a0 + 32LL * warp; e0 < a1; e0 += 32LL * nw)
-            expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, (const float*)nullptr, p.nB,
-                         p.segB, vis, err);
+            sym_chunk<G, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
         __syncthreads();
         int c = 0;
         for (int w = tid; w < p.dw; w += blockDim.x) {
@@ -299,8 +325,7 @@ __global__ void __launch_bounds__(1024) k_symbolic(SymParams p) {
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
         SymVisit vis{p.Bi, bm, p.d, err};
         for (long long e0 = a0; e0 < a1; e0 += 32)
-            expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, (const float*)nullptr, p.nB,
-                         p.segB, vis, err);
+            sym_chunk<G, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
         __syncwarp();
         int c = 0;
         for (int w = lane; w < p.dw; w += 32) {
@@ -353,10 +378,21 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.Cp_next = Cp + 1;
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)p.dw * cfg.warps_per_cta;
-    if ((e = set_smem((const void*)k_symbolic, smem))) return e;
-    const int grid = persistent_grid((const void*)k_symbolic, threads, smem, cfg.sms);
+    const void* k;
+    switch (cfg.group) {
+        case 1: k = (const void*)k_symbolic<1>; break;
+        case 4: k = (const void*)k_symbolic<4>; break;
+        case 8: k = (const void*)k_symbolic<8>; break;
+        case 16: k = (const void*)k_symbolic<16>; break;
+        case 32: k = (const void*)k_symbolic<32>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (threads > 256) return cudaErrorInvalidValue;
+    if ((e = set_smem(k, smem))) return e;
+    const int grid = persistent_grid(k, threads, smem, cfg.sms);
+    void* args[] = {&p};
     count_launch();
-    k_symbolic<<<grid, threads, smem, st>>>(p);
+    if ((e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st))) return e;
     if ((e = cudaGetLastError())) return e;
     return launch_scan_inplace(Cp + 1, n, s.partial, st);
 }
@@ -485,259 +521,6 @@ cudaError_t launch_tile_split(const DevCsr& B, int W, int T, long long* tp, cuda
     if (tot == 0) return cudaSuccess;
     count_launch();
     k_tile_split<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(B.nrows, B.rowptr, B.col, B.nnz, W, T, tp);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Numeric pass, dense accumulator (the paper's SPA, Sec. III-C) of width W in
-// shared memory plus one occupancy byte per column.  Row i of C is produced
-// tile by tile (W columns each); inside a tile the occupied columns are read
-// out in ascending order by ballot/popc over the flags, which also restores
-// the accumulator to zero for the next row.
-// ---------------------------------------------------------------------------
-constexpr int MAX_DENSE_W = 4096;
-
-template <bool VALUES>
-struct NumVisit {
-    const int* __restrict__ Bi;
-    const float* __restrict__ Bx;
-    float* acc;
-    unsigned char* flg;
-    int d;
-    int c0;
-    int W;
-    unsigned long long* err;
-    __device__ __forceinline__ void apply(int c, float v) {
-        const int lc = c - c0;
-        if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
-            flg[lc] = 1;
-            if (VALUES) atomicAdd(acc + lc, v);
-        } else {
-            atomicOr(err, ERR_B_COL);
-        }
-    }
-    __device__ __forceinline__ void step4(const long long* j, const float* a, const int*) {
-        int c[4];
-        float b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            c[u] = __ldg(Bi + j[u]);
-            b[u] = VALUES ? __ldg(Bx + j[u]) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) apply(c[u], a[u] * b[u]);
-    }
-    __device__ __forceinline__ void step1(long long j, float a, int, bool ok) {
-        if (ok) {
-            const int c = __ldg(Bi + j);
-            const float b = VALUES ? __ldg(Bx + j) : 0.0f;
-            apply(c, a * b);
-        }
-    }
-};
-
-struct NumParams {
-    const long long* Ap;
-    const int* Ai;
-    const float* Ax;
-    long long nnzA;
-    const long long* Bp;
-    const int* Bi;
-    const float* Bx;
-    long long nnzB;
-    int nB;
-    int d;
-    int W;
-    int T;
-    const long long* tp;
-    const int* perm;
-    WsHeader* hdr;
-    int cta_class;
-    const long long* Cp;
-    int* Ci;
-    float* Cx;
-    long long nnzC;
-};
-
-template <bool VALUES>
-__device__ __forceinline__ void warp_emit(float* acc, unsigned char* flg, int W, int c0, long long& out,
-                                          long long out_end, int* Ci, float* Cx,
-                                          unsigned long long* err) {
-    const int lane = lane_id();
-    const unsigned lt = lanemask_lt();
-    for (int w0 = 0; w0 < W; w0 += 32) {
-        const int c = w0 + lane;
-        const bool f = flg[c] != 0;
-        const unsigned bal = __ballot_sync(FULL, f);
-        if (f) {
-            const long long pos = out + __popc(bal & lt);
-            if (pos < out_end) {
-                Ci[pos] = c0 + c;
-                if (VALUES) Cx[pos] = acc[c];
-            } else {
-                atomicOr(err, ERR_C_ROW);
-            }
-            flg[c] = 0;
-            if (VALUES) acc[c] = 0.0f;
-        }
-        out += __popc(bal);
-    }
-}
-
-// Block-wide read-out for a heavy row; wcnt has W/32 + 1 entries.
-template <bool VALUES>
-__device__ __forceinline__ void cta_emit(float* acc, unsigned char* flg, int W, int c0, long long& out,
-                                         long long out_end, int* Ci, float* Cx, int* wcnt,
-                                         unsigned long long* err) {
-    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
-    const int words = W >> 5;
-    const unsigned lt = lanemask_lt();
-    for (int w = warp; w < words; w += nw) {
-        const unsigned bal = __ballot_sync(FULL, flg[w * 32 + lane] != 0);
-        if (lane == 0) wcnt[w] = __popc(bal);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int tot = warp_excl_scan_smem(wcnt, words);
-        if (lane == 0) wcnt[words] = tot;
-    }
-    __syncthreads();
-    for (int w = warp; w < words; w += nw) {
-        const int c = w * 32 + lane;
-        const bool f = flg[c] != 0;
-        const unsigned bal = __ballot_sync(FULL, f);
-        if (f) {
-            const long long pos = out + wcnt[w] + __popc(bal & lt);
-            if (pos < out_end) {
-                Ci[pos] = c0 + c;
-                if (VALUES) Cx[pos] = acc[c];
-            } else {
-                atomicOr(err, ERR_C_ROW);
-            }
-            flg[c] = 0;
-            if (VALUES) acc[c] = 0.0f;
-        }
-    }
-    out += wcnt[words];
-    __syncthreads();
-}
-
-template <bool VALUES, bool CTA>
-__device__ __forceinline__ void numeric_row(const NumParams& p, int row, float* acc, unsigned char* flg,
-                                            int* wcnt) {
-    unsigned long long* err = &p.hdr->err;
-    const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
-    const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
-    long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
-    const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
-    const int nw = blockDim.x >> 5;
-    const long long first = CTA ? a0 + 32LL * warp_id() : a0;
-    const long long stride = CTA ? 32LL * nw : 32LL;
-    const float* Ax = VALUES ? p.Ax : nullptr;
-    for (int t = 0; t < p.T; ++t) {
-        NumVisit<VALUES> vis{p.Bi, p.Bx, acc, flg, p.d, t * p.W, p.W, err};
-        if (p.T == 1) {
-            const SegWhole seg{p.Bp, p.nnzB, p.d};
-            for (long long e0 = first; e0 < a1; e0 += stride)
-                expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, Ax, p.nB, seg, vis, err);
-        } else {
-            const SegTile seg{p.tp, p.T + 1, t, p.W};
-            for (long long e0 = first; e0 < a1; e0 += stride)
-                expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, Ax, p.nB, seg, vis, err);
-        }
-        if (CTA) {
-            __syncthreads();
-            cta_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, wcnt, err);
-        } else {
-            __syncwarp();
-            warp_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, err);
-            __syncwarp();
-        }
-    }
-    if (out != out_end && (CTA ? threadIdx.x == 0 : lane_id() == 0)) atomicOr(err, ERR_C_ROW);
-}
-
-template <bool VALUES>
-__global__ void __launch_bounds__(1024) k_numeric_dense(NumParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
-    __shared__ long long s_item, s_nheavy, s_nrows;
-    const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
-    const int slot = VALUES ? 5 * p.W : p.W;  // bytes per warp: W floats + W flags
-    for (int i = tid; i < nw * slot / 4; i += blockDim.x) ((unsigned*)smem)[i] = 0;
-    if (tid == 0) {
-        long long nh, nr;
-        sched_counts(p.hdr, p.cta_class, nh, nr);
-        s_nheavy = nh;
-        s_nrows = nr;
-    }
-    __syncthreads();
-    const long long nheavy = s_nheavy, nrows = s_nrows;
-    {
-        float* acc = (float*)smem;
-        unsigned char* flg = smem + (VALUES ? 4 * p.W : 0);
-        for (;;) {
-            if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
-            __syncthreads();
-            const long long h = s_item;
-            __syncthreads();
-            if (h >= nheavy) break;
-            numeric_row<VALUES, true>(p, p.perm[h], acc, flg, s_wcnt);
-        }
-    }
-    float* acc = (float*)(smem + (size_t)warp * slot);
-    unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
-    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
-         idx += (long long)gridDim.x * nw)
-        numeric_row<VALUES, false>(p, p.perm[idx], acc, flg, nullptr);
-}
-
-size_t numeric_dense_smem(int W, int warps, bool values) {
-    return (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
-}
-
-cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
-                                 const long long* tp, bool values, const Sched& s,
-                                 const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx,
-                                 long long nnzC, cudaStream_t st) {
-    cudaError_t e;
-    if (A.nrows == 0) return cudaSuccess;
-    if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
-    NumParams p;
-    p.Ap = A.rowptr;
-    p.Ai = A.col;
-    p.Ax = A.val;
-    p.nnzA = A.nnz;
-    p.Bp = B.rowptr;
-    p.Bi = B.col;
-    p.Bx = B.val;
-    p.nnzB = B.nnz;
-    p.nB = (int)B.nrows;
-    p.d = (int)d;
-    p.W = W;
-    p.T = T;
-    p.tp = tp;
-    p.perm = s.perm;
-    p.hdr = s.hdr;
-    p.cta_class = cfg.cta_class;
-    p.Cp = Cp;
-    p.Ci = Ci;
-    p.Cx = Cx;
-    p.nnzC = nnzC;
-    const int threads = 32 * cfg.warps_per_cta;
-    const size_t smem = numeric_dense_smem(W, cfg.warps_per_cta, values);
-    const void* k = values ? (const void*)k_numeric_dense<true> : (const void*)k_numeric_dense<false>;
-    if ((e = set_smem(k, smem))) return e;
-    const int grid = persistent_grid(k, threads, smem, cfg.sms);
-    if (values) {
-        count_launch();
-        k_numeric_dense<true><<<grid, threads, smem, st>>>(p);
-    }
-    else {
-        count_launch();
-        k_numeric_dense<false><<<grid, threads, smem, st>>>(p);
-    }
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream
         raise ValueError("msbfs: source out of range")
     dw = (d + 31) // 32
     sz = ctypes.c_size_t()
-    N.call("msbfs_workspace_size", n, d, ctypes.byref(sz))
+    N.call("msbfs_workspace_size", n, A.nnz, d, ctypes.byref(sz))
     ws = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=dev)
     visited = torch.empty(n * dw, dtype=torch.int32, device=dev)
     levels = torch.empty(n * d, dtype=torch.int32, device=dev)

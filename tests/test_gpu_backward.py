@@ -35,7 +35,8 @@ def _run(A, B, tuning=None, seed=1):
 
 
 @pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1}, {"cta_min_flops": 128, "warps_per_cta": 4},
-                                    {"warps_per_cta": 1}])
+                                    {"warps_per_cta": 1}, {"group": 1}, {"group": 4}, {"group": 32},
+                                    {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64}])
 def test_backward_matches_oracle(tuning):
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -44,9 +45,10 @@ def test_backward_matches_oracle(tuning):
     assert np.all(np.abs(dB - rB) <= REL * bB), np.max(np.abs(dB - rB) / np.maximum(bB, 1e-30))
 
 
-def test_backward_ragged_and_empty_rows():
+@pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}])
+def test_backward_ragged_and_empty_rows(tuning):
     A, B = synth.er_product(n=3000, k=5, d=100, density=0.05, seed=51)
-    rp, col, dC, dA, dB = _run(A, B)
+    rp, col, dC, dA, dB = _run(A, B, tuning)
     rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
     assert np.all(np.abs(dA - rA) <= REL * bA)
     assert np.all(np.abs(dB - rB) <= REL * bB)
