@@ -117,54 +117,101 @@ struct BwdOp {
     }
 };
 
-template <int G, class BA, bool CTA>
-__device__ __forceinline__ void backward_row(const BwdParams& p, const BA& ba, int row, float* g, float* sdA) {
+// dC row i scattered into the dense row g (or cleared again).
+__device__ __forceinline__ void scatter_dc(const BwdParams& p, long long c0, long long c1, float* g, bool clear,
+                                           int tid, int nthr, unsigned long long* err) {
+    for (long long e = c0 + tid; e < c1; e += nthr) {
+        const int c = __ldg(p.Ci + e);
+        if ((unsigned)c < (unsigned)p.d) g[c] = clear ? 0.0f : __ldg(p.dC + e);
+        else if (!clear) atomicOr(err, ERR_C_ROW);
+    }
+}
+
+// Products of one chunk, with the flattened-mode dA write-back.
+template <int G, class BA>
+__device__ __forceinline__ void bwd_chunk(const BwdParams& p, const Chunk& ch, int nv, long long e0, BwdOp<BA>& op,
+                                          float* sdA) {
+    if constexpr (G == 1) {
+        expand_loaded(ch, op);
+        __syncwarp();
+        if (p.dA) {
+            const int lane = lane_id();
+            if (lane < nv) p.dA[e0 + lane] = sdA[lane];
+            sdA[lane] = 0.0f;
+            __syncwarp();
+        }
+    } else {
+        grouped_loaded<G>(ch, nv, e0, op);
+    }
+}
+
+// Heavy row: the whole block works on one row.
+template <int G, class BA>
+__device__ __forceinline__ void backward_row_cta(const BwdParams& p, const BA& ba, int row, float* g, float* sdA) {
     unsigned long long* err = &p.hdr->err;
-    const int lane = lane_id();
     const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
     const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
     const long long c0 = clampll(__ldg(p.Cp + row), 0, p.nnzC);
     const long long c1 = clampll(__ldg(p.Cp + row + 1), c0, p.nnzC);
-    const int tid = CTA ? threadIdx.x : lane;
-    const int nthr = CTA ? blockDim.x : 32;
-    for (long long e = c0 + tid; e < c1; e += nthr) {
-        const int c = __ldg(p.Ci + e);
-        if ((unsigned)c < (unsigned)p.d) g[c] = __ldg(p.dC + e);
-        else atomicOr(err, ERR_C_ROW);
-    }
-    if (CTA) __syncthreads();
-    else __syncwarp();
+    scatter_dc(p, c0, c1, g, false, threadIdx.x, blockDim.x, err);
+    __syncthreads();
     const int nw = blockDim.x >> 5;
-    const long long first = CTA ? a0 + 32LL * warp_id() : a0;
-    const long long stride = CTA ? 32LL * nw : 32LL;
     const SegWhole seg{p.Bp, p.nnzB, p.d};
     BwdOp<BA> op{ba, g, sdA, p.dA, p.dB, p.dA != nullptr, p.d, err, {0.0f, 0.0f}};
-    for (long long e0 = first; e0 < a1; e0 += stride) {
+    for (long long e0 = a0 + 32LL * warp_id(); e0 < a1; e0 += 32LL * nw) {
         const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
-        if constexpr (G == 1) {
-            expand_chunk(e0, nv, p.Ai, p.Ax, p.nB, seg, op, err);
-            __syncwarp();
-            if (p.dA) {
-                if (lane < nv) p.dA[e0 + lane] = sdA[lane];
-                sdA[lane] = 0.0f;
-                __syncwarp();
-            }
-        } else {
-            grouped_chunk<G>(e0, nv, p.Ai, p.Ax, p.nB, seg, op, err);
-        }
+        bwd_chunk<G>(p, load_chunk(e0, nv, p.Ai, p.Ax, p.nB, seg, err), nv, e0, op, sdA);
     }
-    if (CTA) __syncthreads();
-    else __syncwarp();
-    for (long long e = c0 + tid; e < c1; e += nthr) {
-        const int c = __ldg(p.Ci + e);
-        if ((unsigned)c < (unsigned)p.d) g[c] = 0.0f;
-    }
-    if (CTA) __syncthreads();
-    else __syncwarp();
+    __syncthreads();
+    scatter_dc(p, c0, c1, g, true, threadIdx.x, blockDim.x, err);
+    __syncthreads();
 }
 
+// Light row, one warp, driven by pipelined_rows; the next row's range in C
+// is requested one row ahead.
+template <int G, class BA>
+struct BwdRowBody {
+    const BwdParams& p;
+    const BA& ba;
+    float* g;
+    float* sdA;
+    unsigned long long* err;
+    int pref_row;
+    long long pc0, pc1;
+    long long c0, c1;
+    __device__ __forceinline__ void gather(int row, long long a0, long long a1, const Chunk& ch0, int nv0,
+                                           int next_row) {
+        if (pref_row == row) {
+            c0 = pc0;
+            c1 = pc1;
+        } else {
+            c0 = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+            c1 = clampll(__ldg(p.Cp + row + 1), c0, p.nnzC);
+        }
+        if (next_row >= 0) {
+            pc0 = clampll(__ldg(p.Cp + next_row), 0, p.nnzC);
+            pc1 = clampll(__ldg(p.Cp + next_row + 1), pc0, p.nnzC);
+            pref_row = next_row;
+        }
+        scatter_dc(p, c0, c1, g, false, lane_id(), 32, err);
+        __syncwarp();
+        const SegWhole seg{p.Bp, p.nnzB, p.d};
+        BwdOp<BA> op{ba, g, sdA, p.dA, p.dB, p.dA != nullptr, p.d, err, {0.0f, 0.0f}};
+        bwd_chunk<G>(p, ch0, nv0, a0, op, sdA);
+        for (long long e0 = a0 + 32; e0 < a1; e0 += 32) {
+            const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
+            bwd_chunk<G>(p, load_chunk(e0, nv, p.Ai, p.Ax, p.nB, seg, err), nv, e0, op, sdA);
+        }
+    }
+    __device__ __forceinline__ void finish(int) {
+        __syncwarp();
+        scatter_dc(p, c0, c1, g, true, lane_id(), 32, err);
+        __syncwarp();
+    }
+};
+
 template <int G, bool PACKED>
-__global__ void __launch_bounds__(256, 6) k_backward(BwdParams p) {
+__global__ void __launch_bounds__(256, 4) k_backward(BwdParams p) {
     extern __shared__ __align__(16) float fsm[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
@@ -192,12 +239,12 @@ __global__ void __launch_bounds__(256, 6) k_backward(BwdParams p) {
         const long long h = s_item;
         __syncthreads();
         if (h >= nheavy) break;
-        backward_row<G, BA, true>(p, ba, p.perm[h], fsm, sdA);
+        backward_row_cta<G, BA>(p, ba, p.perm[h], fsm, sdA);
     }
     float* g = fsm + (size_t)warp * p.dpad;
-    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
-         idx += (long long)gridDim.x * nw)
-        backward_row<G, BA, false>(p, ba, p.perm[idx], g, sdA);
+    BwdRowBody<G, BA> body{p, ba, g, sdA, &p.hdr->err, -1, 0, 0, 0, 0};
+    pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
+                   p.nnzA, p.Ai, p.Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, &p.hdr->err, body);
 }
 
 size_t backward_smem(long long d, int warps) {

@@ -113,32 +113,45 @@ struct SegTile {
     }
 };
 
-// Expand the products of the A entries e0 + lane (lane < nvalid) of one
-// chunk of up to 32 entries: for every pair (entry q, position j in B's
-// segment of row A.col[e0+q]) call visit.step(j, a_q, q, ok) with all 32
-// lanes converged; `ok` is false for padding lanes.  Steps are issued four at
-// a time where possible so that every lane has several gathers in flight.
-template <class Seg, class Visit>
-__device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
-                                             const float* __restrict__ Ax, int nB, const Seg& seg,
-                                             Visit& visit, unsigned long long* err) {
+// Per-lane view of one chunk of up to 32 entries of A: lane l holds entry
+// e0 + l (if l < nvalid): the start and length of its segment of B and its
+// value a (1 when A has no values).
+struct Chunk {
+    long long start;
+    int len;
+    float a;
+};
+
+template <class Seg>
+__device__ __forceinline__ Chunk load_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
+                                            const float* __restrict__ Ax, int nB, const Seg& seg,
+                                            unsigned long long* err) {
     const int lane = lane_id();
-    long long start = 0;
-    int len = 0;
-    float a = 1.0f;
+    Chunk c{0, 0, 1.0f};
     if (lane < nvalid) {
-        int k = __ldg(Ai + e0 + lane);
+        const int k = __ldg(Ai + e0 + lane);
         if ((unsigned)k < (unsigned)nB) {
-            seg(k, start, len);
-            if (Ax) a = __ldg(Ax + e0 + lane);
+            seg(k, c.start, c.len);
+            if (Ax) c.a = __ldg(Ax + e0 + lane);
         } else {
             atomicOr(err, ERR_A_COL);
         }
     }
-    const int incl = warp_incl_scan(len);
+    return c;
+}
+
+// Flattened expansion of a loaded chunk: the products (entry q, position j in
+// q's segment of B) are numbered across the 32 entries and lane l takes
+// numbers l, l+32, ...; visit.step4/step1(j, a_q, q[, ok]) are called with all
+// lanes converged (ok is false for padding lanes).  Steps are issued four at
+// a time where possible so that every lane has several gathers in flight.
+template <class Visit>
+__device__ __forceinline__ void expand_loaded(const Chunk& ch, Visit& visit) {
+    const int lane = lane_id();
+    const int incl = warp_incl_scan(ch.len);
     const int total = __shfl_sync(FULL, incl, 31);
-    const int excl = incl - len;
-    const long long shift = start - excl;  // position in B = shift(owner) + p
+    const int excl = incl - ch.len;
+    const long long shift = ch.start - excl;  // position in B = shift(owner) + p
     int p0 = 0;
     for (; p0 + 128 <= total; p0 += 128) {
         long long j[4];
@@ -149,7 +162,7 @@ __device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int
             const int p = p0 + 32 * u + lane;
             q[u] = owner_lane(excl, p);
             j[u] = shfl64(shift, q[u]) + p;
-            av[u] = __shfl_sync(FULL, a, q[u]);
+            av[u] = __shfl_sync(FULL, ch.a, q[u]);
         }
         visit.step4(j, av, q);
     }
@@ -157,9 +170,17 @@ __device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int
         const int p = p0 + lane;
         const int q = owner_lane(excl, p);
         const long long j = shfl64(shift, q) + p;
-        const float av = __shfl_sync(FULL, a, q);
+        const float av = __shfl_sync(FULL, ch.a, q);
         visit.step1(j, av, q, p < total);
     }
+}
+
+template <class Seg, class Visit>
+__device__ __forceinline__ void expand_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
+                                             const float* __restrict__ Ax, int nB, const Seg& seg,
+                                             Visit& visit, unsigned long long* err) {
+    const Chunk ch = load_chunk(e0, nvalid, Ai, Ax, nB, seg, err);
+    expand_loaded(ch, visit);
 }
 
 // B's entries either as the caller's two arrays or as (column, value bits)
@@ -191,31 +212,17 @@ struct BPacked {
 // outstanding.  `op` provides fetch(j) -> Item, apply(item, a_q, j, slot) and
 // done<G>(q0, q1, nvalid, e0), called once per pass with all 32 lanes
 // converged after both entries' segments are complete.
-template <int G, class Seg, class Op>
-__device__ __forceinline__ void grouped_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
-                                              const float* __restrict__ Ax, int nB, const Seg& seg,
-                                              Op& op, unsigned long long* err) {
+template <int G, class Op>
+__device__ __forceinline__ void grouped_loaded(const Chunk& ch, int nvalid, long long e0, Op& op) {
     static_assert(G >= 2 && G <= 32 && (32 % G) == 0, "group size");
     constexpr int NG = 32 / G;
     const int lane = lane_id();
-    long long start = 0;
-    int len = 0;
-    float a = 1.0f;
-    if (lane < nvalid) {
-        const int k = __ldg(Ai + e0 + lane);
-        if ((unsigned)k < (unsigned)nB) {
-            seg(k, start, len);
-            if (Ax) a = __ldg(Ax + e0 + lane);
-        } else {
-            atomicOr(err, ERR_A_COL);
-        }
-    }
     const int gi = lane / G, gl = lane % G;
     for (int t = 0; t < nvalid; t += 2 * NG) {
         const int q0 = t + gi, q1 = t + NG + gi;  // both <= 31 because 2*NG divides 32
-        const long long s0 = shfl64(start, q0), s1 = shfl64(start, q1);
-        const int l0 = __shfl_sync(FULL, len, q0), l1 = __shfl_sync(FULL, len, q1);
-        const float a0 = __shfl_sync(FULL, a, q0), a1 = __shfl_sync(FULL, a, q1);
+        const long long s0 = shfl64(ch.start, q0), s1 = shfl64(ch.start, q1);
+        const int l0 = __shfl_sync(FULL, ch.len, q0), l1 = __shfl_sync(FULL, ch.len, q1);
+        const float a0 = __shfl_sync(FULL, ch.a, q0), a1 = __shfl_sync(FULL, ch.a, q1);
         const int lm = l0 > l1 ? l0 : l1;
         for (int r = gl; r < lm; r += G) {
             const bool v0 = r < l0, v1 = r < l1;
@@ -226,6 +233,64 @@ __device__ __forceinline__ void grouped_chunk(long long e0, int nvalid, const in
             if (v1) op.apply(i1, a1, s1 + r, 1);
         }
         op.template done<G>(q0, q1, nvalid, e0);
+    }
+}
+
+template <int G, class Seg, class Op>
+__device__ __forceinline__ void grouped_chunk(long long e0, int nvalid, const int* __restrict__ Ai,
+                                              const float* __restrict__ Ax, int nB, const Seg& seg,
+                                              Op& op, unsigned long long* err) {
+    const Chunk ch = load_chunk(e0, nvalid, Ai, Ax, nB, seg, err);
+    grouped_loaded<G>(ch, nvalid, e0, op);
+}
+
+// Products of one chunk in the chosen distribution (G = 1: flattened).
+template <int G, class Op>
+__device__ __forceinline__ void expand_any(const Chunk& ch, int nvalid, long long e0, Op& op) {
+    if constexpr (G == 1) expand_loaded(ch, op);
+    else grouped_loaded<G>(ch, nvalid, e0, op);
+}
+
+// Software-pipelined walk over the light rows assigned to one warp (rows
+// perm[idx0], perm[idx0 + step], ...): while row r is processed, the row
+// index, row pointers and first chunk of A of row r+1 are already loaded.
+// body.gather(row, a0, a1, chunk0, nvalid0, next_row) gathers one row's
+// products (it consumes the first chunk from `chunk0`, loads any further
+// chunks itself, and may prefetch for next_row, -1 at the end); then
+// body.finish(row) completes the row (read-out), overlapping with the loads
+// of the next row's first chunk.
+template <class Seg, class Body>
+__device__ __forceinline__ void pipelined_rows(const int* __restrict__ perm, long long idx0, long long end,
+                                               long long step, const long long* __restrict__ Ap,
+                                               long long nnzA, const int* __restrict__ Ai,
+                                               const float* __restrict__ Ax, int nB, const Seg& seg,
+                                               unsigned long long* err, Body& body) {
+    if (idx0 >= end) return;
+    int row = __ldg(perm + idx0);
+    long long a0 = clampll(__ldg(Ap + row), 0, nnzA);
+    long long a1 = clampll(__ldg(Ap + row + 1), a0, nnzA);
+    int nv = (int)(a1 - a0 < 32 ? a1 - a0 : 32);
+    Chunk ch = load_chunk(a0, nv, Ai, Ax, nB, seg, err);
+    for (long long idx = idx0; idx < end; idx += step) {
+        // next row's meta data first, so that it is in flight during this row
+        const long long nidx = idx + step;
+        int nrow = 0;
+        long long na0 = 0, na1 = 0;
+        if (nidx < end) {
+            nrow = __ldg(perm + nidx);
+            na0 = clampll(__ldg(Ap + nrow), 0, nnzA);
+            na1 = clampll(__ldg(Ap + nrow + 1), na0, nnzA);
+        }
+        const int nnv = (int)(na1 - na0 < 32 ? na1 - na0 : 32);
+        body.gather(row, a0, a1, ch, nv, nidx < end ? nrow : -1);
+        // the next row's first chunk is loaded before this row's read-out
+        const Chunk nch = load_chunk(na0, nnv, Ai, Ax, nB, seg, err);
+        body.finish(row);
+        row = nrow;
+        a0 = na0;
+        a1 = na1;
+        nv = nnv;
+        ch = nch;
     }
 }
 

@@ -178,14 +178,15 @@ __device__ __forceinline__ void numeric_tile(const NumParams& p, const BA& ba, c
     const float* Ax = VALUES ? p.Ax : nullptr;
     for (long long e0 = first; e0 < a1; e0 += stride) {
         const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
-        if constexpr (G == 1) expand_chunk(e0, nv, p.Ai, Ax, p.nB, seg, op, err);
-        else grouped_chunk<G>(e0, nv, p.Ai, Ax, p.nB, seg, op, err);
+        const Chunk ch = load_chunk(e0, nv, p.Ai, Ax, p.nB, seg, err);
+        expand_any<G>(ch, nv, e0, op);
     }
 }
 
-template <bool VALUES, int G, class BA, bool CTA>
-__device__ __forceinline__ void numeric_row(const NumParams& p, const BA& ba, int row, float* acc,
-                                            unsigned char* flg, int* wcnt) {
+// Heavy row: the whole block works on one row.
+template <bool VALUES, int G, class BA>
+__device__ __forceinline__ void numeric_row_cta(const NumParams& p, const BA& ba, int row, float* acc,
+                                                unsigned char* flg, int* wcnt) {
     unsigned long long* err = &p.hdr->err;
     const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
     const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
@@ -193,22 +194,66 @@ __device__ __forceinline__ void numeric_row(const NumParams& p, const BA& ba, in
     const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
     for (int t = 0; t < p.T; ++t) {
         DenseOp<VALUES, BA> op{ba, acc, flg, p.d, t * p.W, p.W, err};
-        if (p.T == 1) numeric_tile<VALUES, G, BA, CTA>(p, ba, SegWhole{p.Bp, p.nnzB, p.d}, a0, a1, op);
-        else numeric_tile<VALUES, G, BA, CTA>(p, ba, SegTile{p.tp, p.T + 1, t, p.W}, a0, a1, op);
-        if (CTA) {
-            __syncthreads();
-            cta_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, wcnt, err);
-        } else {
-            __syncwarp();
-            warp_emit4<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, err);
-            __syncwarp();
-        }
+        if (p.T == 1) numeric_tile<VALUES, G, BA, true>(p, ba, SegWhole{p.Bp, p.nnzB, p.d}, a0, a1, op);
+        else numeric_tile<VALUES, G, BA, true>(p, ba, SegTile{p.tp, p.T + 1, t, p.W}, a0, a1, op);
+        __syncthreads();
+        cta_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, wcnt, err);
     }
-    if (out != out_end && (CTA ? threadIdx.x == 0 : lane_id() == 0)) atomicOr(err, ERR_C_ROW);
+    if (out != out_end && threadIdx.x == 0) atomicOr(err, ERR_C_ROW);
 }
 
+// Light row, one warp, driven by pipelined_rows: the first chunk of A (for
+// column tile 0) arrives preloaded; the row's output range is requested at
+// the start of the gather and used by the read-out.
+template <bool VALUES, int G, class BA>
+struct NumRowBody {
+    const NumParams& p;
+    const BA& ba;
+    float* acc;
+    unsigned char* flg;
+    unsigned long long* err;
+    long long out, out_end;
+    __device__ __forceinline__ void gather(int row, long long a0, long long a1, const Chunk& ch0, int nv0, int) {
+        out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+        out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+        const float* Ax = VALUES ? p.Ax : nullptr;
+        for (int t = 0; t < p.T; ++t) {
+            DenseOp<VALUES, BA> op{ba, acc, flg, p.d, t * p.W, p.W, err};
+            long long e_next = a0;
+            if (t == 0) {
+                expand_any<G>(ch0, nv0, a0, op);
+                e_next = a0 + 32;
+            }
+            if (p.T == 1) {
+                const SegWhole seg{p.Bp, p.nnzB, p.d};
+                for (long long e0 = e_next; e0 < a1; e0 += 32) {
+                    const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
+                    expand_any<G>(load_chunk(e0, nv, p.Ai, Ax, p.nB, seg, err), nv, e0, op);
+                }
+            } else {
+                const SegTile seg{p.tp, p.T + 1, t, p.W};
+                for (long long e0 = e_next; e0 < a1; e0 += 32) {
+                    const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
+                    expand_any<G>(load_chunk(e0, nv, p.Ai, Ax, p.nB, seg, err), nv, e0, op);
+                }
+                if (t + 1 < p.T) {  // the last tile is read out by finish()
+                    __syncwarp();
+                    warp_emit4<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, err);
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void finish(int) {
+        __syncwarp();
+        warp_emit4<VALUES>(acc, flg, p.W, (p.T - 1) * p.W, out, out_end, p.Ci, p.Cx, err);
+        __syncwarp();
+        if (out != out_end && lane_id() == 0) atomicOr(err, ERR_C_ROW);
+    }
+};
+
 template <bool VALUES, int G, bool PACKED>
-__global__ void __launch_bounds__(256, 6) k_numeric(NumParams p) {
+__global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
     __shared__ long long s_item, s_nheavy, s_nrows;
@@ -236,14 +281,21 @@ __global__ void __launch_bounds__(256, 6) k_numeric(NumParams p) {
             const long long h = s_item;
             __syncthreads();
             if (h >= nheavy) break;
-            numeric_row<VALUES, G, BA, true>(p, ba, p.perm[h], acc, flg, s_wcnt);
+            numeric_row_cta<VALUES, G, BA>(p, ba, p.perm[h], acc, flg, s_wcnt);
         }
     }
     float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
     unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
-    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
-         idx += (long long)gridDim.x * nw)
-        numeric_row<VALUES, G, BA, false>(p, ba, p.perm[idx], acc, flg, nullptr);
+    NumRowBody<VALUES, G, BA> body{p, ba, acc, flg, &p.hdr->err, 0, 0};
+    const long long idx0 = nheavy + (long long)blockIdx.x * nw + warp;
+    const long long step = (long long)gridDim.x * nw;
+    const float* Ax = VALUES ? p.Ax : nullptr;
+    if (p.T == 1)
+        pipelined_rows(p.perm, idx0, nrows, step, p.Ap, p.nnzA, p.Ai, Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d},
+                       &p.hdr->err, body);
+    else
+        pipelined_rows(p.perm, idx0, nrows, step, p.Ap, p.nnzA, p.Ai, Ax, p.nB,
+                       SegTile{p.tp, p.T + 1, 0, p.W}, &p.hdr->err, body);
 }
 
 __global__ void k_pack_b(long long nnz, const int* __restrict__ Bi, const float* __restrict__ Bx,

@@ -270,8 +270,35 @@ __device__ __forceinline__ void sym_chunk(const SymParams& p, long long e0, int 
     else grouped_chunk<G>(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
 }
 
+// Light row of the symbolic pass, driven by pipelined_rows.
 template <int G>
-__global__ void __launch_bounds__(256, 6) k_symbolic(SymParams p) {
+struct SymRowBody {
+    const SymParams& p;
+    unsigned* bm;
+    unsigned long long* err;
+    __device__ __forceinline__ void gather(int, long long a0, long long a1, const Chunk& ch0, int nv0, int) {
+        SymVisit vis{p.Bi, bm, p.d, err};
+        expand_any<G>(ch0, nv0, a0, vis);
+        for (long long e0 = a0 + 32; e0 < a1; e0 += 32) {
+            const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
+            expand_any<G>(load_chunk(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, err), nv, e0, vis);
+        }
+    }
+    __device__ __forceinline__ void finish(int row) {
+        __syncwarp();
+        int c = 0;
+        for (int w = lane_id(); w < p.dw; w += 32) {
+            c += __popc(bm[w]);
+            bm[w] = 0;
+        }
+        c = warp_sum(c);
+        if (lane_id() == 0) p.Cp_next[row] = c;
+        __syncwarp();
+    }
+};
+
+template <int G>
+__global__ void __launch_bounds__(256, 4) k_symbolic(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];
@@ -318,24 +345,9 @@ __global__ void __launch_bounds__(256, 6) k_symbolic(SymParams p) {
 
     // light rows: one warp per row, static round robin over the class order
     unsigned* bm = smem_u + warp * p.dw;
-    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
-         idx += (long long)gridDim.x * nw) {
-        const int row = p.perm[idx];
-        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
-        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
-        SymVisit vis{p.Bi, bm, p.d, err};
-        for (long long e0 = a0; e0 < a1; e0 += 32)
-            sym_chunk<G, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
-        __syncwarp();
-        int c = 0;
-        for (int w = lane; w < p.dw; w += 32) {
-            c += __popc(bm[w]);
-            bm[w] = 0;
-        }
-        c = warp_sum(c);
-        if (lane == 0) p.Cp_next[row] = c;
-        __syncwarp();
-    }
+    SymRowBody<G> body{p, bm, err};
+    pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
+                   p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body);
 }
 
 static std::atomic<long long> g_launches{0};
