@@ -167,6 +167,8 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
 
 struct Layout {
     size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, tp = 0, bpk = 0, total = 0;
+    size_t split_rows = 0, split_done = 0, split_items = 0, stg_bits = 0, stg_vals = 0, stg_flags = 0;
+    int dw = 0, dpad = 0;
     int W = 0, T = 1;
 };
 
@@ -188,6 +190,16 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     L.perm = take(sizeof(int) * (size_t)n);
     L.partial = take(sizeof(long long) * scan_partial_count(n));
     L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
+    L.dw = (int)((d + 31) / 32);
+    L.dpad = 32 * L.dw;
+    L.split_rows = take(sizeof(int) * MAX_SPLIT_ROWS);
+    L.split_done = take(sizeof(int) * MAX_SPLIT_ROWS);
+    L.split_items = take(sizeof(long long) * (size_t)split_item_capacity(nnzA));
+    L.stg_bits = take(sizeof(unsigned) * (size_t)MAX_SPLIT_ROWS * L.dw);
+    if (L.dpad <= 4096) {  // dense accumulators only
+        L.stg_vals = take(sizeof(float) * (size_t)MAX_SPLIT_ROWS * L.dpad);
+        L.stg_flags = take((size_t)MAX_SPLIT_ROWS * L.dpad);
+    }
     L.W = t.col_tile;
     L.T = (int)((d + L.W - 1) / L.W);
     if (L.T < 1) L.T = 1;
@@ -211,6 +223,14 @@ static Sched carve(void* ws, const Layout& L) {
     s.perm = (int*)(b + L.perm);
     s.partial = (long long*)(b + L.partial);
     s.items = (long long*)(b + L.items);
+    s.split_rows = (int*)(b + L.split_rows);
+    s.split_done = (int*)(b + L.split_done);
+    s.split_items = (long long*)(b + L.split_items);
+    s.stg_bits = (unsigned*)(b + L.stg_bits);
+    s.stg_vals = L.stg_vals ? (float*)(b + L.stg_vals) : nullptr;
+    s.stg_flags = L.stg_flags ? (unsigned char*)(b + L.stg_flags) : nullptr;
+    s.dw = L.dw;
+    s.dpad = L.dpad;
     return s;
 }
 

@@ -34,6 +34,8 @@ struct BwdParams {
     const int* perm;
     WsHeader* hdr;
     int cta_class;
+    Sched s;
+    long long item_cap;
 };
 
 // Sum of v over the run of equal keys that starts at this lane (keys are
@@ -145,12 +147,13 @@ __device__ __forceinline__ void bwd_chunk(const BwdParams& p, const Chunk& ch, i
     }
 }
 
-// Heavy row: the whole block works on one row.
+// Heavy row or one part [a0, a1) of a split row: the whole block works on it.
+// The parts of a split row are independent: each writes dA of its own
+// entries and adds its dB terms.
 template <int G, class BA>
-__device__ __forceinline__ void backward_row_cta(const BwdParams& p, const BA& ba, int row, float* g, float* sdA) {
+__device__ __forceinline__ void backward_range_cta(const BwdParams& p, const BA& ba, int row, long long a0,
+                                                   long long a1, float* g, float* sdA) {
     unsigned long long* err = &p.hdr->err;
-    const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
-    const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
     const long long c0 = clampll(__ldg(p.Cp + row), 0, p.nnzC);
     const long long c1 = clampll(__ldg(p.Cp + row + 1), c0, p.nnzC);
     scatter_dc(p, c0, c1, g, false, threadIdx.x, blockDim.x, err);
@@ -233,18 +236,29 @@ __global__ void __launch_bounds__(256, 4) k_backward(BwdParams p) {
     BA ba;
     if constexpr (PACKED) ba = BPacked{p.Bpk};
     else ba = BSep{p.Bi, p.Bx};
+    const long long* mark = p.s.flops;
+    {
+        const long long nitems = min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap);
+        SplitItem it;
+        while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it))
+            backward_range_cta<G, BA>(p, ba, it.row, it.e0, it.e1, fsm, sdA);
+    }
     for (;;) {
         if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
         __syncthreads();
         const long long h = s_item;
         __syncthreads();
         if (h >= nheavy) break;
-        backward_row_cta<G, BA>(p, ba, p.perm[h], fsm, sdA);
+        const int row = p.perm[h];
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        if (is_split_row(mark, row, a1 - a0)) continue;
+        backward_range_cta<G, BA>(p, ba, row, a0, a1, fsm, sdA);
     }
     float* g = fsm + (size_t)warp * p.dpad;
     BwdRowBody<G, BA> body{p, ba, g, sdA, &p.hdr->err, -1, 0, 0, 0, 0};
     pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
-                   p.nnzA, p.Ai, p.Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, &p.hdr->err, body);
+                   p.nnzA, p.Ai, p.Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, &p.hdr->err, body, mark);
 }
 
 size_t backward_smem(long long d, int warps) {
@@ -265,7 +279,7 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     if (dA && A.nnz && (e = cudaMemsetAsync(dA, 0, sizeof(float) * A.nnz, st))) return e;
     if (dB && B.nnz && (e = cudaMemsetAsync(dB, 0, sizeof(float) * B.nnz, st))) return e;
     if (A.nrows == 0 || (!dA && !dB)) return cudaSuccess;
-    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
     BwdParams p;
     p.Ap = A.rowptr;
     p.Ai = A.col;
@@ -288,6 +302,8 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     p.perm = s.perm;
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
+    p.s = s;
+    p.item_cap = split_item_capacity(A.nnz);
     int warps = cfg.warps_per_cta;
     if (warps > 8) return cudaErrorInvalidValue;
     size_t smem = backward_smem(d, warps);

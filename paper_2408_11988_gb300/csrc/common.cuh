@@ -13,6 +13,7 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+#include "kernels.h"
 #include "layout.h"
 
 namespace ts {
@@ -251,6 +252,12 @@ __device__ __forceinline__ void expand_any(const Chunk& ch, int nvalid, long lon
     else grouped_loaded<G>(ch, nvalid, e0, op);
 }
 
+// A row cut into split work items carries the mark -1 - slot in the flops
+// array (only rows with more than SPLIT_ENTRIES entries can be cut).
+__device__ __forceinline__ bool is_split_row(const long long* mark, int row, long long alen) {
+    return alen > SPLIT_ENTRIES && __ldg(mark + row) < 0;
+}
+
 // Software-pipelined walk over the light rows assigned to one warp (rows
 // perm[idx0], perm[idx0 + step], ...): while row r is processed, the row
 // index, row pointers and first chunk of A of row r+1 are already loaded.
@@ -264,7 +271,8 @@ __device__ __forceinline__ void pipelined_rows(const int* __restrict__ perm, lon
                                                long long step, const long long* __restrict__ Ap,
                                                long long nnzA, const int* __restrict__ Ai,
                                                const float* __restrict__ Ax, int nB, const Seg& seg,
-                                               unsigned long long* err, Body& body) {
+                                               unsigned long long* err, Body& body,
+                                               const long long* split_mark = nullptr) {
     if (idx0 >= end) return;
     int row = __ldg(perm + idx0);
     long long a0 = clampll(__ldg(Ap + row), 0, nnzA);
@@ -282,10 +290,11 @@ __device__ __forceinline__ void pipelined_rows(const int* __restrict__ perm, lon
             na1 = clampll(__ldg(Ap + nrow + 1), na0, nnzA);
         }
         const int nnv = (int)(na1 - na0 < 32 ? na1 - na0 : 32);
-        body.gather(row, a0, a1, ch, nv, nidx < end ? nrow : -1);
+        const bool skip = split_mark && is_split_row(split_mark, row, a1 - a0);
+        if (!skip) body.gather(row, a0, a1, ch, nv, nidx < end ? nrow : -1);
         // the next row's first chunk is loaded before this row's read-out
         const Chunk nch = load_chunk(na0, nnv, Ai, Ax, nB, seg, err);
-        body.finish(row);
+        if (!skip) body.finish(row);
         row = nrow;
         a0 = na0;
         a1 = na1;
@@ -305,6 +314,45 @@ __device__ __forceinline__ void sched_counts(const WsHeader* hdr, int cta_class,
     }
     nheavy = nh;
     nrows = nr;
+}
+
+// Fetch the next split item for this block; false when none is left.  On
+// true, row/slot/[e0, e1)/nsub describe the item.
+struct SplitItem {
+    int row;
+    int slot;
+    long long e0, e1;
+    int nsub;
+};
+
+__device__ __forceinline__ bool next_split_item(const Sched& s, const long long* __restrict__ Ap, long long nnzA,
+                                                long long nitems, long long* s_item, SplitItem& it) {
+    if (threadIdx.x == 0) *s_item = (long long)atomicAdd(&s.hdr->item_ctr, 1ull);
+    __syncthreads();
+    const long long k = *s_item;
+    __syncthreads();
+    if (k >= nitems) return false;
+    const long long code = s.split_items[k];
+    it.slot = (int)(code >> 32);
+    const long long part = code & 0xFFFFFFFFLL;
+    it.row = s.split_rows[it.slot];
+    const long long a0 = clampll(__ldg(Ap + it.row), 0, nnzA), a1 = clampll(__ldg(Ap + it.row + 1), a0, nnzA);
+    it.nsub = (int)((a1 - a0 + SPLIT_ENTRIES - 1) / SPLIT_ENTRIES);
+    it.e0 = a0 + part * SPLIT_ENTRIES;
+    it.e1 = it.e0 + SPLIT_ENTRIES < a1 ? it.e0 + SPLIT_ENTRIES : a1;
+    return true;
+}
+
+// After a block flushed its part of split row `slot` into the staging slot:
+// count it and return (to every thread) whether this block was the last.
+__device__ __forceinline__ bool split_part_done(const Sched& s, int slot, int nsub, int* s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = (atomicAdd(s.split_done + slot, 1) == nsub - 1) ? 1 : 0;
+    __syncthreads();
+    const bool last = *s_flag != 0;
+    if (last) __threadfence();
+    return last;
 }
 
 // Exclusive-scan helper for per-word counts held in shared memory by one warp.

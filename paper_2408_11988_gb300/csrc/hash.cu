@@ -258,7 +258,7 @@ cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, i
         smem = (size_t)warps * ((size_t)slots * 8 + (size_t)dw * 4);
     }
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
     HashParams p;
     p.Ap = A.rowptr;
     p.Ai = A.col;

@@ -25,7 +25,19 @@ struct Sched {
     int* perm = nullptr;         // non-empty rows, heaviest class first, int32[n]
     long long* partial = nullptr;// scan partial sums
     long long* items = nullptr;  // (row, chunk) work items of long rows for the flops pass
+    // split rows (more than SPLIT_ENTRIES entries of A): row ids, completion
+    // counters, (slot, part) work items and per-slot staging of partial rows
+    int* split_rows = nullptr;        // [MAX_SPLIT_ROWS]
+    int* split_done = nullptr;        // [MAX_SPLIT_ROWS]
+    long long* split_items = nullptr; // [split_item_capacity]
+    unsigned* stg_bits = nullptr;     // [MAX_SPLIT_ROWS][dw]     symbolic
+    float* stg_vals = nullptr;        // [MAX_SPLIT_ROWS][dpad]   numeric (dense)
+    unsigned char* stg_flags = nullptr; // [MAX_SPLIT_ROWS][dpad] numeric (dense)
+    int dw = 0, dpad = 0;
 };
+
+// Capacity (entries) of Sched::split_items for nnzA entries of A.
+long long split_item_capacity(long long nnzA);
 
 // Capacity (entries) of Sched::items for a matrix with n rows and nnzA entries.
 long long flops_item_capacity(long long n, long long nnzA);

@@ -40,6 +40,8 @@ struct NumParams {
     int* Ci;
     float* Cx;
     long long nnzC;
+    Sched s;
+    long long item_cap;
 };
 
 template <bool VALUES, class BA>
@@ -202,6 +204,74 @@ __device__ __forceinline__ void numeric_row_cta(const NumParams& p, const BA& ba
     if (out != out_end && threadIdx.x == 0) atomicOr(err, ERR_C_ROW);
 }
 
+// One part of a split row: the block accumulates entries [e0, e1) tile by
+// tile and adds each tile into the row's staging slot (columns t*W + c).  The
+// block finishing the last part reads the row out of the staging slot in
+// ascending column order and clears the slot.
+template <bool VALUES, int G, class BA>
+__device__ __forceinline__ void numeric_split_part(const NumParams& p, const BA& ba, const SplitItem& it,
+                                                   float* acc, unsigned char* flg, int* wcnt, int* s_last) {
+    unsigned long long* err = &p.hdr->err;
+    float* sv = p.s.stg_vals + (size_t)it.slot * p.s.dpad;
+    unsigned char* sf = p.s.stg_flags + (size_t)it.slot * p.s.dpad;
+    for (int t = 0; t < p.T; ++t) {
+        DenseOp<VALUES, BA> op{ba, acc, flg, p.d, t * p.W, p.W, err};
+        if (p.T == 1) numeric_tile<VALUES, G, BA, true>(p, ba, SegWhole{p.Bp, p.nnzB, p.d}, it.e0, it.e1, op);
+        else numeric_tile<VALUES, G, BA, true>(p, ba, SegTile{p.tp, p.T + 1, t, p.W}, it.e0, it.e1, op);
+        __syncthreads();
+        for (int c = threadIdx.x; c < p.W; c += blockDim.x) {
+            if (flg[c]) {
+                if (VALUES) {
+                    atomicAdd(sv + t * p.W + c, acc[c]);
+                    acc[c] = 0.0f;
+                }
+                sf[t * p.W + c] = 1;
+                flg[c] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    if (!split_part_done(p.s, it.slot, it.nsub, s_last)) return;
+    // last part: read the row out of the staging slot
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    const int words = p.s.dpad >> 5;
+    const unsigned lt = lanemask_lt();
+    long long out = clampll(__ldg(p.Cp + it.row), 0, p.nnzC);
+    const long long out_end = clampll(__ldg(p.Cp + it.row + 1), out, p.nnzC);
+    for (int w = warp; w < words; w += nw) {
+        const unsigned bal = __ballot_sync(FULL, __ldcg(sf + w * 32 + lane) != 0);
+        if (lane == 0) wcnt[w] = __popc(bal);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int tot = warp_excl_scan_smem(wcnt, words);
+        if (lane == 0) wcnt[words] = tot;
+    }
+    __syncthreads();
+    for (int w = warp; w < words; w += nw) {
+        const int c = w * 32 + lane;
+        const bool f = __ldcg(sf + c) != 0;
+        const unsigned bal = __ballot_sync(FULL, f);
+        if (f) {
+            const long long pos = out + wcnt[w] + __popc(bal & lt);
+            if (pos < out_end) {
+                p.Ci[pos] = c;
+                if (VALUES) p.Cx[pos] = __ldcg(sv + c);
+            } else {
+                atomicOr(err, ERR_C_ROW);
+            }
+            if (VALUES) sv[c] = 0.0f;
+            sf[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (out + wcnt[words] != out_end) atomicOr(err, ERR_C_ROW);
+        p.s.split_done[it.slot] = 0;
+    }
+    __syncthreads();
+}
+
 // Light row, one warp, driven by pipelined_rows: the first chunk of A (for
 // column tile 0) arrives preloaded; the row's output range is requested at
 // the start of the gather and used by the read-out.
@@ -272,16 +342,25 @@ __global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
     BA ba;
     if constexpr (PACKED) ba = BPacked{p.Bpk};
     else ba = BSep{p.Bi, VALUES ? p.Bx : nullptr};
+    const long long* mark = p.s.flops;
     {
         float* acc = reinterpret_cast<float*>(smem);
         unsigned char* flg = smem + (VALUES ? 4 * p.W : 0);
+        // parts of split rows first (any block), then whole heavy rows
+        const long long nitems = min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap);
+        __shared__ int s_last;
+        SplitItem it;
+        while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it))
+            numeric_split_part<VALUES, G, BA>(p, ba, it, acc, flg, s_wcnt, &s_last);
         for (;;) {
             if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
             __syncthreads();
             const long long h = s_item;
             __syncthreads();
             if (h >= nheavy) break;
-            numeric_row_cta<VALUES, G, BA>(p, ba, p.perm[h], acc, flg, s_wcnt);
+            const int row = p.perm[h];
+            if (is_split_row(mark, row, __ldg(p.Ap + row + 1) - __ldg(p.Ap + row))) continue;
+            numeric_row_cta<VALUES, G, BA>(p, ba, row, acc, flg, s_wcnt);
         }
     }
     float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
@@ -292,10 +371,10 @@ __global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
     const float* Ax = VALUES ? p.Ax : nullptr;
     if (p.T == 1)
         pipelined_rows(p.perm, idx0, nrows, step, p.Ap, p.nnzA, p.Ai, Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d},
-                       &p.hdr->err, body);
+                       &p.hdr->err, body, mark);
     else
         pipelined_rows(p.perm, idx0, nrows, step, p.Ap, p.nnzA, p.Ai, Ax, p.nB,
-                       SegTile{p.tp, p.T + 1, 0, p.W}, &p.hdr->err, body);
+                       SegTile{p.tp, p.T + 1, 0, p.W}, &p.hdr->err, body, mark);
 }
 
 __global__ void k_pack_b(long long nnz, const int* __restrict__ Bi, const float* __restrict__ Bx,
@@ -352,7 +431,8 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if (A.nrows == 0) return cudaSuccess;
     if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
+    if (s.dpad > MAX_DENSE_W || !s.stg_vals) return cudaErrorInvalidValue;
     NumParams p;
     p.Ap = A.rowptr;
     p.Ai = A.col;
@@ -375,6 +455,8 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     p.Ci = Ci;
     p.Cx = Cx;
     p.nnzC = nnzC;
+    p.s = s;
+    p.item_cap = split_item_capacity(A.nnz);
     if (values) {
         if (Bpk) return launch_g<true, true>(p, G, cfg.warps_per_cta, cfg.sms, st);
         return launch_g<true, false>(p, G, cfg.warps_per_cta, cfg.sms, st);

@@ -216,6 +216,46 @@ cudaError_t launch_row_schedule(const DevCsr& A, const DevCsr& B, const Sched& s
 }
 
 // ---------------------------------------------------------------------------
+// Split rows: a row with more than SPLIT_ENTRIES entries of A (and some
+// products) gets a slot u < MAX_SPLIT_ROWS and ceil(len / SPLIT_ENTRIES)
+// work items (u, part) that any block may take, so that one very heavy row
+// is spread over many SMs instead of forming the tail of the pass.  The
+// row's flops entry becomes the mark -1 - u, and its staging slot is cleared.
+// ---------------------------------------------------------------------------
+long long split_item_capacity(long long nnzA) { return nnzA / SPLIT_ENTRIES + MAX_SPLIT_ROWS + 1; }
+
+__global__ void __launch_bounds__(256) k_split_rows(long long n, const long long* __restrict__ Ap, long long nnzA,
+                                                    long long* flops, Sched s, long long item_cap) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long a0 = clampll(Ap[i], 0, nnzA), a1 = clampll(Ap[i + 1], a0, nnzA);
+    const long long alen = a1 - a0;
+    if (alen <= SPLIT_ENTRIES || flops[i] <= 0) return;
+    const long long u = (long long)atomicAdd((unsigned long long*)&s.hdr->scratch[1], 1ull);
+    if (u >= MAX_SPLIT_ROWS) return;  // out of slots: the row runs whole
+    const long long nsub = (alen + SPLIT_ENTRIES - 1) / SPLIT_ENTRIES;
+    const long long base = (long long)atomicAdd((unsigned long long*)&s.hdr->scratch[2], (unsigned long long)nsub);
+    if (base + nsub > item_cap) {
+        atomicOr(&s.hdr->err, ERR_CAPACITY);
+        return;
+    }
+    for (int w = 0; w < s.dw; ++w) s.stg_bits[u * s.dw + w] = 0u;
+    if (s.stg_vals) {
+        float4* v = reinterpret_cast<float4*>(s.stg_vals + u * s.dpad);
+        unsigned* f = reinterpret_cast<unsigned*>(s.stg_flags + u * s.dpad);
+        for (int c = 0; c < s.dpad / 4; ++c) {
+            v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            f[c] = 0u;
+        }
+    }
+    s.split_rows[u] = (int)i;
+    s.split_done[u] = 0;
+    for (long long q = 0; q < nsub; ++q) s.split_items[base + q] = (u << 32) | q;
+    flops[i] = -1 - u;
+}
+
+
+// ---------------------------------------------------------------------------
 // Symbolic pass: nnz(C_i) = number of distinct columns over the rows B_k,
 // k in A_i (Eq. 1 on patterns).  A bitmap of d bits per warp (shared by the
 // whole block for heavy rows) collects the columns; popcounts give the count.
@@ -261,6 +301,8 @@ struct SymParams {
     WsHeader* hdr;
     int cta_class;
     long long* Cp_next;
+    Sched s;
+    long long item_cap;
 };
 
 template <int G, class Seg>
@@ -313,6 +355,48 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SymParams p) {
     __syncthreads();
     const long long nheavy = s_nheavy, nrows = s_nrows;
     unsigned long long* err = &p.hdr->err;
+    const long long* mark = p.s.flops;
+
+    // split rows: parts of very long rows, any block; partial bitmaps are OR-ed
+    // into the row's staging slot and the last part counts the row
+    {
+        const long long nitems = min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap);
+        __shared__ int s_last;
+        SplitItem it;
+        while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
+            SymVisit vis{p.Bi, smem_u, p.d, err};
+            for (long long e0 = it.e0 + 32LL * warp; e0 < it.e1; e0 += 32LL * nw)
+                sym_chunk<G, SegWhole>(p, e0, (int)(it.e1 - e0 < 32 ? it.e1 - e0 : 32), vis, err);
+            __syncthreads();
+            unsigned* stg = p.s.stg_bits + (size_t)it.slot * p.dw;
+            for (int w = tid; w < p.dw; w += blockDim.x) {
+                const unsigned v = smem_u[w];
+                if (v) {
+                    atomicOr(stg + w, v);
+                    smem_u[w] = 0u;
+                }
+            }
+            if (split_part_done(p.s, it.slot, it.nsub, &s_last)) {
+                int c = 0;
+                for (int w = tid; w < p.dw; w += blockDim.x) {
+                    c += __popc(__ldcg(stg + w));
+                    stg[w] = 0u;
+                }
+                c = warp_sum(c);
+                if (lane == 0) s_red[warp] = c;
+                __syncthreads();
+                if (warp == 0) {
+                    int v = lane < nw ? s_red[lane] : 0;
+                    v = warp_sum(v);
+                    if (lane == 0) {
+                        p.Cp_next[it.row] = v;
+                        p.s.split_done[it.slot] = 0;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
 
     // heavy rows: one block per row, dynamic
     for (;;) {
@@ -324,6 +408,7 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SymParams p) {
         const int row = p.perm[h];
         const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        if (is_split_row(mark, row, a1 - a0)) continue;
         SymVisit vis{p.Bi, smem_u, p.d, err};
         for (long long e0 = a0 + 32LL * warp; e0 < a1; e0 += 32LL * nw)
             sym_chunk<G, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
@@ -347,7 +432,7 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SymParams p) {
     unsigned* bm = smem_u + warp * p.dw;
     SymRowBody<G> body{p, bm, err};
     pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
-                   p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body);
+                   p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body, mark);
 }
 
 static std::atomic<long long> g_launches{0};
@@ -374,7 +459,10 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     const long long n = A.nrows;
     if ((e = cudaMemsetAsync(Cp, 0, sizeof(long long), st))) return e;
     if (n == 0) return cudaSuccess;
-    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, sizeof(unsigned long long), st))) return e;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
+    const long long item_cap = split_item_capacity(A.nnz);
+    count_launch();
+    k_split_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A.rowptr, A.nnz, s.flops, s, item_cap);
     SymParams p;
     p.Ap = A.rowptr;
     p.Ai = A.col;
@@ -388,6 +476,8 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
     p.Cp_next = Cp + 1;
+    p.s = s;
+    p.item_cap = item_cap;
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)p.dw * cfg.warps_per_cta;
     const void* k;

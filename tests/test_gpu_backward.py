@@ -125,3 +125,22 @@ def test_backward_full_size_sampled():
     idx = np.concatenate([np.arange(B.rowptr[k], B.rowptr[k + 1]) for k in krows])
     gB = dB.cpu().numpy()[idx]
     assert np.all(np.abs(gB - sB) <= REL * bB)
+
+
+def test_backward_split_rows():
+    n, d = 4000, 256
+    rng = np.random.default_rng(80)
+    rows = [np.arange(n), rng.choice(n, 2500, replace=False)]
+    rows += [rng.choice(n, size=int(rng.integers(0, 10)), replace=False) for _ in range(n - 2)]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.sort(r) for r in rows]).astype(np.int32)
+    from synth import CSR
+    A = CSR(n, n, rowptr, col, synth.uniform(col.size, 81))
+    B = synth.tall_skinny(n, d, 0.05, 82)
+    B.val = synth.normal(B.nnz, 83)
+    for t in (None, {"group": 1}, {"pack_b": 1}):
+        rp, ci, dC, dA, dB = _run(A, B, t, seed=4)
+        rA, bA, rB, bB = oracle.backward(A, B, rp, ci, dC.astype(np.float64))
+        assert np.all(np.abs(dA - rA) <= REL * bA)
+        assert np.all(np.abs(dB - rB) <= REL * bB)

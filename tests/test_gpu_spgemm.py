@@ -201,3 +201,35 @@ def test_autotune_keeps_results():
     assert best["col_tile"] % 32 == 0
     compare_full(C, A, B)
     compare_full(plan.forward(Ad, Bd), A, B)
+
+
+@pytest.mark.parametrize("tuning", [None, {"col_tile": 256}, {"col_tile": 256, "group": 1}, {"pack_b": 1}])
+def test_split_rows_with_tiles(tuning):
+    # rows longer than 1024 entries of A are cut into parts processed by
+    # different blocks and merged through a staging row; with d = 1024 and
+    # 256-wide tiles every part adds four tiles
+    n, d = 5000, 1024
+    rng = np.random.default_rng(70)
+    rows = [np.arange(n), rng.choice(n, 3000, replace=False), np.arange(0, n, 2)]
+    rows += [rng.choice(n, size=int(rng.integers(0, 12)), replace=False) for _ in range(n - 3)]
+    A = _csr(n, n, rows, seed=71)
+    B = synth.tall_skinny(n, d, 0.01, 72)
+    B.val = synth.normal(B.nnz, 73)
+    compare_full(spgemm(dev(A), dev(B), tuning=tuning), A, B)
+    Cb = spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=tuning)
+    compare_full(Cb, A, B, semiring=oracle.OR_SELECT2ND)
+
+
+def test_more_long_rows_than_split_slots():
+    # 8300 rows of 1100 entries: more long rows than the 8192 split slots, so
+    # some run as whole rows
+    n, d, per = 8300, 32, 1100
+    rng = np.random.default_rng(74)
+    col = np.sort(np.stack([rng.choice(n, per, replace=False) for _ in range(n)]), axis=1)
+    A = CSR(n, n, np.arange(n + 1, dtype=np.int64) * per, col.reshape(-1).astype(np.int32),
+            synth.uniform(n * per, 75))
+    B = synth.tall_skinny(n, d, 1.0 / 32, 76)
+    B.val = synth.uniform(B.nnz, 77)
+    C = spgemm(dev(A), dev(B))
+    rng2 = np.random.default_rng(1)
+    compare_rows(C, A, B, rng2.choice(n, 400, replace=False))
