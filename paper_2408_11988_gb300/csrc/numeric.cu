@@ -342,12 +342,15 @@ __global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
     BA ba;
     if constexpr (PACKED) ba = BPacked{p.Bpk};
     else ba = BSep{p.Bi, VALUES ? p.Bx : nullptr};
-    const long long* mark = p.s.flops;
+    // without a staging area (d above the dense staging width) split rows are
+    // processed whole like any other row
+    const bool split_ok = p.s.stg_vals != nullptr;
+    const long long* mark = split_ok ? p.s.flops : nullptr;
     {
         float* acc = reinterpret_cast<float*>(smem);
         unsigned char* flg = smem + (VALUES ? 4 * p.W : 0);
         // parts of split rows first (any block), then whole heavy rows
-        const long long nitems = min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap);
+        const long long nitems = split_ok ? min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap) : 0;
         __shared__ int s_last;
         SplitItem it;
         while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it))
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
             __syncthreads();
             if (h >= nheavy) break;
             const int row = p.perm[h];
-            if (is_split_row(mark, row, __ldg(p.Ap + row + 1) - __ldg(p.Ap + row))) continue;
+            if (mark && is_split_row(mark, row, __ldg(p.Ap + row + 1) - __ldg(p.Ap + row))) continue;
             numeric_row_cta<VALUES, G, BA>(p, ba, row, acc, flg, s_wcnt);
         }
     }
@@ -432,7 +435,6 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
-    if (s.dpad > MAX_DENSE_W || !s.stg_vals) return cudaErrorInvalidValue;
     NumParams p;
     p.Ap = A.rowptr;
     p.Ai = A.col;
