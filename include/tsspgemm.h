@@ -96,6 +96,9 @@ typedef struct ts_csr_desc {
  *                 entry's row of B (best for rows of about that length).
  *  pack_b         1 = gather B from a packed (column, value) copy built in the
  *                 workspace at each call, 2 = from B's own arrays.
+ *  stage          1 = gather B's entries into shared memory with asynchronous
+ *                 copies, a window of 256 products per warp in flight (implies
+ *                 pack_b = 1 for plus-times); 2 = load them into registers.
  */
 typedef struct ts_tuning {
     int32_t accum;
@@ -105,6 +108,7 @@ typedef struct ts_tuning {
     int32_t hash_slots;
     int32_t group;
     int32_t pack_b;
+    int32_t stage;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;

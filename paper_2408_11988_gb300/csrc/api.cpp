@@ -148,7 +148,10 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
     t.hash_slots = force.hash_slots ? force.hash_slots : 1024;
     t.group = force.group ? force.group : auto_group(nB, nnzB);
-    t.pack_b = force.pack_b ? force.pack_b : 2;
+    t.stage = force.stage ? force.stage : 1;
+    t.pack_b = force.pack_b ? force.pack_b : (t.stage == 1 ? 1 : 2);
+    if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
+    if (t.stage == 1) t.pack_b = 1;
     if (t.group != 1 && t.group != 4 && t.group != 8 && t.group != 16 && t.group != 32)
         return fail(TS_ERR_INVALID_ARG, "tuning: group must be 1, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
@@ -403,9 +406,15 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
             bpk = (int2*)((char*)ws + L.bpk);
             TS_CUDA(launch_pack_b(dB, bpk, st), fn);
         }
-        TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, cfg,
-                                     (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
-                fn);
+        if (plan->cur.stage == 1 && numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024 &&
+            (!vals || bpk || B->nnz == 0)) {
+            TS_CUDA(launch_numeric_staged(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                    fn);
+        } else {
+            TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, cfg,
+                                         (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                    fn);
+        }
     } else {
         TS_CUDA(launch_numeric_hash(dA, dB, plan->d, plan->cur.hash_slots, vals, sc, cfg,
                                     (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
@@ -546,7 +555,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         if (w <= dpad && w >= std::max<long long>(64, round_up(dpad / 8, 32))) tiles.push_back(w);
     if (tiles.empty() || tiles.back() < std::min<long long>(dpad, 4096))
         tiles.push_back((int)std::min<long long>(dpad, 4096));
-    for (int field = 0; field < 6 && s == TS_OK; ++field) {
+    for (int field = 0; field < 7 && s == TS_OK; ++field) {
         std::vector<ts_tuning> cands;
         ts_tuning c = best;
         switch (field) {
@@ -573,6 +582,10 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
             case 5:
                 if (plan->force.warps_per_cta) break;
                 for (int w : {2, 4, 8}) { c.warps_per_cta = w; cands.push_back(c); }
+                break;
+            case 6:
+                if (plan->force.stage) break;
+                for (int sg : {1, 2}) { c.stage = sg; c.pack_b = sg == 1 ? 1 : best.pack_b; cands.push_back(c); }
                 break;
         }
         for (const ts_tuning& cand : cands) {

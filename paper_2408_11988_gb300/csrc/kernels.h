@@ -79,6 +79,12 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
                                  const long long* tp, bool values, const int2* Bpk, int G,
                                  const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,
                                  float* Cx, long long nnzC, cudaStream_t st);
+// Numeric pass with the dense accumulator and cp.async staging of B.
+cudaError_t launch_numeric_staged(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                  const long long* tp, bool values, const int2* Bpk, const Sched& s,
+                                  const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
+                                  cudaStream_t st);
+size_t numeric_staged_smem(int W, int warps, bool values);
 // Packed (column, value bits) copy of B's entries.
 cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st);
 

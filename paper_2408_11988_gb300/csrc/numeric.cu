@@ -13,6 +13,7 @@
 // B is read from its two arrays or from a packed (column, value) copy.
 #include "common.cuh"
 #include "kernels.h"
+#include "staged.cuh"
 
 namespace ts {
 
@@ -464,6 +465,335 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
         return launch_g<true, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
     }
     return launch_g<false, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
+}
+
+}  // namespace ts
+
+// ===========================================================================
+// Staged numeric pass: the same dense accumulator and read-out, with B's
+// entries gathered into shared memory by cp.async windows (staged.cuh).
+// ===========================================================================
+namespace ts {
+
+// A window whose copies are in flight, with what to do after it.
+struct Pending {
+    int buf;
+    int m;
+    int row;   // -1: no window
+    int tile;
+    bool last_of_tile;
+    bool last_of_row;
+    long long out, out_end;
+};
+
+template <bool VALUES>
+__device__ __forceinline__ void process_window(const StageArea<VALUES ? 8 : 4>& sa, int b, int m, float* acc,
+                                               unsigned char* flg, int d, int c0, int W, unsigned long long* err) {
+    const int lane = lane_id();
+    const unsigned char* own = sa.owner(b);
+    const float* av = sa.avals(b);
+#pragma unroll 4
+    for (int k = 0; k < STAGE_P / 32; ++k) {
+        const int s = lane + 32 * k;
+        if (s < m) {
+            int c;
+            float v = 0.0f;
+            if (VALUES) {
+                const int2 e = reinterpret_cast<const int2*>(sa.payload(b))[s];
+                c = e.x;
+                v = av[own[s]] * __int_as_float(e.y);
+            } else {
+                c = reinterpret_cast<const int*>(sa.payload(b))[s];
+            }
+            const int lc = c - c0;
+            if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
+                flg[lc] = 1;
+                if (VALUES) atomicAdd(acc + lc, v);
+            } else {
+                atomicOr(err, ERR_B_COL);
+            }
+        }
+    }
+}
+
+// Every window of entries [e0, e1) (this warp's chunks, stride `stride`) of
+// tile t accumulated into acc/flg; no read-out.  Used by block rows.
+template <bool VALUES, class Seg>
+__device__ __forceinline__ void staged_range(const NumParams& p, const StageArea<VALUES ? 8 : 4>& sa, long long e0,
+                                             long long e1, long long stride, const Seg& seg, int t, float* acc,
+                                             unsigned char* flg) {
+    unsigned long long* err = &p.hdr->err;
+    const void* src = VALUES ? (const void*)p.Bpk : (const void*)p.Bi;
+    const float* Ax = VALUES ? p.Ax : nullptr;
+    int buf = 0, pbuf = -1, pm = 0;
+    for (long long c = e0; c < e1; c += stride) {
+        const int nv = (int)(e1 - c < 32 ? e1 - c : 32);
+        const Chunk ch = load_chunk(c, nv, p.Ai, Ax, p.nB, seg, err);
+        const ChunkScan cs = scan_chunk(ch);
+        for (int p0 = 0; p0 < cs.total; p0 += STAGE_P) {
+            const int m = stage_issue(sa, buf, ch, cs, p0, src);
+            if (pbuf >= 0) {
+                cp_async_wait<1>();
+                __syncwarp();
+                process_window<VALUES>(sa, pbuf, pm, acc, flg, p.d, t * p.W, p.W, err);
+            }
+            pbuf = buf;
+            pm = m;
+            buf ^= 1;
+        }
+    }
+    if (pbuf >= 0) {
+        cp_async_wait<0>();
+        __syncwarp();
+        process_window<VALUES>(sa, pbuf, pm, acc, flg, p.d, t * p.W, p.W, err);
+    }
+}
+
+template <bool VALUES>
+__device__ __forceinline__ void staged_row_cta(const NumParams& p, const StageArea<VALUES ? 8 : 4>& sa, int row,
+                                               long long a0, long long a1, float* acc, unsigned char* flg,
+                                               int* wcnt) {
+    unsigned long long* err = &p.hdr->err;
+    long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+    const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+    const long long first = a0 + 32LL * warp_id(), stride = 32LL * (blockDim.x >> 5);
+    for (int t = 0; t < p.T; ++t) {
+        if (p.T == 1) staged_range<VALUES>(p, sa, first, a1, stride, SegWhole{p.Bp, p.nnzB, p.d}, t, acc, flg);
+        else staged_range<VALUES>(p, sa, first, a1, stride, SegTile{p.tp, p.T + 1, t, p.W}, t, acc, flg);
+        __syncthreads();
+        cta_emit<VALUES>(acc, flg, p.W, t * p.W, out, out_end, p.Ci, p.Cx, wcnt, err);
+    }
+    if (out != out_end && threadIdx.x == 0) atomicOr(err, ERR_C_ROW);
+}
+
+template <bool VALUES>
+__device__ __forceinline__ void staged_split_part(const NumParams& p, const StageArea<VALUES ? 8 : 4>& sa,
+                                                  const SplitItem& it, float* acc, unsigned char* flg, int* wcnt,
+                                                  int* s_last) {
+    unsigned long long* err = &p.hdr->err;
+    float* sv = p.s.stg_vals + (size_t)it.slot * p.s.dpad;
+    unsigned char* sf = p.s.stg_flags + (size_t)it.slot * p.s.dpad;
+    const long long first = it.e0 + 32LL * warp_id(), stride = 32LL * (blockDim.x >> 5);
+    for (int t = 0; t < p.T; ++t) {
+        if (p.T == 1) staged_range<VALUES>(p, sa, first, it.e1, stride, SegWhole{p.Bp, p.nnzB, p.d}, t, acc, flg);
+        else staged_range<VALUES>(p, sa, first, it.e1, stride, SegTile{p.tp, p.T + 1, t, p.W}, t, acc, flg);
+        __syncthreads();
+        for (int c = threadIdx.x; c < p.W; c += blockDim.x) {
+            if (flg[c]) {
+                if (VALUES) {
+                    atomicAdd(sv + t * p.W + c, acc[c]);
+                    acc[c] = 0.0f;
+                }
+                sf[t * p.W + c] = 1;
+                flg[c] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    if (!split_part_done(p.s, it.slot, it.nsub, s_last)) return;
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    const int words = p.s.dpad >> 5;
+    const unsigned lt = lanemask_lt();
+    long long out = clampll(__ldg(p.Cp + it.row), 0, p.nnzC);
+    const long long out_end = clampll(__ldg(p.Cp + it.row + 1), out, p.nnzC);
+    for (int w = warp; w < words; w += nw) {
+        const unsigned bal = __ballot_sync(FULL, __ldcg(sf + w * 32 + lane) != 0);
+        if (lane == 0) wcnt[w] = __popc(bal);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int tot = warp_excl_scan_smem(wcnt, words);
+        if (lane == 0) wcnt[words] = tot;
+    }
+    __syncthreads();
+    for (int w = warp; w < words; w += nw) {
+        const int c = w * 32 + lane;
+        const bool f = __ldcg(sf + c) != 0;
+        const unsigned bal = __ballot_sync(FULL, f);
+        if (f) {
+            const long long pos = out + wcnt[w] + __popc(bal & lt);
+            if (pos < out_end) {
+                p.Ci[pos] = c;
+                if (VALUES) p.Cx[pos] = __ldcg(sv + c);
+            } else {
+                atomicOr(err, ERR_C_ROW);
+            }
+            if (VALUES) sv[c] = 0.0f;
+            sf[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (out + wcnt[words] != out_end) atomicOr(err, ERR_C_ROW);
+        p.s.split_done[it.slot] = 0;
+    }
+    __syncthreads();
+}
+
+// Light rows of one warp: windows of consecutive rows flow through the two
+// buffers; a row's read-out happens when its last window has been
+// processed, while the next row's first window is already in flight.
+template <bool VALUES>
+__device__ __forceinline__ void staged_light_rows(const NumParams& p, const StageArea<VALUES ? 8 : 4>& sa,
+                                                  float* acc, unsigned char* flg, long long idx0, long long end,
+                                                  long long step, const long long* mark) {
+    unsigned long long* err = &p.hdr->err;
+    const void* src = VALUES ? (const void*)p.Bpk : (const void*)p.Bi;
+    const float* Ax = VALUES ? p.Ax : nullptr;
+    Pending pend;
+    pend.row = -1;
+    int buf = 0;
+    long long out = 0, out_end = 0;  // read-out cursor of the row being processed
+    int cur = -1;
+    auto finish_pending = [&](bool all) {
+        if (pend.row < 0) return;
+        if (all) cp_async_wait<0>();
+        else cp_async_wait<1>();
+        __syncwarp();
+        if (pend.row != cur) {
+            cur = pend.row;
+            out = pend.out;
+            out_end = pend.out_end;
+        }
+        process_window<VALUES>(sa, pend.buf, pend.m, acc, flg, p.d, pend.tile * p.W, p.W, err);
+        if (pend.last_of_tile) {
+            __syncwarp();
+            warp_emit4<VALUES>(acc, flg, p.W, pend.tile * p.W, out, out_end, p.Ci, p.Cx, err);
+            __syncwarp();
+            if (pend.last_of_row && out != out_end && lane_id() == 0) atomicOr(err, ERR_C_ROW);
+        }
+        pend.row = -1;
+    };
+    int nrow = idx0 < end ? __ldg(p.perm + idx0) : 0;
+    for (long long idx = idx0; idx < end; idx += step) {
+        const int row = nrow;
+        if (idx + step < end) nrow = __ldg(p.perm + idx + step);  // one row ahead
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        if (mark && is_split_row(mark, row, a1 - a0)) continue;
+        const long long o0 = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+        const long long o1 = clampll(__ldg(p.Cp + row + 1), o0, p.nnzC);
+        for (int t = 0; t < p.T; ++t) {
+            for (long long c = a0; c < a1; c += 32) {
+                const int nv = (int)(a1 - c < 32 ? a1 - c : 32);
+                const Chunk ch = (p.T == 1) ? load_chunk(c, nv, p.Ai, Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, err)
+                                            : load_chunk(c, nv, p.Ai, Ax, p.nB, SegTile{p.tp, p.T + 1, t, p.W}, err);
+                const ChunkScan cs = scan_chunk(ch);
+                const bool last_chunk = c + 32 >= a1;
+                int p0 = 0;
+                do {  // an empty chunk still issues one (empty) window so that read-outs stay in order
+                    const int m = stage_issue(sa, buf, ch, cs, p0, src);
+                    const bool last_win = p0 + STAGE_P >= cs.total;
+                    finish_pending(false);
+                    pend = Pending{buf, m, row, t, last_chunk && last_win, last_chunk && last_win && t + 1 == p.T,
+                                   o0, o1};
+                    buf ^= 1;
+                    p0 += STAGE_P;
+                } while (p0 < cs.total);
+            }
+        }
+    }
+    finish_pending(true);
+}
+
+template <bool VALUES>
+__global__ void __launch_bounds__(256, 4) k_numeric_staged(NumParams p) {
+    constexpr int E = VALUES ? 8 : 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
+    __shared__ long long s_item, s_nheavy, s_nrows;
+    const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
+    const int slot = VALUES ? 5 * p.W : p.W;
+    // layout: [nw][slot] accumulators, then [nw] staging areas
+    for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
+    const StageArea<E> sa{smem + (size_t)nw * slot + (size_t)warp * StageArea<E>::BYTES};
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    const long long nheavy = s_nheavy, nrows = s_nrows;
+    const bool split_ok = p.s.stg_vals != nullptr;
+    const long long* mark = split_ok ? p.s.flops : nullptr;
+    {
+        float* acc = reinterpret_cast<float*>(smem);
+        unsigned char* flg = smem + (VALUES ? 4 * p.W : 0);
+        const long long nitems = split_ok ? min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap) : 0;
+        __shared__ int s_last;
+        SplitItem it;
+        while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it))
+            staged_split_part<VALUES>(p, sa, it, acc, flg, s_wcnt, &s_last);
+        for (;;) {
+            if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
+            __syncthreads();
+            const long long h = s_item;
+            __syncthreads();
+            if (h >= nheavy) break;
+            const int row = p.perm[h];
+            const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+            const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+            if (mark && is_split_row(mark, row, a1 - a0)) continue;
+            staged_row_cta<VALUES>(p, sa, row, a0, a1, acc, flg, s_wcnt);
+        }
+    }
+    float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
+    unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
+    staged_light_rows<VALUES>(p, sa, acc, flg, nheavy + (long long)blockIdx.x * nw + warp, nrows,
+                              (long long)gridDim.x * nw, mark);
+}
+
+size_t numeric_staged_smem(int W, int warps, bool values) {
+    return numeric_dense_smem(W, warps, values) +
+           (size_t)warps * (values ? StageArea<8>::BYTES : StageArea<4>::BYTES);
+}
+
+cudaError_t launch_numeric_staged(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                  const long long* tp, bool values, const int2* Bpk, const Sched& s,
+                                  const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
+                                  cudaStream_t st) {
+    cudaError_t e;
+    if (A.nrows == 0) return cudaSuccess;
+    if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
+    if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
+    if (values && !Bpk && B.nnz > 0) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
+    NumParams p;
+    p.Ap = A.rowptr;
+    p.Ai = A.col;
+    p.Ax = A.val;
+    p.nnzA = A.nnz;
+    p.Bp = B.rowptr;
+    p.Bi = B.col;
+    p.Bx = B.val;
+    p.Bpk = Bpk;
+    p.nnzB = B.nnz;
+    p.nB = (int)B.nrows;
+    p.d = (int)d;
+    p.W = W;
+    p.T = T;
+    p.tp = tp;
+    p.perm = s.perm;
+    p.hdr = s.hdr;
+    p.cta_class = cfg.cta_class;
+    p.Cp = Cp;
+    p.Ci = Ci;
+    p.Cx = Cx;
+    p.nnzC = nnzC;
+    p.s = s;
+    p.item_cap = split_item_capacity(A.nnz);
+    const int warps = cfg.warps_per_cta;
+    const size_t smem = numeric_staged_smem(W, warps, values);
+    const void* k = values ? (const void*)k_numeric_staged<true> : (const void*)k_numeric_staged<false>;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid(k, 32 * warps, smem, cfg.sms);
+    void* args[] = {&p};
+    count_launch();
+    return cudaLaunchKernel(k, dim3(grid), dim3(32 * warps), args, smem, st);
 }
 
 }  // namespace ts

@@ -41,7 +41,7 @@ def test_host_side_errors(lib):
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 7, None, ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
     Bbig = N.CsrDesc(100, 1 << 21, 0, 8, None, None)
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(Bbig), 0, None, ctypes.byref(h)) == N.TS_ERR_UNSUPPORTED
-    bad_t = N.Tuning(0, 48, 0, 0, 0, 0, 0)
+    bad_t = N.Tuning(0, 48, 0, 0, 0, 0, 0, 0)
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bad_t), ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, None, ctypes.byref(h)) == N.TS_OK
     t = N.Tuning()

@@ -30,9 +30,11 @@ TUNINGS = [
     {"cta_min_flops": 64},
     {"warps_per_cta": 1},
     {"warps_per_cta": 8, "cta_min_flops": 16},
-    {"group": 1},                              # flattened products
-    {"group": 4}, {"group": 16}, {"group": 32, "cta_min_flops": 32},
-    {"pack_b": 1}, {"pack_b": 1, "group": 1, "col_tile": 32}, {"pack_b": 1, "cta_min_flops": 1},
+    {"stage": 2},                              # direct gathers (no cp.async staging)
+    {"stage": 2, "group": 1},                  # flattened products
+    {"stage": 2, "group": 4}, {"stage": 2, "group": 16}, {"stage": 2, "group": 32, "cta_min_flops": 32},
+    {"stage": 2, "pack_b": 1}, {"stage": 2, "pack_b": 1, "group": 1, "col_tile": 32},
+    {"stage": 2, "pack_b": 1, "cta_min_flops": 1}, {"col_tile": 32, "cta_min_flops": 1},
     {"accum": ACC_HASH, "hash_slots": 128},
     {"accum": ACC_HASH, "hash_slots": 1024, "warps_per_cta": 4},
 ]
@@ -52,7 +54,7 @@ def test_er_full_size(er_case, tuning):
 
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH},
-                                    {"group": 1}, {"group": 32}])
+                                    {"stage": 2, "group": 1}, {"stage": 2, "group": 32}])
 def test_er_boolean(er_case, tuning):
     A, B = er_case
     C = spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=tuning)
@@ -61,8 +63,9 @@ def test_er_boolean(er_case, tuning):
 
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 64}, {"col_tile": 96}, {"cta_min_flops": 128},
-                                    {"accum": ACC_HASH, "hash_slots": 512}, {"group": 1}, {"group": 8},
-                                    {"group": 32, "pack_b": 1}, {"pack_b": 1, "col_tile": 64}])
+                                    {"accum": ACC_HASH, "hash_slots": 512}, {"stage": 2, "group": 1},
+                                    {"stage": 2, "group": 8}, {"stage": 2, "group": 32, "pack_b": 1},
+                                    {"stage": 2, "pack_b": 1, "col_tile": 64}, {"col_tile": 64, "warps_per_cta": 2}])
 def test_rmat_embedding_small(tuning):
     A, B = synth.rmat_embedding(scale=13, edge_factor=16, d=256, density=0.05, seed=31)
     C = spgemm(dev(A), dev(B), tuning=tuning)
@@ -104,7 +107,8 @@ def test_small_shapes_and_ragged_d(n, d):
     A = _csr(n, n, [rng.choice(n, size=rng.integers(0, n + 1), replace=False) for _ in range(n)], seed=1)
     B = _csr(n, d, [rng.choice(d, size=rng.integers(0, d + 1), replace=False) for _ in range(n)], seed=2)
     for t in (None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH, "hash_slots": 256},
-              {"group": 1}, {"group": 4, "pack_b": 1}, {"group": 32, "cta_min_flops": 1}):
+              {"stage": 2, "group": 1}, {"stage": 2, "group": 4, "pack_b": 1},
+              {"stage": 2, "group": 32, "cta_min_flops": 1}, {"warps_per_cta": 1}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -138,7 +142,8 @@ def test_hub_row_and_dense_b():
     A = _csr(n, n, rows, seed=10)                  # row 0 touches every row of B
     B = synth.tall_skinny(n, d, 1.0, 11)           # fully dense rows
     B.val = synth.uniform(B.nnz, 12)
-    for t in (None, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 2}, {"group": 1}, {"group": 32}):
+    for t in (None, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 2}, {"stage": 2, "group": 1},
+              {"stage": 2, "group": 32}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -203,7 +208,8 @@ def test_autotune_keeps_results():
     compare_full(plan.forward(Ad, Bd), A, B)
 
 
-@pytest.mark.parametrize("tuning", [None, {"col_tile": 256}, {"col_tile": 256, "group": 1}, {"pack_b": 1}])
+@pytest.mark.parametrize("tuning", [None, {"col_tile": 256}, {"col_tile": 256, "stage": 2, "group": 1},
+                                    {"stage": 2, "pack_b": 1}, {"stage": 2}])
 def test_split_rows_with_tiles(tuning):
     # rows longer than 1024 entries of A are cut into parts processed by
     # different blocks and merged through a staging row; with d = 1024 and
