@@ -131,11 +131,11 @@ static const long long MAX_D = 1LL << 20;
 // Lanes per A entry: the power of two at or above the mean row length of B,
 // in [4, 32]; rows of fewer than 3 entries on average use the flattened mode.
 static int auto_group(long long nB, long long nnzB) {
+    // measured: the flattened distribution is at least as fast as lane groups
+    // for rows of B up to ~16 entries; groups only pay off for long rows
     const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
-    if (avg < 3.0) return 1;
-    int g = 4;
-    while (g < 32 && g < avg) g *= 2;
-    return g;
+    if (avg < 24.0) return 1;
+    return 32;
 }
 
 static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t,
@@ -148,8 +148,8 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
     t.hash_slots = force.hash_slots ? force.hash_slots : 1024;
     t.group = force.group ? force.group : auto_group(nB, nnzB);
-    t.stage = force.stage ? force.stage : 1;
-    t.pack_b = force.pack_b ? force.pack_b : (t.stage == 1 ? 1 : 2);
+    t.stage = force.stage ? force.stage : 2;
+    t.pack_b = force.pack_b ? force.pack_b : 1;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
     if (t.group != 1 && t.group != 4 && t.group != 8 && t.group != 16 && t.group != 32)
