@@ -297,6 +297,36 @@ TS_API ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count
                                      float* const* dB_val, void* ws, size_t ws_bytes,
                                      void* stream);
 
+/*
+ * Forward product that allocates nothing (the paper has no counterpart; this
+ * is a service for callers).  Some callers cannot allocate device memory when
+ * they need a product: code running inside another framework's memory pool
+ * or under a fixed memory budget, serving loops that must not call cudaMalloc
+ * (it can synchronise the whole device), or code run from a callback where
+ * allocation is not allowed.  This call runs the symbolic and numeric passes
+ * with scratch space taken from a fixed array compiled into the library
+ * (ts_noalloc_scratch_bytes(), 32 MiB, held by every GPU that loads the
+ * library until the process exits) instead of a caller workspace.
+ *
+ * The caller passes A, B and C as for the other calls: C->rowptr (n+1 int64)
+ * and C->col / C->val with room for C->nnz entries (the capacity).  On return
+ * *nnzC_host holds nnz(C); if it exceeds the capacity the call returns
+ * TS_ERR_CAPACITY after writing C->rowptr only.  Products whose workspace
+ * (ts_workspace_size) exceeds the scratch are rejected with TS_ERR_UNSUPPORTED
+ * before anything is enqueued.  The call synchronises `stream` once (to read
+ * nnz(C)) and calls no allocating function.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array and each call re-initialises what it needs, so calls whose work
+ * overlaps on the GPU (different streams, different threads) race: serialise
+ * them.
+ */
+TS_API size_t ts_noalloc_scratch_bytes(void);
+TS_API ts_status ts_spgemm_forward_noalloc(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
+                                           const ts_csr_desc* C, int64_t* nnzC_host, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

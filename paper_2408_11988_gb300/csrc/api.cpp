@@ -47,6 +47,14 @@ static ts_status ok() {
 
 extern "C" const char* ts_last_error(void) { return g_last_error.c_str(); }
 
+// Lets other translation units of the library report an error message.
+namespace ts {
+ts_status set_last_error(ts_status s, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return s;
+}
+}  // namespace ts
+
 extern "C" const char* ts_status_string(ts_status s) {
     switch (s) {
         case TS_OK: return "TS_OK";
