@@ -262,40 +262,57 @@ TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, 
                      size_t ws_bytes, void* stream);
 
 /*
- * Batched products: `count` independent C_b = A_b * B_b of uneven shapes in
- * one launch per phase, graph capturable.
+ * Batched products: `count` independent C_b = A_b * B_b of uneven shapes,
+ * each phase one launch over all instances, graph capturable.  The batch is
+ * computed as the one product of the block-diagonal matrix diag(A_1..A_m)
+ * with the stacked [B_1; ...; B_m] (row block b of it is C_b): the instances
+ * are gathered into the workspace, the single-product passes run once, and
+ * the rows are scattered back into each instance's C.
  *
- * ts_batched_plan_create reads the shapes and patterns' sizes (host side) and
- * picks, per instance, the accumulator width and row-bin threshold (unless
- * `force` fixes them).  ts_batched_bounds gives, per instance, an upper bound
- * on nnz(C_b) (sum over rows of min(d_b, nnz(A_b row) * max nnz(B_b row)),
- * computed on the device from the patterns, synchronises) for allocating C.
- * ts_batched_bind uploads the descriptors (A, B, C arrays of `count` host
- * descriptors with device pointers; C_b.rowptr has n_b+1 entries and
- * C_b.col/val the bound's capacity) into ws; it synchronises.
- * ts_spgemm_batched then runs every product without any host synchronisation
- * or allocation, so it can be captured in a CUDA graph and replayed; after
- * it, C_b.rowptr is the exact structure and nnz(C_b) = C_b.rowptr[n_b].
- * The descriptor arrays passed to it must equal those bound (checked on the
- * host).  ts_spgemm_batched_backward is the batched ts_spgemm_backward
- * (gradient arrays are per instance; NULL entries skip that output).
+ * Protocol (descriptor arrays are host arrays of `count` descriptors with
+ * device pointers):
+ *  1. ts_batched_plan_create reads shapes and nnz only (host).  `force` fixes
+ *     tuning fields of the concatenated product (NULL: automatic).
+ *  2. ts_batched_workspace_size, then ts_batched_bounds: computes, on the
+ *     device, C_capacity[b] = sum over the rows of A_b of min(d_b, flops_i),
+ *     an upper bound on nnz(C_b) (synchronises).  The bounds enlarge the
+ *     workspace: query ts_batched_workspace_size again afterwards.
+ *  3. ts_batched_bind: the caller allocates C_b (rowptr n_b+1, col/val with
+ *     C_b.nnz >= C_capacity[b]) and binds A, B, C (uploads the descriptors,
+ *     synchronises).  ts_batched_bind_grads binds per-instance dC (nnz(C_b)
+ *     entries), dA (nnz(A_b)) and dB (nnz(B_b)) arrays; NULL entries skip an
+ *     output.
+ *  4. ts_spgemm_batched / ts_spgemm_batched_backward: no host
+ *     synchronisation and no allocation, so they can be captured in a CUDA
+ *     graph and replayed.  The descriptor / gradient arrays passed must equal
+ *     those bound (checked on the host).  After the forward, C_b.rowptr holds
+ *     the exact structure and nnz(C_b) = C_b.rowptr[n_b]; an instance whose C
+ *     exceeds its capacity keeps only its rowptr and the error is reported by
+ *     ts_batched_check.  The backward uses the C pattern of the preceding
+ *     forward.
+ *  ts_batched_check synchronises and reports device-side errors;
+ *  ts_batched_autotune tunes the concatenated product on the bound data.
  */
 TS_API ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A, const ts_csr_desc* B,
-                                 int32_t semiring, const ts_tuning* force,
-                                 ts_batched_plan** out);
+                                        int32_t semiring, const ts_tuning* force, ts_batched_plan** out);
 TS_API ts_status ts_batched_plan_destroy(ts_batched_plan* plan);
 TS_API ts_status ts_batched_workspace_size(const ts_batched_plan* plan, size_t* bytes);
 TS_API ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
-                            int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream);
+                                   int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream);
 TS_API ts_status ts_batched_bind(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
-                          const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream);
+                                 const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream);
+TS_API ts_status ts_batched_bind_grads(ts_batched_plan* plan, int32_t count, const float* const* dC_val,
+                                       float* const* dA_val, float* const* dB_val, void* ws, size_t ws_bytes,
+                                       void* stream);
 TS_API ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, const ts_csr_desc* A,
-                            const ts_csr_desc* B, const ts_csr_desc* C, void* ws,
-                            size_t ws_bytes, void* stream);
-TS_API ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count,
-                                     const float* const* dC_val, float* const* dA_val,
-                                     float* const* dB_val, void* ws, size_t ws_bytes,
-                                     void* stream);
+                                   const ts_csr_desc* B, const ts_csr_desc* C, void* ws, size_t ws_bytes,
+                                   void* stream);
+TS_API ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count, const float* const* dC_val,
+                                            float* const* dA_val, float* const* dB_val, void* ws,
+                                            size_t ws_bytes, void* stream);
+TS_API ts_status ts_batched_check(ts_batched_plan* plan, void* ws, size_t ws_bytes, void* stream);
+TS_API ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tuning* chosen, void* ws,
+                                     size_t ws_bytes, void* stream);
 
 /*
  * Forward product that allocates nothing (the paper has no counterpart; this

@@ -767,47 +767,367 @@ extern "C" ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capaci
 }
 
 // ---------------------------------------------------------------------------
-// batched products (filled in by batched.cu's launchers)
+// batched products: the block-diagonal concatenation as one product
 // ---------------------------------------------------------------------------
 struct ts_batched_plan {
     int count = 0;
+    int semiring = 0;
+    std::vector<long long> n, d, annz, bnnz, row_off, annz_off, bnnz_off, cap;
+    long long N = 0, D = 0, NNZA = 0, NNZB = 0, CAP = 0;
+    long long max_rows = 0, max_annz = 0, max_bnnz = 0, max_cap = 0;
+    ts_plan* inner = nullptr;
+    bool have_bounds = false;
+    bool bound = false;
+    std::vector<ts_csr_desc> bA, bB, bC;
+    std::vector<const float*> gdC;
+    std::vector<float*> gdA, gdB;
+    bool grads = false;
+    ~ts_batched_plan() { delete inner; }
 };
+
+struct BLayout {
+    size_t inst = 0, bound = 0, Ap = 0, Ai = 0, Ax = 0, Bp = 0, Bi = 0, Bx = 0, Cp = 0, Ci = 0, Cx = 0;
+    size_t dC = 0, dA = 0, dB = 0, inner = 0, inner_bytes = 0, total = 0;
+};
+
+static BLayout batched_layout(const ts_batched_plan* p) {
+    BLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const bool vals = p->semiring == TS_SR_PLUS_TIMES_F32;
+    L.inst = take(sizeof(InstDesc) * (size_t)p->count);
+    L.bound = take(sizeof(long long) * (size_t)p->count);
+    L.Ap = take(sizeof(long long) * (size_t)(p->N + 1));
+    L.Ai = take(sizeof(int) * (size_t)p->NNZA);
+    L.Ax = vals ? take(sizeof(float) * (size_t)p->NNZA) : 0;
+    L.Bp = take(sizeof(long long) * (size_t)(p->N + 1));
+    L.Bi = take(sizeof(int) * (size_t)p->NNZB);
+    L.Bx = vals ? take(sizeof(float) * (size_t)p->NNZB) : 0;
+    L.Cp = take(sizeof(long long) * (size_t)(p->N + 1));
+    L.Ci = take(sizeof(int) * (size_t)p->CAP);
+    L.Cx = vals ? take(sizeof(float) * (size_t)p->CAP) : 0;
+    if (vals) {
+        L.dC = take(sizeof(float) * (size_t)p->CAP);
+        L.dA = take(sizeof(float) * (size_t)p->NNZA);
+        L.dB = take(sizeof(float) * (size_t)p->NNZB);
+    }
+    size_t inner = 0;
+    ts_workspace_size(p->inner, &inner);
+    L.inner = take(inner);
+    L.inner_bytes = inner;
+    L.total = off;
+    return L;
+}
+
+static ts_csr_desc cat_desc(char* ws, const ts_batched_plan* p, const BLayout& L, char which) {
+    const bool vals = p->semiring == TS_SR_PLUS_TIMES_F32;
+    ts_csr_desc c{};
+    if (which == 'A') {
+        c = ts_csr_desc{p->N, p->N, p->NNZA, (int64_t*)(ws + L.Ap), (int32_t*)(ws + L.Ai),
+                        vals ? (void*)(ws + L.Ax) : nullptr};
+    } else if (which == 'B') {
+        c = ts_csr_desc{p->N, p->D, p->NNZB, (int64_t*)(ws + L.Bp), (int32_t*)(ws + L.Bi),
+                        vals ? (void*)(ws + L.Bx) : nullptr};
+    } else {
+        c = ts_csr_desc{p->N, p->D, p->CAP, (int64_t*)(ws + L.Cp), (int32_t*)(ws + L.Ci),
+                        vals ? (void*)(ws + L.Cx) : nullptr};
+    }
+    return c;
+}
+
+static ts_status batched_ws_check(const ts_batched_plan* p, void* ws, size_t ws_bytes, const BLayout& L,
+                                  const char* fn) {
+    if (!ws) return fail(TS_ERR_INVALID_ARG, "%s: workspace is NULL", fn);
+    if (((uintptr_t)ws) & 255) return fail(TS_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
+    if (ws_bytes < L.total)
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, L.total);
+    (void)p;
+    return TS_OK;
+}
+
+static ts_status upload_insts(ts_batched_plan* p, const ts_csr_desc* A, const ts_csr_desc* B,
+                              const ts_csr_desc* C, char* ws, const BLayout& L, cudaStream_t st, const char* fn) {
+    std::vector<InstDesc> h((size_t)p->count);
+    for (int b = 0; b < p->count; ++b) {
+        InstDesc& I = h[b];
+        I.n = p->n[b];
+        I.d = p->d[b];
+        I.annz = p->annz[b];
+        I.bnnz = p->bnnz[b];
+        I.cap = C ? C[b].nnz : 0;
+        I.row_off = p->row_off[b];
+        I.annz_off = p->annz_off[b];
+        I.bnnz_off = p->bnnz_off[b];
+        I.A_rowptr = (const long long*)A[b].rowptr;
+        I.A_col = A[b].col;
+        I.A_val = (const float*)A[b].val;
+        I.B_rowptr = (const long long*)B[b].rowptr;
+        I.B_col = B[b].col;
+        I.B_val = (const float*)B[b].val;
+        I.C_rowptr = C ? (long long*)C[b].rowptr : nullptr;
+        I.C_col = C ? C[b].col : nullptr;
+        I.C_val = C ? (float*)C[b].val : nullptr;
+        I.dC = p->grads ? p->gdC[b] : nullptr;
+        I.dA = p->grads ? p->gdA[b] : nullptr;
+        I.dB = p->grads ? p->gdB[b] : nullptr;
+    }
+    TS_CUDA(cudaMemcpyAsync(ws + L.inst, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    return TS_OK;
+}
 
 extern "C" ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A, const ts_csr_desc* B,
                                             int32_t semiring, const ts_tuning* force,
                                             ts_batched_plan** out) {
-    (void)count; (void)A; (void)B; (void)semiring; (void)force;
-    if (out) *out = nullptr;
-    return fail(TS_ERR_UNSUPPORTED, "ts_batched_plan_create: not built yet");
+    const char* fn = "ts_batched_plan_create";
+    if (!out) return fail(TS_ERR_INVALID_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    if (count < 1 || !A || !B) return fail(TS_ERR_INVALID_ARG, "%s: need count >= 1 and descriptor arrays", fn);
+    if (semiring != TS_SR_PLUS_TIMES_F32 && semiring != TS_SR_OR_SELECT2ND_BOOL)
+        return fail(TS_ERR_INVALID_ARG, "%s: unknown semiring %d", fn, semiring);
+    ts_batched_plan* p = new ts_batched_plan;
+    p->count = count;
+    p->semiring = semiring;
+    for (int b = 0; b < count; ++b) {
+        if (A[b].nrows < 0 || A[b].ncols != A[b].nrows || B[b].nrows != A[b].nrows || B[b].ncols < 1 ||
+            A[b].nnz < 0 || B[b].nnz < 0) {
+            delete p;
+            return fail(TS_ERR_INVALID_ARG, "%s: instance %d: A must be n x n and B n x d (d >= 1)", fn, b);
+        }
+        p->n.push_back(A[b].nrows);
+        p->d.push_back(B[b].ncols);
+        p->annz.push_back(A[b].nnz);
+        p->bnnz.push_back(B[b].nnz);
+        p->row_off.push_back(p->N);
+        p->annz_off.push_back(p->NNZA);
+        p->bnnz_off.push_back(p->NNZB);
+        p->N += A[b].nrows;
+        p->NNZA += A[b].nnz;
+        p->NNZB += B[b].nnz;
+        p->D = std::max<long long>(p->D, B[b].ncols);
+        p->max_rows = std::max<long long>(p->max_rows, A[b].nrows + 1);
+        p->max_annz = std::max<long long>(p->max_annz, A[b].nnz);
+        p->max_bnnz = std::max<long long>(p->max_bnnz, B[b].nnz);
+    }
+    if (p->N > INT32_MAX) {
+        delete p;
+        return fail(TS_ERR_UNSUPPORTED, "%s: more than 2^31-1 rows in total", fn);
+    }
+    p->cap.assign((size_t)count, 0);
+    const ts_csr_desc iA{p->N, p->N, p->NNZA, nullptr, nullptr, nullptr};
+    const ts_csr_desc iB{p->N, p->D, p->NNZB, nullptr, nullptr, nullptr};
+    ts_status s = ts_plan_create(&iA, &iB, semiring, force, &p->inner);
+    if (s != TS_OK) {
+        delete p;
+        return s;
+    }
+    *out = p;
+    return ok();
 }
+
 extern "C" ts_status ts_batched_plan_destroy(ts_batched_plan* plan) {
     delete plan;
     return ok();
 }
+
 extern "C" ts_status ts_batched_workspace_size(const ts_batched_plan* plan, size_t* bytes) {
-    (void)plan; (void)bytes;
-    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+    if (!plan || !bytes) return fail(TS_ERR_INVALID_ARG, "ts_batched_workspace_size: NULL argument");
+    *bytes = batched_layout(plan).total;
+    return ok();
 }
+
 extern "C" ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                        int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream) {
-    (void)plan; (void)A; (void)B; (void)C_capacity; (void)ws; (void)ws_bytes; (void)stream;
-    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+    const char* fn = "ts_batched_bounds";
+    if (!plan || !A || !B || !C_capacity) return fail(TS_ERR_INVALID_ARG, "%s: NULL argument", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    for (int b = 0; b < plan->count; ++b) {
+        if (A[b].nrows != plan->n[b] || A[b].nnz != plan->annz[b] || B[b].ncols != plan->d[b] ||
+            B[b].nnz != plan->bnnz[b])
+            return fail(TS_ERR_INVALID_ARG, "%s: instance %d differs from the plan", fn, b);
+        if ((s = check_desc(&A[b], "A", vals)) != TS_OK || (s = check_desc(&B[b], "B", vals)) != TS_OK) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    if ((s = upload_insts(plan, A, B, nullptr, w, L, st, fn)) != TS_OK) return s;
+    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B');
+    const InstDesc* inst = (const InstDesc*)(w + L.inst);
+    TS_CUDA(launch_batch_gather(inst, plan->count, std::max(plan->max_rows, std::max(plan->max_annz, plan->max_bnnz)),
+                                (long long*)cA.rowptr, cA.col, (float*)cA.val, (long long*)cB.rowptr, cB.col,
+                                (float*)cB.val, st),
+            fn);
+    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
+    const Sched sc = carve(w + L.inner, IL);
+    TS_CUDA(launch_row_flops(dev(&cA), dev(&cB), sc, st), fn);
+    TS_CUDA(launch_batch_bounds(inst, plan->count, sc.flops, (long long*)(w + L.bound), st), fn);
+    std::vector<long long> bnd((size_t)plan->count);
+    TS_CUDA(cudaMemcpyAsync(bnd.data(), w + L.bound, sizeof(long long) * bnd.size(), cudaMemcpyDeviceToHost, st), fn);
+    if ((s = read_errors(w + L.inner, IL, st, fn)) != TS_OK) return s;
+    plan->CAP = 0;
+    plan->max_cap = 0;
+    for (int b = 0; b < plan->count; ++b) {
+        plan->cap[b] = bnd[b];
+        C_capacity[b] = bnd[b];
+        plan->CAP += bnd[b];
+        plan->max_cap = std::max(plan->max_cap, bnd[b]);
+    }
+    plan->have_bounds = true;
+    plan->bound = false;
+    return ok();
 }
+
 extern "C" ts_status ts_batched_bind(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                      const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream) {
-    (void)plan; (void)A; (void)B; (void)C; (void)ws; (void)ws_bytes; (void)stream;
-    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+    const char* fn = "ts_batched_bind";
+    if (!plan || !A || !B || !C) return fail(TS_ERR_INVALID_ARG, "%s: NULL argument", fn);
+    if (!plan->have_bounds) return fail(TS_ERR_STATE, "%s: call ts_batched_bounds first", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    for (int b = 0; b < plan->count; ++b) {
+        if (A[b].nrows != plan->n[b] || A[b].nnz != plan->annz[b] || B[b].ncols != plan->d[b] ||
+            B[b].nnz != plan->bnnz[b])
+            return fail(TS_ERR_INVALID_ARG, "%s: instance %d differs from the plan", fn, b);
+        if ((s = check_desc(&A[b], "A", vals)) != TS_OK || (s = check_desc(&B[b], "B", vals)) != TS_OK) return s;
+        if (!C[b].rowptr || C[b].nrows != plan->n[b] || C[b].ncols != plan->d[b] ||
+            (C[b].nnz > 0 && (!C[b].col || (vals && !C[b].val))))
+            return fail(TS_ERR_INVALID_ARG, "%s: instance %d: bad C descriptor", fn, b);
+    }
+    plan->bA.assign(A, A + plan->count);
+    plan->bB.assign(B, B + plan->count);
+    plan->bC.assign(C, C + plan->count);
+    if ((s = upload_insts(plan, A, B, C, (char*)ws, L, (cudaStream_t)stream, fn)) != TS_OK) return s;
+    plan->bound = true;
+    return ok();
 }
+
+extern "C" ts_status ts_batched_bind_grads(ts_batched_plan* plan, int32_t count, const float* const* dC_val,
+                                           float* const* dA_val, float* const* dB_val, void* ws, size_t ws_bytes,
+                                           void* stream) {
+    const char* fn = "ts_batched_bind_grads";
+    if (!plan || !dC_val || count != plan->count) return fail(TS_ERR_INVALID_ARG, "%s: bad arguments", fn);
+    if (plan->semiring != TS_SR_PLUS_TIMES_F32)
+        return fail(TS_ERR_UNSUPPORTED, "%s: the boolean semiring has no gradient", fn);
+    if (!plan->bound) return fail(TS_ERR_STATE, "%s: call ts_batched_bind first", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    plan->gdC.assign(dC_val, dC_val + count);
+    plan->gdA.assign((size_t)count, nullptr);
+    plan->gdB.assign((size_t)count, nullptr);
+    for (int b = 0; b < count; ++b) {
+        if (dA_val) plan->gdA[b] = dA_val[b];
+        if (dB_val) plan->gdB[b] = dB_val[b];
+    }
+    plan->grads = true;
+    return upload_insts(plan, plan->bA.data(), plan->bB.data(), plan->bC.data(), (char*)ws, L,
+                        (cudaStream_t)stream, fn) == TS_OK ? ok() : TS_ERR_CUDA;
+}
+
+static bool same_descs(const std::vector<ts_csr_desc>& v, const ts_csr_desc* x, int count) {
+    if ((int)v.size() != count || !x) return false;
+    for (int b = 0; b < count; ++b)
+        if (v[b].nrows != x[b].nrows || v[b].ncols != x[b].ncols || v[b].nnz != x[b].nnz ||
+            v[b].rowptr != x[b].rowptr || v[b].col != x[b].col || v[b].val != x[b].val)
+            return false;
+    return true;
+}
+
 extern "C" ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, const ts_csr_desc* A,
-                                       const ts_csr_desc* B, const ts_csr_desc* C, void* ws,
-                                       size_t ws_bytes, void* stream) {
-    (void)plan; (void)count; (void)A; (void)B; (void)C; (void)ws; (void)ws_bytes; (void)stream;
-    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+                                       const ts_csr_desc* B, const ts_csr_desc* C, void* ws, size_t ws_bytes,
+                                       void* stream) {
+    const char* fn = "ts_spgemm_batched";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    if (!plan->bound) return fail(TS_ERR_STATE, "%s: call ts_batched_bind first", fn);
+    if (count != plan->count || !same_descs(plan->bA, A, count) || !same_descs(plan->bB, B, count) ||
+        !same_descs(plan->bC, C, count))
+        return fail(TS_ERR_INVALID_ARG, "%s: descriptors differ from those bound", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
+    const InstDesc* inst = (const InstDesc*)(w + L.inst);
+    TS_CUDA(launch_batch_gather(inst, plan->count, std::max(plan->max_rows, std::max(plan->max_annz, plan->max_bnnz)),
+                                (long long*)cA.rowptr, cA.col, (float*)cA.val, (long long*)cB.rowptr, cB.col,
+                                (float*)cB.val, st),
+            fn);
+    if ((s = ts_spgemm_symbolic(plan->inner, &cA, &cB, cC.rowptr, nullptr, w + L.inner, L.inner_bytes, stream)) != TS_OK)
+        return s;
+    if ((s = ts_spgemm_numeric(plan->inner, &cA, &cB, &cC, w + L.inner, L.inner_bytes, stream)) != TS_OK) return s;
+    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
+    TS_CUDA(launch_batch_scatter(inst, plan->count, std::max(plan->max_rows, plan->max_cap), (const long long*)cC.rowptr,
+                                 cC.col,
+                                 (const float*)cC.val, &carve(w + L.inner, IL).hdr->err, st),
+            fn);
+    return ok();
 }
+
 extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count,
                                                 const float* const* dC_val, float* const* dA_val,
                                                 float* const* dB_val, void* ws, size_t ws_bytes,
                                                 void* stream) {
-    (void)plan; (void)count; (void)dC_val; (void)dA_val; (void)dB_val; (void)ws; (void)ws_bytes; (void)stream;
-    return fail(TS_ERR_UNSUPPORTED, "batched: not built yet");
+    const char* fn = "ts_spgemm_batched_backward";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    if (!plan->grads) return fail(TS_ERR_STATE, "%s: call ts_batched_bind_grads first", fn);
+    if (count != plan->count || !dC_val) return fail(TS_ERR_INVALID_ARG, "%s: bad arguments", fn);
+    for (int b = 0; b < count; ++b)
+        if (dC_val[b] != plan->gdC[b] || (dA_val ? dA_val[b] : nullptr) != plan->gdA[b] ||
+            (dB_val ? dB_val[b] : nullptr) != plan->gdB[b])
+            return fail(TS_ERR_INVALID_ARG, "%s: gradient arrays differ from those bound", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
+    const InstDesc* inst = (const InstDesc*)(w + L.inst);
+    float* dC = (float*)(w + L.dC);
+    float* dA = (float*)(w + L.dA);
+    float* dB = (float*)(w + L.dB);
+    TS_CUDA(launch_batch_gather_dc(inst, plan->count, plan->max_cap, (const long long*)cC.rowptr, dC, st), fn);
+    if ((s = ts_spgemm_backward(plan->inner, &cA, &cB, &cC, dC, dA, dB, w + L.inner, L.inner_bytes, stream)) != TS_OK)
+        return s;
+    TS_CUDA(launch_batch_scatter_grads(inst, plan->count, std::max(plan->max_annz, plan->max_bnnz), dA, dB, st), fn);
+    return ok();
+}
+
+extern "C" ts_status ts_batched_check(ts_batched_plan* plan, void* ws, size_t ws_bytes, void* stream) {
+    const char* fn = "ts_batched_check";
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
+    s = read_errors((char*)ws + L.inner, IL, (cudaStream_t)stream, fn);
+    return s == TS_OK ? ok() : s;
+}
+
+extern "C" ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tuning* chosen, void* ws,
+                                         size_t ws_bytes, void* stream) {
+    const char* fn = "ts_batched_autotune";
+    if (!plan || !plan->bound) return fail(TS_ERR_STATE, "%s: bind the plan first", fn);
+    const BLayout L = batched_layout(plan);
+    ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
+    if (s != TS_OK) return s;
+    char* w = (char*)ws;
+    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
+    // one forward leaves the concatenated operands and the schedule in ws
+    if ((s = ts_spgemm_batched(plan, plan->count, plan->bA.data(), plan->bB.data(), plan->bC.data(), ws, ws_bytes,
+                               stream)) != TS_OK)
+        return s;
+    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    s = ts_plan_autotune(plan->inner, &cA, &cB, &cC, vals ? (const float*)(w + L.dC) : nullptr,
+                         vals ? (float*)(w + L.dA) : nullptr, vals ? (float*)(w + L.dB) : nullptr, reps, chosen,
+                         w + L.inner, L.inner_bytes, stream);
+    return s;
 }

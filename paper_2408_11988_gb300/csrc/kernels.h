@@ -111,6 +111,34 @@ cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned*
 cudaError_t launch_msbfs_emit(long long n, int d, const unsigned* newbits, const long long* rp,
                               int* col, long long cap, WsHeader* hdr, cudaStream_t st);
 
+// One instance of a batched product (device-side descriptor).
+struct InstDesc {
+    long long n, d, annz, bnnz, cap;
+    long long row_off, annz_off, bnnz_off;
+    const long long* A_rowptr;
+    const int* A_col;
+    const float* A_val;
+    const long long* B_rowptr;
+    const int* B_col;
+    const float* B_val;
+    long long* C_rowptr;
+    int* C_col;
+    float* C_val;
+    const float* dC;
+    float* dA;
+    float* dB;
+};
+cudaError_t launch_batch_gather(const InstDesc* inst, int count, long long max_work, long long* Ap, int* Ai,
+                                float* Ax, long long* Bp, int* Bi, float* Bx, cudaStream_t st);
+cudaError_t launch_batch_scatter(const InstDesc* inst, int count, long long max_work, const long long* Cp,
+                                 const int* Ci, const float* Cx, unsigned long long* err, cudaStream_t st);
+cudaError_t launch_batch_bounds(const InstDesc* inst, int count, const long long* flops, long long* bound,
+                                cudaStream_t st);
+cudaError_t launch_batch_gather_dc(const InstDesc* inst, int count, long long max_work, const long long* Cp,
+                                   float* dC, cudaStream_t st);
+cudaError_t launch_batch_scatter_grads(const InstDesc* inst, int count, long long max_work, const float* dA,
+                                       const float* dB, cudaStream_t st);
+
 // CSR validation; writes the first bad row (or -1) into *bad (device).
 cudaError_t launch_validate(const DevCsr& M, long long* bad, cudaStream_t st);
 
