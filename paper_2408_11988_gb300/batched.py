@@ -14,14 +14,6 @@ import torch
 from . import _native as N
 from .ops import DeviceCSR, _ptr, _stream
 
-N._SIGS.update({
-    "ts_batched_bind_grads": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
-                                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
-                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
-    "ts_batched_check": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
-    "ts_batched_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(N.Tuning),
-                                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
-})
 
 
 def _descs(ms: Sequence[DeviceCSR]):
