@@ -44,6 +44,11 @@ WORKLOADS = {
                   {"col_tile": 256}, True),
     "er-16k": ("Erdos-Renyi A n=16384, 8 per row, U(0,1); B 16384x64 at 10% U(0,1); plus-times "
                "forward only", None, None, False),
+    "batched-64": ("64 uneven R-MAT instances, n log-uniform in [2^12, 2^18], edge factor U{8..32}, "
+                   "d in {32,64,128,256}, density log-uniform 1-50%, U(0,1); plus-times forward + backward "
+                   "as one CUDA-graph replay", None, None, True),
+    "msbfs-s20": ("multi-source BFS, R-MAT scale 20, edge factor 16, symmetrised, 128 sources, "
+                  "(or, select2nd) iterated to an empty frontier", None, None, False),
 }
 
 
@@ -187,6 +192,10 @@ def main():
     desc, _, wl_tuning, want_bwd = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, ws, rank, desc, want_bwd)
+    if args.workload == "batched-64":
+        return run_batched(args, ws, rank, local, desc)
+    if args.workload == "msbfs-s20":
+        return run_msbfs(args, ws, rank, local, desc)
 
     import torch
     torch.cuda.set_device(local)
@@ -364,6 +373,166 @@ def run_e2e(args, A, B, dC, want_bwd, tuning, flop_step, ws, dist):
         ms = float(t.item())
     return {"value": round(flop_step * ws / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
             "ms_per_step": round(ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def _dist_setup(ws, local):
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist
+    return None
+
+
+def _max_over_ranks(dist, v):
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_batched(args, ws, rank, local, desc):
+    """The uneven batch: plain per-instance forwards (each a symbolic with a
+    host sync plus a numeric) against one CUDA-graph replay of the batched
+    forward, and of the batched forward + backward."""
+    import torch
+    import synth
+    from paper_2408_11988_gb300 import DeviceCSR, Plan
+    from paper_2408_11988_gb300 import _native as N
+    from paper_2408_11988_gb300.batched import BatchedProduct
+    dist = _dist_setup(ws, local)
+    inst = synth.batched_instances(seed=synth.BASE_SEED + 4 + 1000 * rank)
+    F = sum(int(products_per_row(A, B).sum()) for A, B in inst)
+    As = [DeviceCSR.from_host(A) for A, _ in inst]
+    Bs = [DeviceCSR.from_host(B) for _, B in inst]
+    tuning = json.loads(args.tuning) if args.tuning else None
+    plans = [Plan(A, B, tuning=tuning) for A, B in zip(As, Bs)]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def plain():
+        for p, A, B in zip(plans, As, Bs):
+            p.forward(A, B)
+
+    for _ in range(args.warmup):
+        plain()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(args.steps):
+        plain()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = _max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
+    bp = BatchedProduct(As, Bs, tuning=tuning)
+    if args.autotune:
+        bp.autotune()
+    Cs = bp.forward()
+    torch.cuda.synchronize()
+    dCs = [torch.as_tensor(synth.grad_output(int(C.rowptr[-1].item()), 1 + i), device="cuda")
+           for i, C in enumerate(Cs)]
+    bp.bind_grads(dCs)
+    gf = bp.capture(backward=False)
+    gfb = bp.capture(backward=True)
+    nnzC = sum(int(C.rowptr[-1].item()) for C in Cs)
+
+    def timed(g):
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return _max_over_ranks(dist, a.elapsed_time(b) / args.steps)
+
+    l0 = N.lib().ts_kernel_launches()
+    with ClockSampler(local) as clk:
+        fwd_ms = timed(gf)
+        fb_ms = timed(gfb)
+    bp.check()
+    launches = N.lib().ts_kernel_launches() - l0
+    n = sum(A.nrows for A, _ in inst)
+    nnzA = sum(A.nnz for A, _ in inst)
+    num_bytes = 16 * (n + 1) + 24 * nnzA + 8 * F + 8 * nnzC
+    peak, peak_kind = _peaks()
+    value = 6.0 * F * ws / (fb_ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        A, B = max(inst, key=lambda ab: ab[0].nnz)
+        cpu = cpu_baseline(A, B, True)
+        cpu["sample"] = "largest instance: " + cpu["sample"]
+    if rank == 0:
+        print(json.dumps({
+            "metric": "TS-SpGEMM GFLOP/s (batched forward + backward, plus-times)", "value": round(value, 3),
+            "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(fb_ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-64", "description": desc, "instances": len(inst), "rows": n,
+                       "nnz_A": nnzA, "nnz_C": nnzC, "products": F, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2"},
+            "plain_forward": {"ms": round(plain_ms, 4), "gflops": round(2.0 * F / (plain_ms * 1e-3) / 1e9, 3),
+                              "what": "64 separate symbolic+numeric calls (host sync each)"},
+            "batched_forward": {"ms": round(fwd_ms, 4), "gflops": round(2.0 * F / (fwd_ms * 1e-3) / 1e9, 3),
+                                "what": "one CUDA-graph replay"},
+            "batched_forward_backward": {"ms": round(fb_ms, 4), "gflops": round(value / ws, 3)},
+            "roofline": {"bound": "hbm", "kernel": "whole batched forward (gather, passes, scatter)",
+                         "achieved": round(num_bytes / (fwd_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(num_bytes / (fwd_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+                         "traffic": None},
+            "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_msbfs(args, ws, rank, local, desc):
+    """Multi-source BFS to completion; products = the multiplications of the
+    boolean products (sum over reached (vertex, source) of the degree)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2408_11988_gb300 import DeviceCSR
+    from paper_2408_11988_gb300 import _native as N
+    from paper_2408_11988_gb300.msbfs import msbfs
+    dist = _dist_setup(ws, local)
+    A, src = synth.msbfs_graph(seed=synth.BASE_SEED + 2 + 1000 * rank)
+    Ad = DeviceCSR.from_host(A, with_values=False)
+    s = torch.as_tensor(src)
+    for _ in range(args.warmup):
+        r = msbfs(Ad, s)
+    torch.cuda.synchronize()
+    deg = np.diff(A.rowptr)
+    lev = r.levels.cpu().numpy()
+    products = int((deg[:, None] * (lev >= 0)).sum())
+    l0 = N.lib().ts_kernel_launches()
+    with ClockSampler(local) as clk:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            r = msbfs(Ad, s)
+        b.record()
+        torch.cuda.synchronize()
+    launches = N.lib().ts_kernel_launches() - l0
+    ms = _max_over_ranks(dist, a.elapsed_time(b) / args.steps)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "multi-source BFS boolean products/s", "value": round(products * ws / (ms * 1e-3), 1),
+            "unit": "products/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "msbfs-s20", "description": desc, "n": A.nrows, "nnz_A": A.nnz,
+                       "sources": len(src), "levels": r.products, "frontier_nnz": r.frontier_nnz,
+                       "products": products, "parallelism": f"replicas x{ws}"},
+            "roofline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "cpu_baseline": None}), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_reference(args, ws, rank, desc, want_bwd):
