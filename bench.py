@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -62,13 +63,17 @@ def _kernel_sources_hash():
 
 
 def _traffic(workload):
-    """DRAM bytes per launch of the numeric pass from profiles/traffic.json,
-    or None if that capture was taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of the numeric pass, from the JSON block of
+    profiles/dram_traffic.md, or None if that capture was taken on different
+    kernel sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        rec = json.load(f).get(workload)
+        m = re.search(r"```json\n(.*?)\n```", f.read(), re.S)
+    if not m:
+        return None
+    rec = json.loads(m.group(1)).get(workload)
     if not rec or rec.get("sources_sha1") != _kernel_sources_hash():
         return None
     return rec.get("dram_bytes_per_launch")
@@ -138,10 +143,8 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2408_11988_gb300.replicas import world
+    return world()
 
 
 def make_inputs(name, seed_offset=0, scale=None):
@@ -152,7 +155,8 @@ def make_inputs(name, seed_offset=0, scale=None):
     if name == "er-16k":
         A, B = synth.er_product(seed=synth.BASE_SEED + 1 + 1000 * seed_offset)
     else:
-        seed = synth.BASE_SEED + (3 if name == "embed-s22" else 5) + 1000 * seed_offset
+        from paper_2408_11988_gb300.replicas import replica_seed
+        seed = replica_seed(synth.BASE_SEED + (3 if name == "embed-s22" else 5), seed_offset)
         A, B = synth.rmat_embedding(seed=seed, **kw)
     return A, B
 
@@ -285,10 +289,7 @@ def main():
     sym = [e[0].elapsed_time(e[1]) for e in evs]
     num = [e[1].elapsed_time(e[2]) for e in evs]
     bwd = [e[2].elapsed_time(e[3]) for e in evs]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, total_ms)
     ms = total_ms / args.steps
     flop_step = (6.0 if want_bwd else 2.0) * F
     value = flop_step * ws / (ms * 1e-3) / 1e9
@@ -392,10 +393,7 @@ def run_e2e(args, A, B, dC, want_bwd, tuning, flop_step, ws, dist):
     s1.record()
     torch.cuda.synchronize()
     ms = s0.elapsed_time(s1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(dist, ms)
     return {"value": round(flop_step * ws / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
             "ms_per_step": round(ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
@@ -411,12 +409,8 @@ def _dist_setup(ws, local):
 
 
 def _max_over_ranks(dist, v):
-    if not dist:
-        return v
-    import torch
-    t = torch.tensor([v], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2408_11988_gb300.replicas import max_over_ranks
+    return max_over_ranks(v, dist, device="cuda")
 
 
 def run_batched(args, ws, rank, local, desc):

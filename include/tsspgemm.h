@@ -96,6 +96,8 @@ typedef struct ts_csr_desc {
  *                 entry's row of B (best for rows of about that length).
  *  pack_b         1 = gather B from a packed (column, value) copy built in the
  *                 workspace at each call, 2 = from B's own arrays.
+ *  sym_group,     the same choice as `group` for the symbolic pass and for
+ *  bwd_group      the backward pass (each pass may prefer its own).
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.
@@ -109,6 +111,8 @@ typedef struct ts_tuning {
     int32_t group;
     int32_t pack_b;
     int32_t stage;
+    int32_t sym_group;
+    int32_t bwd_group;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;

@@ -138,13 +138,19 @@ static const long long MAX_D = 1LL << 20;
 
 // Lanes per A entry: the power of two at or above the mean row length of B,
 // in [4, 32]; rows of fewer than 3 entries on average use the flattened mode.
-static int auto_group(long long nB, long long nnzB) {
-    // measured: the flattened distribution is at least as fast as lane groups
-    // for rows of B up to ~16 entries; groups only pay off for long rows
+// Lanes per A entry.  Measured on the R-MAT embedding products (rows of B
+// with 10-13 entries): the numeric pass is fastest flattened, while the
+// symbolic and backward passes prefer groups of 16 (fewer shuffles per
+// product); long rows of B favour full-warp groups everywhere.
+static int auto_group(long long nB, long long nnzB, int pass) {
     const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
-    if (avg < 24.0) return 1;
-    return 32;
+    if (avg < 3.0) return 1;
+    if (avg >= 24.0) return 32;
+    if (pass == 0) return 1;
+    return avg <= 8.0 ? 8 : 16;
 }
+
+static bool valid_group(int g) { return g == 1 || g == 4 || g == 8 || g == 16 || g == 32; }
 
 static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t,
                                 long long nB = 0, long long nnzB = 0) {
@@ -155,13 +161,15 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.cta_min_flops = force.cta_min_flops ? force.cta_min_flops : 4096;
     t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
     t.hash_slots = force.hash_slots ? force.hash_slots : 1024;
-    t.group = force.group ? force.group : auto_group(nB, nnzB);
+    t.group = force.group ? force.group : auto_group(nB, nnzB, 0);
+    t.sym_group = force.sym_group ? force.sym_group : auto_group(nB, nnzB, 1);
+    t.bwd_group = force.bwd_group ? force.bwd_group : auto_group(nB, nnzB, 2);
     t.stage = force.stage ? force.stage : 2;
     t.pack_b = force.pack_b ? force.pack_b : 1;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
-    if (t.group != 1 && t.group != 4 && t.group != 8 && t.group != 16 && t.group != 32)
-        return fail(TS_ERR_INVALID_ARG, "tuning: group must be 1, 4, 8, 16 or 32");
+    if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
+        return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
     if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH)
         return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE or TS_ACC_HASH");
@@ -367,7 +375,9 @@ extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, con
     const DevCsr dA = dev(A), dB = dev(B);
     plan->sym_valid = false;
     TS_CUDA(launch_row_schedule(dA, dB, sc, (long long*)C_rowptr, st), fn);
-    TS_CUDA(launch_symbolic(dA, dB, plan->d, sc, cfg_of(plan->cur), (long long*)C_rowptr, st), fn);
+    LaunchCfg scfg = cfg_of(plan->cur);
+    scfg.group = plan->cur.sym_group;
+    TS_CUDA(launch_symbolic(dA, dB, plan->d, sc, scfg, (long long*)C_rowptr, st), fn);
     plan->sym_valid = true;
     plan->sym_ws = ws;
     plan->sym_ptrs[0] = A->rowptr;
@@ -470,8 +480,10 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
         bpk = (int2*)((char*)ws + L.bpk);
         TS_CUDA(launch_pack_b(dev(B), bpk, (cudaStream_t)stream), fn);
     }
+    LaunchCfg bcfg = cfg_of(plan->cur);
+    bcfg.group = plan->cur.bwd_group;
     TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
-                            dA, dB, bpk, sc, cfg_of(plan->cur), (cudaStream_t)stream),
+                            dA, dB, bpk, sc, bcfg, (cudaStream_t)stream),
             fn);
     return ok();
 }
@@ -563,7 +575,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         if (w <= dpad && w >= std::max<long long>(64, round_up(dpad / 8, 32))) tiles.push_back(w);
     if (tiles.empty() || tiles.back() < std::min<long long>(dpad, 4096))
         tiles.push_back((int)std::min<long long>(dpad, 4096));
-    for (int field = 0; field < 7 && s == TS_OK; ++field) {
+    for (int field = 0; field < 8 && s == TS_OK; ++field) {
         std::vector<ts_tuning> cands;
         ts_tuning c = best;
         switch (field) {
@@ -590,6 +602,10 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
             case 5:
                 if (plan->force.warps_per_cta) break;
                 for (int w : {2, 4, 8}) { c.warps_per_cta = w; cands.push_back(c); }
+                break;
+            case 7:
+                if (plan->force.bwd_group || !do_bwd) break;
+                for (int g : {1, 8, 16, 32}) { c.bwd_group = g; cands.push_back(c); }
                 break;
             case 6:
                 if (plan->force.stage) break;

@@ -214,7 +214,7 @@ struct BwdRowBody {
 };
 
 template <int G, bool PACKED>
-__global__ void __launch_bounds__(256, 4) k_backward(BwdParams p) {
+__global__ void __launch_bounds__(256, 5) k_backward(BwdParams p) {
     extern __shared__ __align__(16) float fsm[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;

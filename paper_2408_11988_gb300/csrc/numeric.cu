@@ -324,7 +324,7 @@ struct NumRowBody {
 };
 
 template <bool VALUES, int G, bool PACKED>
-__global__ void __launch_bounds__(256, 4) k_numeric(NumParams p) {
+__global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
     __shared__ long long s_item, s_nheavy, s_nrows;

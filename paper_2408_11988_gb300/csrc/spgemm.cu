@@ -340,7 +340,7 @@ struct SymRowBody {
 };
 
 template <int G>
-__global__ void __launch_bounds__(256, 4) k_symbolic(SymParams p) {
+__global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];

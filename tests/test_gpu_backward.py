@@ -36,7 +36,8 @@ def _run(A, B, tuning=None, seed=1):
 
 @pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1}, {"cta_min_flops": 128, "warps_per_cta": 4},
                                     {"warps_per_cta": 1}, {"group": 1}, {"group": 4}, {"group": 32},
-                                    {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64}])
+                                    {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64},
+                                    {"bwd_group": 1}, {"bwd_group": 4}, {"bwd_group": 32, "sym_group": 1}])
 def test_backward_matches_oracle(tuning):
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
     rp, col, dC, dA, dB = _run(A, B, tuning)

@@ -31,6 +31,7 @@ TUNINGS = [
     {"warps_per_cta": 1},
     {"warps_per_cta": 8, "cta_min_flops": 16},
     {"stage": 2},                              # direct gathers (no cp.async staging)
+    {"sym_group": 1}, {"sym_group": 32}, {"sym_group": 4, "group": 8},
     {"stage": 2, "group": 1},                  # flattened products
     {"stage": 2, "group": 4}, {"stage": 2, "group": 16}, {"stage": 2, "group": 32, "cta_min_flops": 32},
     {"stage": 2, "pack_b": 1}, {"stage": 2, "pack_b": 1, "group": 1, "col_tile": 32},
