@@ -69,6 +69,9 @@ typedef int32_t ts_status;
 #define TS_ACC_AUTO 0
 #define TS_ACC_DENSE 1   /* shared-memory dense accumulator + occupancy flags   */
 #define TS_ACC_HASH 2    /* shared-memory open-addressing hash accumulator      */
+#define TS_ACC_COPIES 3  /* dense accumulator, one private copy per lane group
+                          * and no atomics (plus-times; the boolean semiring
+                          * uses TS_ACC_DENSE)                                  */
 
 typedef struct ts_csr_desc {
     int64_t nrows;
@@ -94,6 +97,8 @@ typedef struct ts_csr_desc {
  *                 lanes: 1 = one product per lane across entries (any mix of
  *                 B row lengths); 4, 8, 16 or 32 = that many lanes walk one
  *                 entry's row of B (best for rows of about that length).
+ *                 TS_ACC_COPIES needs 8, 16 or 32 (32/group copies per warp);
+ *                 with 1 or 4 it picks from B's mean row length.
  *  pack_b         1 = gather B from a packed (column, value) copy built in the
  *                 workspace at each call, 2 = from B's own arrays.
  *  sym_group,     the same choice as `group` for the symbolic pass and for
@@ -101,6 +106,11 @@ typedef struct ts_csr_desc {
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.
+ *  bwd_vec        1 = the backward pass reads B's packed copy four entries
+ *                 per lane (16-byte loads) and adds the dB terms with 16-byte
+ *                 float atomics (needs pack_b = 1 and a 16-byte aligned dB;
+ *                 otherwise the bwd_group kernel runs); 2 = one entry per
+ *                 lane as chosen by bwd_group.
  */
 typedef struct ts_tuning {
     int32_t accum;
@@ -113,6 +123,7 @@ typedef struct ts_tuning {
     int32_t stage;
     int32_t sym_group;
     int32_t bwd_group;
+    int32_t bwd_vec;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;

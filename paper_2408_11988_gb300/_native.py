@@ -29,6 +29,7 @@ OR_SELECT2ND = 1
 ACC_AUTO = 0
 ACC_DENSE = 1
 ACC_HASH = 2
+ACC_COPIES = 3
 
 
 class CsrDesc(ctypes.Structure):
@@ -39,7 +40,8 @@ class CsrDesc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("accum", c_int32), ("col_tile", c_int32), ("cta_min_flops", c_int64),
                 ("warps_per_cta", c_int32), ("hash_slots", c_int32), ("group", c_int32),
-                ("pack_b", c_int32), ("stage", c_int32), ("sym_group", c_int32), ("bwd_group", c_int32)]
+                ("pack_b", c_int32), ("stage", c_int32), ("sym_group", c_int32), ("bwd_group", c_int32),
+                ("bwd_vec", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

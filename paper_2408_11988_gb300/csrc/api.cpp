@@ -136,12 +136,12 @@ struct ts_plan {
 
 static const long long MAX_D = 1LL << 20;
 
-// Lanes per A entry: the power of two at or above the mean row length of B,
-// in [4, 32]; rows of fewer than 3 entries on average use the flattened mode.
-// Lanes per A entry.  Measured on the R-MAT embedding products (rows of B
-// with 10-13 entries): the numeric pass is fastest flattened, while the
-// symbolic and backward passes prefer groups of 16 (fewer shuffles per
-// product); long rows of B favour full-warp groups everywhere.
+// Lanes per A entry for pass 0 (numeric), 1 (symbolic), 2 (backward); B rows
+// of fewer than 3 entries on average use the flattened mode.  Measured on the
+// R-MAT embedding products (rows of B with 10-13 entries): the flag-based
+// numeric pass is fastest flattened, while the symbolic and backward passes
+// prefer groups of 16 (fewer shuffles per product); long rows of B favour
+// full-warp groups everywhere.
 static int auto_group(long long nB, long long nnzB, int pass) {
     const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
     if (avg < 3.0) return 1;
@@ -151,6 +151,14 @@ static int auto_group(long long nB, long long nnzB, int pass) {
 }
 
 static bool valid_group(int g) { return g == 1 || g == 4 || g == 8 || g == 16 || g == 32; }
+
+// Lanes per entry of A for TS_ACC_COPIES: the tuned group if it is 8, 16 or
+// 32, else the smallest of those that covers B's mean row length.
+static int copies_group(int group, long long nB, long long nnzB) {
+    if (group == 8 || group == 16 || group == 32) return group;
+    const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
+    return avg <= 8.0 ? 8 : (avg <= 16.0 ? 16 : 32);
+}
 
 static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t,
                                 long long nB = 0, long long nnzB = 0) {
@@ -166,13 +174,17 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.bwd_group = force.bwd_group ? force.bwd_group : auto_group(nB, nnzB, 2);
     t.stage = force.stage ? force.stage : 2;
     t.pack_b = force.pack_b ? force.pack_b : 1;
+    t.bwd_vec = force.bwd_vec ? force.bwd_vec : 1;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
     if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
         return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
-    if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH)
-        return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE or TS_ACC_HASH");
+    if (t.bwd_vec != 1 && t.bwd_vec != 2) return fail(TS_ERR_INVALID_ARG, "tuning: bwd_vec must be 1 or 2");
+    if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES)
+        return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH or TS_ACC_COPIES");
+    if (t.accum == TS_ACC_COPIES && dpad > 4096)
+        return fail(TS_ERR_INVALID_ARG, "tuning: TS_ACC_COPIES needs d <= 4096");
     if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
         return fail(TS_ERR_INVALID_ARG, "tuning: col_tile must be a multiple of 32 in [32, 4096]");
     if (t.col_tile > dpad) t.col_tile = (int)dpad;
@@ -222,14 +234,15 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     L.W = t.col_tile;
     L.T = (int)((d + L.W - 1) / L.W);
     if (L.T < 1) L.T = 1;
-    int Tmax = (t.accum == TS_ACC_DENSE) ? L.T : 1;
+    int Tmax = (t.accum != TS_ACC_HASH) ? L.T : 1;
     if (cover_autotune) {
         const long long dpad = round_up(d, 32);
         const long long wmin = std::max<long long>(64, round_up(dpad / 8, 32));
         Tmax = std::max<int>(Tmax, (int)((d + wmin - 1) / wmin));
     }
     if (Tmax > 1) L.tp = take(sizeof(long long) * (size_t)n * (Tmax + 1));
-    if (t.pack_b == 1 || cover_autotune) L.bpk = take(8 * (size_t)nnzB);
+    // packed B, padded by four entries for the 16-byte loads of whole quads
+    if (t.pack_b == 1 || cover_autotune) L.bpk = take(8 * ((size_t)nnzB + 4));
     L.total = off;
     return L;
 }
@@ -413,7 +426,7 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
     const Sched sc = carve(ws, L);
     const DevCsr dA = dev(A), dB = dev(B);
     const LaunchCfg cfg = cfg_of(plan->cur);
-    if (plan->cur.accum == TS_ACC_DENSE) {
+    if (plan->cur.accum == TS_ACC_DENSE || plan->cur.accum == TS_ACC_COPIES) {
         long long* tp = nullptr;
         if (L.T > 1) {
             tp = (long long*)((char*)ws + L.tp);
@@ -424,8 +437,14 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
             bpk = (int2*)((char*)ws + L.bpk);
             TS_CUDA(launch_pack_b(dB, bpk, st), fn);
         }
-        if (plan->cur.stage == 1 && numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024 &&
-            (!vals || bpk || B->nnz == 0)) {
+        const int cg = copies_group(plan->cur.group, plan->n, plan->nnzB);
+        if (vals && plan->cur.accum == TS_ACC_COPIES &&
+            numeric_copies_smem(L.W, cg, cfg.warps_per_cta) <= 227 * 1024) {
+            TS_CUDA(launch_numeric_copies(dA, dB, plan->d, L.W, L.T, tp, bpk, cg, sc, cfg,
+                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                    fn);
+        } else if (plan->cur.stage == 1 && numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024 &&
+                   (!vals || bpk || B->nnz == 0)) {
             TS_CUDA(launch_numeric_staged(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                     fn);
         } else {
@@ -482,6 +501,7 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
     }
     LaunchCfg bcfg = cfg_of(plan->cur);
     bcfg.group = plan->cur.bwd_group;
+    if (plan->cur.bwd_vec == 1 && bpk && !(reinterpret_cast<uintptr_t>(dB) & 15)) bcfg.group = 0;  // quads
     TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
                             dA, dB, bpk, sc, bcfg, (cudaStream_t)stream),
             fn);
@@ -588,11 +608,16 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                 for (int pk : {1, 2}) { c.pack_b = pk; cands.push_back(c); }
                 break;
             case 2:
-                if (plan->force.accum || plan->d <= 256) break;
-                for (int acc : {TS_ACC_DENSE, TS_ACC_HASH}) { c.accum = acc; cands.push_back(c); }
+                if (plan->force.accum) break;
+                for (int acc : {TS_ACC_DENSE, TS_ACC_COPIES, TS_ACC_HASH}) {
+                    if (acc == TS_ACC_HASH && plan->d <= 256) continue;
+                    if (acc == TS_ACC_COPIES && (!vals || dpad > 4096)) continue;
+                    c.accum = acc;
+                    cands.push_back(c);
+                }
                 break;
             case 3:
-                if (plan->force.col_tile || best.accum != TS_ACC_DENSE) break;
+                if (plan->force.col_tile || best.accum == TS_ACC_HASH) break;
                 for (int w : tiles) { c.col_tile = w; cands.push_back(c); }
                 break;
             case 4:
@@ -605,7 +630,8 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                 break;
             case 7:
                 if (plan->force.bwd_group || !do_bwd) break;
-                for (int g : {1, 8, 16, 32}) { c.bwd_group = g; cands.push_back(c); }
+                for (int g : {1, 8, 16, 32}) { c.bwd_group = g; c.bwd_vec = 2; cands.push_back(c); }
+                if (!plan->force.bwd_vec && best.pack_b == 1) { c = best; c.bwd_vec = 1; cands.push_back(c); }
                 break;
             case 6:
                 if (plan->force.stage) break;

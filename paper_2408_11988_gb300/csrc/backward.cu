@@ -129,11 +129,67 @@ __device__ __forceinline__ void scatter_dc(const BwdParams& p, long long c0, lon
     }
 }
 
+// Quad mode (G = 0): a group of four lanes takes one entry A(i,k) and walks
+// B's row k four consecutive entries per lane, starting at the multiple of
+// four at or below the row's first entry, with two 16-byte loads of the
+// packed copy (padded by four entries at its end).  The four dB terms of a
+// lane go out as one 16-byte float atomic; entries of the quad outside the
+// row add 0.  dB must be 16-byte aligned (the launcher checks it).
+__device__ __forceinline__ void bwd_quads(const BwdParams& p, const Chunk& ch, int nv, long long e0, const float* g,
+                                          unsigned long long* err) {
+    const int lane = lane_id(), gi = lane >> 2, gl = lane & 3;
+    const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);  // two packed entries per int4
+    for (int r = 0; r < nv; r += 8) {
+        const int q = r + gi;  // <= 31
+        const long long s = shfl64(ch.start, q);
+        const int L = __shfl_sync(FULL, ch.len, q);
+        const float a = __shfl_sync(FULL, ch.a, q);
+        const long long base = s & ~3LL, end = s + L;
+        const int nq = L > 0 ? (int)((end - base + 3) >> 2) : 0;
+        float part = 0.0f;
+        for (int t = gl; t < nq; t += 4) {
+            const long long qb = base + 4LL * t;
+            const int4 v0 = __ldg(P4 + (qb >> 1)), v1 = __ldg(P4 + (qb >> 1) + 1);
+            const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
+            const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+            float t4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                t4[u] = 0.0f;
+                if (qb + u >= s && qb + u < end) {
+                    const int c = cs[u];
+                    if ((unsigned)c < (unsigned)p.d) {
+                        const float gc = g[c];
+                        t4[u] = a * gc;
+                        part += __int_as_float(bs[u]) * gc;
+                    } else {
+                        atomicOr(err, ERR_B_COL);
+                    }
+                }
+            }
+            if (p.dB) {
+                if (qb + 4 <= p.nnzB) {
+                    atomicAdd(reinterpret_cast<float4*>(p.dB + qb), make_float4(t4[0], t4[1], t4[2], t4[3]));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (qb + u >= s && qb + u < end) atomicAdd(p.dB + qb + u, t4[u]);
+                }
+            }
+        }
+        part += __shfl_xor_sync(FULL, part, 1);
+        part += __shfl_xor_sync(FULL, part, 2);
+        if (p.dA && gl == 0 && q < nv) p.dA[e0 + q] = part;
+    }
+}
+
 // Products of one chunk, with the flattened-mode dA write-back.
 template <int G, class BA>
 __device__ __forceinline__ void bwd_chunk(const BwdParams& p, const Chunk& ch, int nv, long long e0, BwdOp<BA>& op,
                                           float* sdA) {
-    if constexpr (G == 1) {
+    if constexpr (G == 0) {
+        bwd_quads(p, ch, nv, e0, op.g, op.err);
+    } else if constexpr (G == 1) {
         expand_loaded(ch, op);
         __syncwarp();
         if (p.dA) {
@@ -314,6 +370,10 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     const void* k;
     const bool pk = Bpk != nullptr;
     switch (cfg.group) {
+        case 0:  // quads: packed B and a 16-byte aligned dB only
+            if (!pk || (dB && (reinterpret_cast<uintptr_t>(dB) & 15))) return cudaErrorInvalidValue;
+            k = bwd_kernel<0, true>();
+            break;
         case 1: k = pk ? bwd_kernel<1, true>() : bwd_kernel<1, false>(); break;
         case 4: k = pk ? bwd_kernel<4, true>() : bwd_kernel<4, false>(); break;
         case 8: k = pk ? bwd_kernel<8, true>() : bwd_kernel<8, false>(); break;

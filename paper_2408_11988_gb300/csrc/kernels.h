@@ -85,6 +85,14 @@ cudaError_t launch_numeric_staged(const DevCsr& A, const DevCsr& B, long long d,
                                   const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
                                   cudaStream_t st);
 size_t numeric_staged_smem(int W, int warps, bool values);
+// Plus-times numeric pass with per-group copies of the dense accumulator (no
+// atomics); G = 8, 16 or 32 lanes per entry of A, 32/G copies per warp.
+cudaError_t launch_numeric_copies(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                  const long long* tp, const int2* Bpk, int G, const Sched& s,
+                                  const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
+                                  cudaStream_t st);
+// Dynamic shared memory of that pass (0 for an unsupported G).
+size_t numeric_copies_smem(int W, int G, int warps);
 // Packed (column, value bits) copy of B's entries.
 cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st);
 

@@ -13,37 +13,10 @@
 // B is read from its two arrays or from a packed (column, value) copy.
 #include "common.cuh"
 #include "kernels.h"
+#include "numeric.cuh"
 #include "staged.cuh"
 
 namespace ts {
-
-constexpr int MAX_DENSE_W = 4096;
-
-struct NumParams {
-    const long long* Ap;
-    const int* Ai;
-    const float* Ax;
-    long long nnzA;
-    const long long* Bp;
-    const int* Bi;
-    const float* Bx;
-    const int2* Bpk;
-    long long nnzB;
-    int nB;
-    int d;
-    int W;
-    int T;
-    const long long* tp;
-    const int* perm;
-    WsHeader* hdr;
-    int cta_class;
-    const long long* Cp;
-    int* Ci;
-    float* Cx;
-    long long nnzC;
-    Sched s;
-    long long item_cap;
-};
 
 template <bool VALUES, class BA>
 struct DenseOp {
@@ -233,44 +206,7 @@ __device__ __forceinline__ void numeric_split_part(const NumParams& p, const BA&
         __syncthreads();
     }
     if (!split_part_done(p.s, it.slot, it.nsub, s_last)) return;
-    // last part: read the row out of the staging slot
-    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
-    const int words = p.s.dpad >> 5;
-    const unsigned lt = lanemask_lt();
-    long long out = clampll(__ldg(p.Cp + it.row), 0, p.nnzC);
-    const long long out_end = clampll(__ldg(p.Cp + it.row + 1), out, p.nnzC);
-    for (int w = warp; w < words; w += nw) {
-        const unsigned bal = __ballot_sync(FULL, __ldcg(sf + w * 32 + lane) != 0);
-        if (lane == 0) wcnt[w] = __popc(bal);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int tot = warp_excl_scan_smem(wcnt, words);
-        if (lane == 0) wcnt[words] = tot;
-    }
-    __syncthreads();
-    for (int w = warp; w < words; w += nw) {
-        const int c = w * 32 + lane;
-        const bool f = __ldcg(sf + c) != 0;
-        const unsigned bal = __ballot_sync(FULL, f);
-        if (f) {
-            const long long pos = out + wcnt[w] + __popc(bal & lt);
-            if (pos < out_end) {
-                p.Ci[pos] = c;
-                if (VALUES) p.Cx[pos] = __ldcg(sv + c);
-            } else {
-                atomicOr(err, ERR_C_ROW);
-            }
-            if (VALUES) sv[c] = 0.0f;
-            sf[c] = 0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (out + wcnt[words] != out_end) atomicOr(err, ERR_C_ROW);
-        p.s.split_done[it.slot] = 0;
-    }
-    __syncthreads();
+    split_row_readout<VALUES>(p, it, wcnt);
 }
 
 // Light row, one warp, driven by pipelined_rows: the first chunk of A (for
@@ -436,30 +372,7 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
-    NumParams p;
-    p.Ap = A.rowptr;
-    p.Ai = A.col;
-    p.Ax = A.val;
-    p.nnzA = A.nnz;
-    p.Bp = B.rowptr;
-    p.Bi = B.col;
-    p.Bx = B.val;
-    p.Bpk = Bpk;
-    p.nnzB = B.nnz;
-    p.nB = (int)B.nrows;
-    p.d = (int)d;
-    p.W = W;
-    p.T = T;
-    p.tp = tp;
-    p.perm = s.perm;
-    p.hdr = s.hdr;
-    p.cta_class = cfg.cta_class;
-    p.Cp = Cp;
-    p.Ci = Ci;
-    p.Cx = Cx;
-    p.nnzC = nnzC;
-    p.s = s;
-    p.item_cap = split_item_capacity(A.nnz);
+    const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
     if (values) {
         if (Bpk) return launch_g<true, true>(p, G, cfg.warps_per_cta, cfg.sms, st);
         return launch_g<true, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
@@ -591,43 +504,7 @@ __device__ __forceinline__ void staged_split_part(const NumParams& p, const Stag
         __syncthreads();
     }
     if (!split_part_done(p.s, it.slot, it.nsub, s_last)) return;
-    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
-    const int words = p.s.dpad >> 5;
-    const unsigned lt = lanemask_lt();
-    long long out = clampll(__ldg(p.Cp + it.row), 0, p.nnzC);
-    const long long out_end = clampll(__ldg(p.Cp + it.row + 1), out, p.nnzC);
-    for (int w = warp; w < words; w += nw) {
-        const unsigned bal = __ballot_sync(FULL, __ldcg(sf + w * 32 + lane) != 0);
-        if (lane == 0) wcnt[w] = __popc(bal);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int tot = warp_excl_scan_smem(wcnt, words);
-        if (lane == 0) wcnt[words] = tot;
-    }
-    __syncthreads();
-    for (int w = warp; w < words; w += nw) {
-        const int c = w * 32 + lane;
-        const bool f = __ldcg(sf + c) != 0;
-        const unsigned bal = __ballot_sync(FULL, f);
-        if (f) {
-            const long long pos = out + wcnt[w] + __popc(bal & lt);
-            if (pos < out_end) {
-                p.Ci[pos] = c;
-                if (VALUES) p.Cx[pos] = __ldcg(sv + c);
-            } else {
-                atomicOr(err, ERR_C_ROW);
-            }
-            if (VALUES) sv[c] = 0.0f;
-            sf[c] = 0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (out + wcnt[words] != out_end) atomicOr(err, ERR_C_ROW);
-        p.s.split_done[it.slot] = 0;
-    }
-    __syncthreads();
+    split_row_readout<VALUES>(p, it, wcnt);
 }
 
 // Light rows of one warp: windows of consecutive rows flow through the two
@@ -759,30 +636,7 @@ cudaError_t launch_numeric_staged(const DevCsr& A, const DevCsr& B, long long d,
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
     if (values && !Bpk && B.nnz > 0) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
-    NumParams p;
-    p.Ap = A.rowptr;
-    p.Ai = A.col;
-    p.Ax = A.val;
-    p.nnzA = A.nnz;
-    p.Bp = B.rowptr;
-    p.Bi = B.col;
-    p.Bx = B.val;
-    p.Bpk = Bpk;
-    p.nnzB = B.nnz;
-    p.nB = (int)B.nrows;
-    p.d = (int)d;
-    p.W = W;
-    p.T = T;
-    p.tp = tp;
-    p.perm = s.perm;
-    p.hdr = s.hdr;
-    p.cta_class = cfg.cta_class;
-    p.Cp = Cp;
-    p.Ci = Ci;
-    p.Cx = Cx;
-    p.nnzC = nnzC;
-    p.s = s;
-    p.item_cap = split_item_capacity(A.nnz);
+    NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
     const int warps = cfg.warps_per_cta;
     const size_t smem = numeric_staged_smem(W, warps, values);
     const void* k = values ? (const void*)k_numeric_staged<true> : (const void*)k_numeric_staged<false>;

@@ -257,12 +257,19 @@ __global__ void __launch_bounds__(256) k_split_rows(long long n, const long long
 
 // ---------------------------------------------------------------------------
 // Symbolic pass: nnz(C_i) = number of distinct columns over the rows B_k,
-// k in A_i (Eq. 1 on patterns).  A bitmap of d bits per warp (shared by the
-// whole block for heavy rows) collects the columns; popcounts give the count.
+// k in A_i (Eq. 1 on patterns).  The columns of a row are collected in one
+// occupancy byte per column (FL, for d up to SYM_FLAG_MAX_D) or one bit per
+// column (wide d) per warp, shared by the whole block for heavy rows; the
+// count is a population count.  Byte marks are plain stores of the value 1:
+// lanes that mark the same column at the same time store the same value, so
+// no atomic is needed; bits are set with shared-memory atomicOr.
 // ---------------------------------------------------------------------------
+constexpr int SYM_FLAG_MAX_D = 4096;
+
+template <bool FL>
 struct SymVisit {
     const int* __restrict__ Bi;
-    unsigned* bm;
+    unsigned* bm;  // bitmap words, or (FL) dpad occupancy bytes
     int d;
     unsigned long long* err;
     struct Item {
@@ -273,8 +280,12 @@ struct SymVisit {
     template <int G>
     __device__ __forceinline__ void done(int, int, int, long long) {}
     __device__ __forceinline__ void mark(int c) {
-        if ((unsigned)c < (unsigned)d) atomicOr(bm + (c >> 5), 1u << (c & 31));
-        else atomicOr(err, ERR_B_COL);
+        if ((unsigned)c < (unsigned)d) {
+            if (FL) reinterpret_cast<unsigned char*>(bm)[c] = 1;
+            else atomicOr(bm + (c >> 5), 1u << (c & 31));
+        } else {
+            atomicOr(err, ERR_B_COL);
+        }
     }
     __device__ __forceinline__ void step4(const long long* j, const float*, const int*) {
         int c[4];
@@ -296,7 +307,8 @@ struct SymParams {
     const int* Bi;
     int nB;
     int d;
-    int dw;  // bitmap words per row
+    int dw;    // bitmap words per row (d/32 rounded up)
+    int slot;  // shared-memory words per warp: dw, or (FL) dw * 8 for the bytes
     const int* perm;
     WsHeader* hdr;
     int cta_class;
@@ -305,21 +317,34 @@ struct SymParams {
     long long item_cap;
 };
 
-template <int G, class Seg>
-__device__ __forceinline__ void sym_chunk(const SymParams& p, long long e0, int nv, SymVisit& vis,
+// Count of the marks in words [w0, dw*8 or dw) of a warp's or block's
+// marks, stride `step`, clearing them.
+template <bool FL>
+__device__ __forceinline__ int count_and_clear(unsigned* bm, int dw, int w0, int step) {
+    int c = 0;
+    const int words = FL ? 8 * dw : dw;  // FL: bytes are 0 or 1, four per word
+    for (int w = w0; w < words; w += step) {
+        c += __popc(bm[w]);
+        bm[w] = 0u;
+    }
+    return c;
+}
+
+template <int G, bool FL, class Seg>
+__device__ __forceinline__ void sym_chunk(const SymParams& p, long long e0, int nv, SymVisit<FL>& vis,
                                           unsigned long long* err) {
     if constexpr (G == 1) expand_chunk(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
     else grouped_chunk<G>(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
 }
 
 // Light row of the symbolic pass, driven by pipelined_rows.
-template <int G>
+template <int G, bool FL>
 struct SymRowBody {
     const SymParams& p;
     unsigned* bm;
     unsigned long long* err;
     __device__ __forceinline__ void gather(int, long long a0, long long a1, const Chunk& ch0, int nv0, int) {
-        SymVisit vis{p.Bi, bm, p.d, err};
+        SymVisit<FL> vis{p.Bi, bm, p.d, err};
         expand_any<G>(ch0, nv0, a0, vis);
         for (long long e0 = a0 + 32; e0 < a1; e0 += 32) {
             const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
@@ -328,24 +353,31 @@ struct SymRowBody {
     }
     __device__ __forceinline__ void finish(int row) {
         __syncwarp();
-        int c = 0;
-        for (int w = lane_id(); w < p.dw; w += 32) {
-            c += __popc(bm[w]);
-            bm[w] = 0;
-        }
-        c = warp_sum(c);
+        const int c = warp_sum(count_and_clear<FL>(bm, p.dw, lane_id(), 32));
         if (lane_id() == 0) p.Cp_next[row] = c;
         __syncwarp();
     }
 };
 
-template <int G>
+// Block total of per-thread counts (all threads get it).
+__device__ __forceinline__ int block_sum(int c, int* s_red) {
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    c = warp_sum(c);
+    if (lane == 0) s_red[warp] = c;
+    __syncthreads();
+    int v = lane < nw ? s_red[lane] : 0;
+    v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+template <int G, bool FL>
 __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
-    for (int i = tid; i < nw * p.dw; i += blockDim.x) smem_u[i] = 0;
+    for (int i = tid; i < nw * p.slot; i += blockDim.x) smem_u[i] = 0;
     if (tid == 0) {
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -364,16 +396,26 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         __shared__ int s_last;
         SplitItem it;
         while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
-            SymVisit vis{p.Bi, smem_u, p.d, err};
+            SymVisit<FL> vis{p.Bi, smem_u, p.d, err};
             for (long long e0 = it.e0 + 32LL * warp; e0 < it.e1; e0 += 32LL * nw)
-                sym_chunk<G, SegWhole>(p, e0, (int)(it.e1 - e0 < 32 ? it.e1 - e0 : 32), vis, err);
+                sym_chunk<G, FL, SegWhole>(p, e0, (int)(it.e1 - e0 < 32 ? it.e1 - e0 : 32), vis, err);
             __syncthreads();
             unsigned* stg = p.s.stg_bits + (size_t)it.slot * p.dw;
-            for (int w = tid; w < p.dw; w += blockDim.x) {
-                const unsigned v = smem_u[w];
-                if (v) {
-                    atomicOr(stg + w, v);
-                    smem_u[w] = 0u;
+            if (FL) {  // bytes -> bitmap words by ballot, one word per warp step
+                const unsigned char* fb = reinterpret_cast<const unsigned char*>(smem_u);
+                for (int w = warp; w < p.dw; w += nw) {
+                    const unsigned v = __ballot_sync(FULL, fb[w * 32 + lane] != 0);
+                    if (lane == 0 && v) atomicOr(stg + w, v);
+                }
+                __syncthreads();
+                for (int w = tid; w < 8 * p.dw; w += blockDim.x) smem_u[w] = 0u;
+            } else {
+                for (int w = tid; w < p.dw; w += blockDim.x) {
+                    const unsigned v = smem_u[w];
+                    if (v) {
+                        atomicOr(stg + w, v);
+                        smem_u[w] = 0u;
+                    }
                 }
             }
             if (split_part_done(p.s, it.slot, it.nsub, &s_last)) {
@@ -382,16 +424,10 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
                     c += __popc(__ldcg(stg + w));
                     stg[w] = 0u;
                 }
-                c = warp_sum(c);
-                if (lane == 0) s_red[warp] = c;
-                __syncthreads();
-                if (warp == 0) {
-                    int v = lane < nw ? s_red[lane] : 0;
-                    v = warp_sum(v);
-                    if (lane == 0) {
-                        p.Cp_next[it.row] = v;
-                        p.s.split_done[it.slot] = 0;
-                    }
+                c = block_sum(c, s_red);
+                if (tid == 0) {
+                    p.Cp_next[it.row] = c;
+                    p.s.split_done[it.slot] = 0;
                 }
                 __syncthreads();
             }
@@ -409,28 +445,17 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
         if (is_split_row(mark, row, a1 - a0)) continue;
-        SymVisit vis{p.Bi, smem_u, p.d, err};
+        SymVisit<FL> vis{p.Bi, smem_u, p.d, err};
         for (long long e0 = a0 + 32LL * warp; e0 < a1; e0 += 32LL * nw)
-            sym_chunk<G, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
+            sym_chunk<G, FL, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
         __syncthreads();
-        int c = 0;
-        for (int w = tid; w < p.dw; w += blockDim.x) {
-            c += __popc(smem_u[w]);
-            smem_u[w] = 0;
-        }
-        c = warp_sum(c);
-        if (lane == 0) s_red[warp] = c;
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < nw ? s_red[lane] : 0;
-            v = warp_sum(v);
-            if (lane == 0) p.Cp_next[row] = v;
-        }
+        const int c = block_sum(count_and_clear<FL>(smem_u, p.dw, tid, blockDim.x), s_red);
+        if (tid == 0) p.Cp_next[row] = c;
     }
 
     // light rows: one warp per row, static round robin over the class order
-    unsigned* bm = smem_u + warp * p.dw;
-    SymRowBody<G> body{p, bm, err};
+    unsigned* bm = smem_u + warp * p.slot;
+    SymRowBody<G, FL> body{p, bm, err};
     pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
                    p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body, mark);
 }
@@ -472,6 +497,8 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.nB = (int)B.nrows;
     p.d = (int)d;
     p.dw = (int)((d + 31) / 32);
+    const bool fl = d <= SYM_FLAG_MAX_D;
+    p.slot = fl ? 8 * p.dw : p.dw;
     p.perm = s.perm;
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
@@ -479,14 +506,14 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.s = s;
     p.item_cap = item_cap;
     const int threads = 32 * cfg.warps_per_cta;
-    const size_t smem = sizeof(unsigned) * (size_t)p.dw * cfg.warps_per_cta;
+    const size_t smem = sizeof(unsigned) * (size_t)p.slot * cfg.warps_per_cta;
     const void* k;
     switch (cfg.group) {
-        case 1: k = (const void*)k_symbolic<1>; break;
-        case 4: k = (const void*)k_symbolic<4>; break;
-        case 8: k = (const void*)k_symbolic<8>; break;
-        case 16: k = (const void*)k_symbolic<16>; break;
-        case 32: k = (const void*)k_symbolic<32>; break;
+        case 1: k = fl ? (const void*)k_symbolic<1, true> : (const void*)k_symbolic<1, false>; break;
+        case 4: k = fl ? (const void*)k_symbolic<4, true> : (const void*)k_symbolic<4, false>; break;
+        case 8: k = fl ? (const void*)k_symbolic<8, true> : (const void*)k_symbolic<8, false>; break;
+        case 16: k = fl ? (const void*)k_symbolic<16, true> : (const void*)k_symbolic<16, false>; break;
+        case 32: k = fl ? (const void*)k_symbolic<32, true> : (const void*)k_symbolic<32, false>; break;
         default: return cudaErrorInvalidValue;
     }
     if (threads > 256) return cudaErrorInvalidValue;

@@ -37,7 +37,9 @@ def _run(A, B, tuning=None, seed=1):
 @pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1}, {"cta_min_flops": 128, "warps_per_cta": 4},
                                     {"warps_per_cta": 1}, {"group": 1}, {"group": 4}, {"group": 32},
                                     {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64},
-                                    {"bwd_group": 1}, {"bwd_group": 4}, {"bwd_group": 32, "sym_group": 1}])
+                                    {"bwd_group": 1}, {"bwd_group": 4}, {"bwd_group": 32, "sym_group": 1},
+                                    {"bwd_vec": 2}, {"bwd_vec": 2, "bwd_group": 16}, {"bwd_vec": 1, "pack_b": 2},
+                                    {"bwd_vec": 1, "cta_min_flops": 1}, {"bwd_vec": 1, "warps_per_cta": 1}])
 def test_backward_matches_oracle(tuning):
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -46,13 +48,39 @@ def test_backward_matches_oracle(tuning):
     assert np.all(np.abs(dB - rB) <= REL * bB), np.max(np.abs(dB - rB) / np.maximum(bB, 1e-30))
 
 
-@pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}])
+@pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}, {"bwd_vec": 2},
+                                    {"bwd_vec": 1, "cta_min_flops": 16}])
 def test_backward_ragged_and_empty_rows(tuning):
     A, B = synth.er_product(n=3000, k=5, d=100, density=0.05, seed=51)
     rp, col, dC, dA, dB = _run(A, B, tuning)
     rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
     assert np.all(np.abs(dA - rA) <= REL * bA)
     assert np.all(np.abs(dB - rB) <= REL * bB)
+
+
+def test_backward_unaligned_db_and_b_tail():
+    # dB one float into a buffer (not 16-byte aligned: the quad kernel must
+    # not be used), and B whose last row ends at an entry count that is not a
+    # multiple of four (the quads at the end of B take the scalar atomics)
+    for seed in range(54, 70):
+        A, B = synth.er_product(n=2001, k=5, d=96, density=0.07, seed=seed)
+        if B.nnz % 4:
+            break
+    assert B.nnz % 4 != 0
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    C = plan.forward(Ad, Bd)
+    dC = synth.grad_output(C.nnz, 5)
+    rp, col, _ = C.to_host()
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
+    g = torch.as_tensor(dC, device="cuda")
+    for off in (0, 1):
+        buf = torch.full((B.nnz + 4,), 7.0, device="cuda")
+        dA, dB = plan.backward(Ad, Bd, C, g, out_dB=buf[off:off + B.nnz])
+        assert np.all(np.abs(dA.cpu().numpy() - rA) <= REL * bA)
+        assert np.all(np.abs(dB.cpu().numpy() - rB) <= REL * bB)
+        rest = torch.cat([buf[:off], buf[off + B.nnz:]]).cpu().numpy()
+        assert np.all(rest == 7.0)  # nothing written outside dB
 
 
 def test_backward_finite_differences():

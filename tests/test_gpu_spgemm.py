@@ -15,7 +15,7 @@ from _cmp import compare_full, compare_rows, assert_pattern_equal, assert_values
 
 pytestmark = pytest.mark.gpu
 
-from paper_2408_11988_gb300 import (ACC_DENSE, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, DeviceCSR, Plan,
+from paper_2408_11988_gb300 import (ACC_COPIES, ACC_DENSE, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, DeviceCSR, Plan,
                                     TSError, spgemm, validate)
 
 
@@ -38,6 +38,10 @@ TUNINGS = [
     {"stage": 2, "pack_b": 1, "cta_min_flops": 1}, {"col_tile": 32, "cta_min_flops": 1},
     {"accum": ACC_HASH, "hash_slots": 128},
     {"accum": ACC_HASH, "hash_slots": 1024, "warps_per_cta": 4},
+    {"accum": ACC_COPIES},                     # private accumulator copies, no atomics
+    {"accum": ACC_COPIES, "group": 16}, {"accum": ACC_COPIES, "group": 32, "cta_min_flops": 1},
+    {"accum": ACC_COPIES, "col_tile": 32}, {"accum": ACC_COPIES, "pack_b": 2, "warps_per_cta": 1},
+    {"accum": ACC_COPIES, "group": 8, "cta_min_flops": 16, "warps_per_cta": 3},
 ]
 
 
@@ -55,7 +59,7 @@ def test_er_full_size(er_case, tuning):
 
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH},
-                                    {"stage": 2, "group": 1}, {"stage": 2, "group": 32}])
+                                    {"stage": 2, "group": 1}, {"stage": 2, "group": 32}, {"accum": ACC_COPIES}])
 def test_er_boolean(er_case, tuning):
     A, B = er_case
     C = spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=tuning)
@@ -66,7 +70,9 @@ def test_er_boolean(er_case, tuning):
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 64}, {"col_tile": 96}, {"cta_min_flops": 128},
                                     {"accum": ACC_HASH, "hash_slots": 512}, {"stage": 2, "group": 1},
                                     {"stage": 2, "group": 8}, {"stage": 2, "group": 32, "pack_b": 1},
-                                    {"stage": 2, "pack_b": 1, "col_tile": 64}, {"col_tile": 64, "warps_per_cta": 2}])
+                                    {"stage": 2, "pack_b": 1, "col_tile": 64}, {"col_tile": 64, "warps_per_cta": 2},
+                                    {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "group": 8, "col_tile": 64},
+                                    {"accum": ACC_COPIES, "cta_min_flops": 128, "pack_b": 2}])
 def test_rmat_embedding_small(tuning):
     A, B = synth.rmat_embedding(scale=13, edge_factor=16, d=256, density=0.05, seed=31)
     C = spgemm(dev(A), dev(B), tuning=tuning)
@@ -76,7 +82,8 @@ def test_rmat_embedding_small(tuning):
 def test_rmat_tiled_d1024():
     # the large tiled product's shape at small scale: d = 1024, 1 %, tiles of 256
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=1024, density=0.01, seed=32, b_values="uniform")
-    for t in (None, {"col_tile": 256}, {"col_tile": 256, "cta_min_flops": 32}, {"accum": ACC_HASH}):
+    for t in (None, {"col_tile": 256}, {"col_tile": 256, "cta_min_flops": 32}, {"accum": ACC_HASH},
+              {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "col_tile": 256, "cta_min_flops": 32}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -109,7 +116,8 @@ def test_small_shapes_and_ragged_d(n, d):
     B = _csr(n, d, [rng.choice(d, size=rng.integers(0, d + 1), replace=False) for _ in range(n)], seed=2)
     for t in (None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH, "hash_slots": 256},
               {"stage": 2, "group": 1}, {"stage": 2, "group": 4, "pack_b": 1},
-              {"stage": 2, "group": 32, "cta_min_flops": 1}, {"warps_per_cta": 1}):
+              {"stage": 2, "group": 32, "cta_min_flops": 1}, {"warps_per_cta": 1}, {"accum": ACC_COPIES},
+              {"accum": ACC_COPIES, "group": 32, "cta_min_flops": 1}, {"accum": ACC_COPIES, "col_tile": 32}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -129,7 +137,8 @@ def test_identity_is_exact():
     B = synth.tall_skinny(n, d, 0.3, 7)
     B.val = synth.normal(B.nnz, 8)
     I = CSR(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n, np.float32))
-    for t in (None, {"col_tile": 32}, {"accum": ACC_HASH}):
+    for t in (None, {"col_tile": 32}, {"accum": ACC_HASH}, {"accum": ACC_COPIES},
+              {"accum": ACC_COPIES, "cta_min_flops": 1}):
         rp, col, val = spgemm(dev(I), dev(B), tuning=t).to_host()
         np.testing.assert_array_equal(rp, B.rowptr)
         np.testing.assert_array_equal(col, B.col)
@@ -144,15 +153,22 @@ def test_hub_row_and_dense_b():
     B = synth.tall_skinny(n, d, 1.0, 11)           # fully dense rows
     B.val = synth.uniform(B.nnz, 12)
     for t in (None, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 2}, {"stage": 2, "group": 1},
-              {"stage": 2, "group": 32}):
+              {"stage": 2, "group": 32}, {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "group": 8},
+              {"accum": ACC_COPIES, "cta_min_flops": 1 << 20}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
-def test_embedding_full_size_sampled():
+@pytest.fixture(scope="module")
+def embed_full():
+    return synth.rmat_embedding()
+
+
+@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}])
+def test_embedding_full_size_sampled(embed_full, tuning):
     # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %
-    A, B = synth.rmat_embedding()
+    A, B = embed_full
     Ad, Bd = dev(A), dev(B)
-    C = spgemm(Ad, Bd)
+    C = spgemm(Ad, Bd, tuning=tuning)
     rp = C.rowptr.cpu().numpy()
     assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= B.ncols)
     deg = np.diff(A.rowptr)
@@ -210,7 +226,8 @@ def test_autotune_keeps_results():
 
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 256}, {"col_tile": 256, "stage": 2, "group": 1},
-                                    {"stage": 2, "pack_b": 1}, {"stage": 2}])
+                                    {"stage": 2, "pack_b": 1}, {"stage": 2}, {"accum": ACC_COPIES},
+                                    {"accum": ACC_COPIES, "col_tile": 256}])
 def test_split_rows_with_tiles(tuning):
     # rows longer than 1024 entries of A are cut into parts processed by
     # different blocks and merged through a staging row; with d = 1024 and
@@ -237,6 +254,27 @@ def test_more_long_rows_than_split_slots():
             synth.uniform(n * per, 75))
     B = synth.tall_skinny(n, d, 1.0 / 32, 76)
     B.val = synth.uniform(B.nnz, 77)
-    C = spgemm(dev(A), dev(B))
     rng2 = np.random.default_rng(1)
-    compare_rows(C, A, B, rng2.choice(n, 400, replace=False))
+    rows = rng2.choice(n, 400, replace=False)
+    for t in (None, {"accum": ACC_COPIES}):
+        compare_rows(spgemm(dev(A), dev(B), tuning=t), A, B, rows)
+
+
+@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "cta_min_flops": 1},
+                                    {"accum": ACC_HASH}])
+def test_nan_products_keep_their_columns(tuning):
+    # NaN values of B (one of them with the copies kernel's empty-column bit
+    # pattern) must give NaN entries at their columns, never drop them
+    A, B = synth.er_product(n=2000, k=6, d=64, density=0.1, seed=90)
+    bits = B.val.view(np.uint32).copy()
+    bits[::97] = 0x7FC00000
+    bits[5::211] = 0xFFBADBAD
+    B.val = bits.view(np.float32)
+    rp, col, val = spgemm(dev(A), dev(B), tuning=tuning).to_host()
+    Cp, Ci, Cx, bound = oracle.spgemm(A, B)
+    np.testing.assert_array_equal(rp, Cp)
+    np.testing.assert_array_equal(col, Ci)
+    nan = np.isnan(Cx)
+    assert nan.any()
+    assert np.array_equal(np.isnan(val), nan)
+    assert np.all(np.abs(val[~nan] - Cx[~nan]) <= 1e-5 * bound[~nan])
