@@ -96,21 +96,26 @@ typedef struct ts_csr_desc {
  *  group          how a warp spreads the products of 32 entries of A over its
  *                 lanes: 1 = one product per lane across entries (any mix of
  *                 B row lengths); 4, 8, 16 or 32 = that many lanes walk one
- *                 entry's row of B (best for rows of about that length).
+ *                 entry's row of B (best for rows of about that length);
+ *                 2 = quads: four lanes walk one entry's row of B, four
+ *                 consecutive entries per lane with 16-byte loads (numeric:
+ *                 plus-times with pack_b = 1; symbolic: B.col 16-byte
+ *                 aligned; backward: pack_b = 1 and dB 16-byte aligned, its
+ *                 dB terms then go out as 16-byte float atomics).  Where a
+ *                 pass cannot use quads it falls back to 16 lanes.
  *                 TS_ACC_COPIES needs 8, 16 or 32 (32/group copies per warp);
  *                 with 1 or 4 it picks from B's mean row length.
  *  pack_b         1 = gather B from a packed (column, value) copy built in the
  *                 workspace at each call, 2 = from B's own arrays.
  *  sym_group,     the same choice as `group` for the symbolic pass and for
  *  bwd_group      the backward pass (each pass may prefer its own).
+ *  row_lanes      numeric pass (plus-times, pack_b = 1, dense accumulator):
+ *                 lanes per light row.  32 = one warp per row; 4, 8 or 16 =
+ *                 row groups, 32/row_lanes rows per warp in lockstep, each
+ *                 with its own accumulator and no atomics.
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.
- *  bwd_vec        1 = the backward pass reads B's packed copy four entries
- *                 per lane (16-byte loads) and adds the dB terms with 16-byte
- *                 float atomics (needs pack_b = 1 and a 16-byte aligned dB;
- *                 otherwise the bwd_group kernel runs); 2 = one entry per
- *                 lane as chosen by bwd_group.
  */
 typedef struct ts_tuning {
     int32_t accum;
@@ -123,7 +128,7 @@ typedef struct ts_tuning {
     int32_t stage;
     int32_t sym_group;
     int32_t bwd_group;
-    int32_t bwd_vec;
+    int32_t row_lanes;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;

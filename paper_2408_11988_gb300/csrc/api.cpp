@@ -136,21 +136,23 @@ struct ts_plan {
 
 static const long long MAX_D = 1LL << 20;
 
-// Lanes per A entry for pass 0 (numeric), 1 (symbolic), 2 (backward); B rows
-// of fewer than 3 entries on average use the flattened mode.  Measured on the
-// R-MAT embedding products (rows of B with 10-13 entries): the flag-based
-// numeric pass is fastest flattened, while the symbolic and backward passes
-// prefer groups of 16 (fewer shuffles per product); long rows of B favour
-// full-warp groups everywhere.
+// Lanes per A entry for pass 0 (numeric), 1 (symbolic), 2 (backward).
+// Measured on the R-MAT embedding products (rows of B with 10-13 entries):
+// the flag-based numeric pass is fastest flattened (its shared-memory float
+// atomics collide more when eight rows of B are in flight, as with quads),
+// the symbolic and backward passes with quads (16-byte loads, and 16-byte
+// dB atomics in the backward); rows of B of fewer than 3 entries on average
+// leave most quad lanes idle and use the flattened mode there.
 static int auto_group(long long nB, long long nnzB, int pass) {
     const double avg = nB > 0 ? (double)nnzB / (double)nB : 0.0;
+    if (pass == 2) return 2;  // backward: quads (16 lanes where quads do not apply)
     if (avg < 3.0) return 1;
+    if (pass == 1) return 2;  // symbolic: quads (16 lanes where quads do not apply)
     if (avg >= 24.0) return 32;
-    if (pass == 0) return 1;
-    return avg <= 8.0 ? 8 : 16;
+    return 1;
 }
 
-static bool valid_group(int g) { return g == 1 || g == 4 || g == 8 || g == 16 || g == 32; }
+static bool valid_group(int g) { return g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; }
 
 // Lanes per entry of A for TS_ACC_COPIES: the tuned group if it is 8, 16 or
 // 32, else the smallest of those that covers B's mean row length.
@@ -174,13 +176,14 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.bwd_group = force.bwd_group ? force.bwd_group : auto_group(nB, nnzB, 2);
     t.stage = force.stage ? force.stage : 2;
     t.pack_b = force.pack_b ? force.pack_b : 1;
-    t.bwd_vec = force.bwd_vec ? force.bwd_vec : 1;
+    t.row_lanes = force.row_lanes ? force.row_lanes : 32;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
     if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
-        return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 4, 8, 16 or 32");
+        return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 2, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
-    if (t.bwd_vec != 1 && t.bwd_vec != 2) return fail(TS_ERR_INVALID_ARG, "tuning: bwd_vec must be 1 or 2");
+    if (t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 && t.row_lanes != 32)
+        return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes must be 4, 8, 16 or 32");
     if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES)
         return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH or TS_ACC_COPIES");
     if (t.accum == TS_ACC_COPIES && dpad > 4096)
@@ -272,6 +275,7 @@ static LaunchCfg cfg_of(const ts_tuning& t) {
     c.cta_class = cta_class_of(t.cta_min_flops);
     c.sms = sm_count();
     c.group = t.group;
+    c.row_lanes = t.row_lanes;
     return c;
 }
 
@@ -448,7 +452,11 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
             TS_CUDA(launch_numeric_staged(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                     fn);
         } else {
-            TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, cfg,
+            LaunchCfg ncfg = cfg;
+            if (ncfg.row_lanes != 32 &&
+                (!vals || !bpk || numeric_dense_smem(L.W, cfg.warps_per_cta, true, ncfg.row_lanes) > 220 * 1024))
+                ncfg.row_lanes = 32;  // row groups need the packed copy and room for their accumulators
+            TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, ncfg,
                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                     fn);
         }
@@ -501,7 +509,7 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
     }
     LaunchCfg bcfg = cfg_of(plan->cur);
     bcfg.group = plan->cur.bwd_group;
-    if (plan->cur.bwd_vec == 1 && bpk && !(reinterpret_cast<uintptr_t>(dB) & 15)) bcfg.group = 0;  // quads
+    if (bcfg.group == 2 && (!bpk || (reinterpret_cast<uintptr_t>(dB) & 15))) bcfg.group = 16;  // no quads
     TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
                             dA, dB, bpk, sc, bcfg, (cudaStream_t)stream),
             fn);
@@ -595,7 +603,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         if (w <= dpad && w >= std::max<long long>(64, round_up(dpad / 8, 32))) tiles.push_back(w);
     if (tiles.empty() || tiles.back() < std::min<long long>(dpad, 4096))
         tiles.push_back((int)std::min<long long>(dpad, 4096));
-    for (int field = 0; field < 8 && s == TS_OK; ++field) {
+    for (int field = 0; field < 9 && s == TS_OK; ++field) {
         std::vector<ts_tuning> cands;
         ts_tuning c = best;
         switch (field) {
@@ -630,8 +638,11 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                 break;
             case 7:
                 if (plan->force.bwd_group || !do_bwd) break;
-                for (int g : {1, 8, 16, 32}) { c.bwd_group = g; c.bwd_vec = 2; cands.push_back(c); }
-                if (!plan->force.bwd_vec && best.pack_b == 1) { c = best; c.bwd_vec = 1; cands.push_back(c); }
+                for (int g : {1, 2, 8, 16, 32}) { c.bwd_group = g; cands.push_back(c); }
+                break;
+            case 8:
+                if (plan->force.row_lanes || !vals) break;
+                for (int rl : {32, 4, 8, 16}) { c.row_lanes = rl; cands.push_back(c); }
                 break;
             case 6:
                 if (plan->force.stage) break;

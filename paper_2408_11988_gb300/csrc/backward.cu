@@ -129,7 +129,7 @@ __device__ __forceinline__ void scatter_dc(const BwdParams& p, long long c0, lon
     }
 }
 
-// Quad mode (G = 0): a group of four lanes takes one entry A(i,k) and walks
+// Quad mode (G = 2): a group of four lanes takes one entry A(i,k) and walks
 // B's row k four consecutive entries per lane, starting at the multiple of
 // four at or below the row's first entry, with two 16-byte loads of the
 // packed copy (padded by four entries at its end).  The four dB terms of a
@@ -187,7 +187,7 @@ __device__ __forceinline__ void bwd_quads(const BwdParams& p, const Chunk& ch, i
 template <int G, class BA>
 __device__ __forceinline__ void bwd_chunk(const BwdParams& p, const Chunk& ch, int nv, long long e0, BwdOp<BA>& op,
                                           float* sdA) {
-    if constexpr (G == 0) {
+    if constexpr (G == 2) {
         bwd_quads(p, ch, nv, e0, op.g, op.err);
     } else if constexpr (G == 1) {
         expand_loaded(ch, op);
@@ -370,9 +370,9 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     const void* k;
     const bool pk = Bpk != nullptr;
     switch (cfg.group) {
-        case 0:  // quads: packed B and a 16-byte aligned dB only
+        case 2:  // quads: packed B and a 16-byte aligned dB only
             if (!pk || (dB && (reinterpret_cast<uintptr_t>(dB) & 15))) return cudaErrorInvalidValue;
-            k = bwd_kernel<0, true>();
+            k = bwd_kernel<2, true>();
             break;
         case 1: k = pk ? bwd_kernel<1, true>() : bwd_kernel<1, false>(); break;
         case 4: k = pk ? bwd_kernel<4, true>() : bwd_kernel<4, false>(); break;

@@ -245,10 +245,32 @@ __device__ __forceinline__ void grouped_chunk(long long e0, int nvalid, const in
     grouped_loaded<G>(ch, nvalid, e0, op);
 }
 
-// Products of one chunk in the chosen distribution (G = 1: flattened).
+// Quad distribution of one loaded chunk: a group of four lanes takes one
+// entry q and walks its segment [s, s + len) of B in quads of four
+// consecutive positions, starting at the multiple of four at or below s;
+// lane gl of the group takes quads gl, gl + 4, ...  visit(qb, s, end, a) is
+// called once per quad (first position qb); positions outside [s, end) are
+// the visitor's to skip.  No lane synchronisation inside.
+template <class F>
+__device__ __forceinline__ void quads_loaded(const Chunk& ch, int nvalid, F&& visit) {
+    const int lane = lane_id(), gi = lane >> 2, gl = lane & 3;
+    for (int r = 0; r < nvalid; r += 8) {
+        const int q = r + gi;  // <= 31
+        const long long s = shfl64(ch.start, q);
+        const int L = __shfl_sync(FULL, ch.len, q);
+        const float a = __shfl_sync(FULL, ch.a, q);
+        const long long base = s & ~3LL, end = s + L;
+        const int nq = L > 0 ? (int)((end - base + 3) >> 2) : 0;
+        for (int t = gl; t < nq; t += 4) visit(base + 4LL * t, s, end, a);
+    }
+}
+
+// Products of one chunk in the chosen distribution (G = 1: flattened;
+// G = 2: quads, through op.quads).
 template <int G, class Op>
 __device__ __forceinline__ void expand_any(const Chunk& ch, int nvalid, long long e0, Op& op) {
-    if constexpr (G == 1) expand_loaded(ch, op);
+    if constexpr (G == 2) op.quads(ch, nvalid);
+    else if constexpr (G == 1) expand_loaded(ch, op);
     else grouped_loaded<G>(ch, nvalid, e0, op);
 }
 

@@ -47,6 +47,7 @@ struct LaunchCfg {
     int cta_class = 14;      // rows of flops class >= this run CTA-per-row
     int sms = 152;
     int group = 1;           // lanes per A entry (1 = flattened products)
+    int row_lanes = 32;      // numeric light rows: 32 = a warp per row, 4/8/16 = row groups
 };
 
 // Bytes of the scan partials for n values.
@@ -101,7 +102,7 @@ cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, i
                                 bool values, const Sched& s, const LaunchCfg& cfg,
                                 const long long* Cp, int* Ci, float* Cx, long long nnzC,
                                 cudaStream_t st);
-size_t numeric_dense_smem(int W, int warps, bool values);
+size_t numeric_dense_smem(int W, int warps, bool values, int row_lanes = 0);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).

@@ -66,6 +66,21 @@ struct DenseOp {
             add(it.c, a * it.b);
         }
     }
+    // quads (plus-times, packed B padded by four entries): two 16-byte loads
+    // give the four (column, value) pairs of a quad
+    __device__ __forceinline__ void quads(const Chunk& ch, int nv) {
+        if constexpr (VALUES && std::is_same<BA, BPacked>::value) {
+            const int4* P4 = reinterpret_cast<const int4*>(ba.P);
+            quads_loaded(ch, nv, [&](long long qb, long long s, long long end, float a) {
+                const int4 v0 = __ldg(P4 + (qb >> 1)), v1 = __ldg(P4 + (qb >> 1) + 1);
+                const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
+                const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (qb + u >= s && qb + u < end) add(cs[u], a * __int_as_float(bs[u]));
+            });
+        }
+    }
 };
 
 // Warp read-out: lane l looks at columns 4l..4l+3 of each 128-column block.
@@ -259,14 +274,182 @@ struct NumRowBody {
     }
 };
 
-template <bool VALUES, int G, bool PACKED>
-__global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
+
+// ---------------------------------------------------------------------------
+// Light rows in row groups (plus-times, packed B; template RG = lanes per
+// row).  A warp takes R = 32/RG consecutive light rows of the schedule at a
+// time; the RG lanes of row slot g accumulate row g into their own dense
+// accumulator of W floats.  The slot walks the segments B(k,:) of its row's
+// entries one after another in quads (RG lanes, four consecutive entries per
+// lane, two 16-byte loads of the packed copy of B, padded by four entries):
+// the columns of one segment are distinct, so acc[c] += A(i,k) * B(k,c) is a
+// plain load and store, and __syncwarp between segments orders the updates
+// of one column made by different lanes.  A column no product reached holds
+// RG_EMPTY, a NaN bit pattern that no product or sum carries (a NaN product
+// is stored as the canonical NaN), so no occupancy flags are kept.  The R
+// rows advance in lockstep (consecutive rows of the schedule share a flop
+// class, so their lengths are close) and are read out together: lane l of a
+// slot takes four columns of every 4*RG-column block, so all 32 lanes work
+// in every read-out step.
+// ---------------------------------------------------------------------------
+constexpr unsigned RG_EMPTY = 0xFFBADBADu;
+
+__device__ __forceinline__ void rg_add(float* acc, int c, float v, int d, int c0, int W, unsigned long long* err) {
+    const int lc = c - c0;
+    if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
+        unsigned x = __float_as_uint(v);
+        if (x == RG_EMPTY) x = 0x7FFFFFFFu;
+        const unsigned old = __float_as_uint(acc[lc]);
+        acc[lc] = old == RG_EMPTY ? __uint_as_float(x) : __uint_as_float(old) + __uint_as_float(x);
+    } else {
+        atomicOr(err, ERR_B_COL);
+    }
+}
+
+// One segment [s, s + L) of B times a, walked by the RG lanes of a slot.
+template <int RG>
+__device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* acc, long long s, int L, float a,
+                                           int gl, int d, int c0, int W, unsigned long long* err) {
+    const long long qbase = s & ~3LL, qend = s + L;
+    const int nq = L > 0 ? (int)((qend - qbase + 3) >> 2) : 0;
+    for (int q = gl; q < nq; q += RG) {
+        const long long qb = qbase + 4LL * q;
+        const int4 v0 = __ldg(P4 + (qb >> 1)), v1 = __ldg(P4 + (qb >> 1) + 1);
+        const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
+        const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (qb + u >= s && qb + u < qend) rg_add(acc, cs[u], a * __int_as_float(bs[u]), d, c0, W, err);
+    }
+}
+
+// Read-out of tile c0 of every slot (all lanes converged).
+template <int RG>
+__device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& out, long long out_end, int* Ci,
+                                        float* Cx, unsigned long long* err) {
+    const int gl = lane_id() % RG;
+    for (int base = 0; base < W; base += 4 * RG) {
+        const int cb = base + 4 * gl;
+        unsigned x[4] = {RG_EMPTY, RG_EMPTY, RG_EMPTY, RG_EMPTY};
+        unsigned f = 0;
+        if (cb < W) {
+            uint4* q = reinterpret_cast<uint4*>(acc + cb);
+            const uint4 v = *q;
+            x[0] = v.x;
+            x[1] = v.y;
+            x[2] = v.z;
+            x[3] = v.w;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) f |= (x[i] != RG_EMPTY ? 1u : 0u) << i;
+            if (f) *q = make_uint4(RG_EMPTY, RG_EMPTY, RG_EMPTY, RG_EMPTY);
+        }
+        const int cnt = __popc(f);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < RG; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o, RG);
+            if (gl >= o) incl += t;
+        }
+        const int tot = __shfl_sync(FULL, incl, RG - 1, RG);
+        long long pos = out + incl - cnt;
+        out += tot;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (f & (1u << i)) {
+                if (pos < out_end) {
+                    Ci[pos] = c0 + cb + i;
+                    Cx[pos] = __uint_as_float(x[i]);
+                } else {
+                    atomicOr(err, ERR_C_ROW);
+                }
+                ++pos;
+            }
+        }
+    }
+}
+
+// Entry e of the slot's row (e < len): its segment of B in tile t and value.
+template <class Seg>
+__device__ __forceinline__ void rg_entry(const NumParams& p, const Seg& seg, long long ei, long long& s, int& L,
+                                         float& a, unsigned long long* err) {
+    const int k = __ldg(p.Ai + ei);
+    if ((unsigned)k < (unsigned)p.nB) {
+        seg(k, s, L);
+        a = __ldg(p.Ax + ei);
+    } else {
+        atomicOr(err, ERR_A_COL);
+    }
+}
+
+// The warp's light rows: row groups idx0, idx0 + step, ... (step = R * warps).
+template <int RG>
+__device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, long long idx0, long long end,
+                                              long long step, const long long* mark) {
+    constexpr int R = 32 / RG;
+    static_assert(RG >= 4 && RG <= 16 && 32 % RG == 0, "lanes per row");
+    const int lane = lane_id(), g = lane / RG, gl = lane % RG;
+    const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);
+    float* acc = racc + g * p.W;
+    unsigned long long* err = &p.hdr->err;
+    for (long long idx = idx0; idx < end; idx += step) {
+        const long long my = idx + g;
+        long long a0 = 0, a1 = 0, out = 0, out_end = 0;
+        bool active = false;
+        if (my < end) {
+            const int row = __ldg(p.perm + my);
+            a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+            a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+            if (mark && is_split_row(mark, row, a1 - a0)) {
+                a1 = a0;  // taken as split parts
+            } else {
+                active = true;
+                out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+                out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+            }
+        }
+        const int len = (int)(a1 - a0);
+        const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        for (int t = 0; t < p.T; ++t) {
+            const int c0 = t * p.W;
+            for (int e = 0; e < lmax; e += RG) {
+                long long s = 0;
+                int L = 0;
+                float a = 0.0f;
+                if (e + gl < len) {
+                    if (p.T == 1) rg_entry(p, SegWhole{p.Bp, p.nnzB, p.d}, a0 + e + gl, s, L, a, err);
+                    else rg_entry(p, SegTile{p.tp, p.T + 1, t, p.W}, a0 + e + gl, s, L, a, err);
+                }
+                const int nu = lmax - e < RG ? lmax - e : RG;
+                for (int u = 0; u < nu; ++u) {
+                    const int src = g * RG + u;
+                    const long long su = shfl64(s, src);
+                    const int Lu = __shfl_sync(FULL, L, src);
+                    const float au = __shfl_sync(FULL, a, src);
+                    rg_segment<RG>(P4, acc, su, Lu, au, gl, p.d, c0, p.W, err);
+                    __syncwarp();
+                }
+            }
+            rg_emit<RG>(acc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
+            __syncwarp();
+        }
+        if (active && gl == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
+    }
+}
+
+template <bool VALUES, int G, bool PACKED, int RG>
+__global__ void __launch_bounds__(256, (RG ? 4 : 5)) k_numeric(NumParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     const int slot = VALUES ? 5 * p.W : p.W;  // bytes per warp: W floats + W flags
     for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
+    // row groups: R accumulators of W floats per warp after the block's flag region
+    float* rg_base = reinterpret_cast<float*>(smem + (size_t)nw * slot);
+    if (RG) {
+        for (int i = tid; i < nw * 32 / (RG ? RG : 1) * p.W; i += blockDim.x)
+            reinterpret_cast<unsigned*>(rg_base)[i] = RG_EMPTY;
+    }
     if (tid == 0) {
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -303,6 +486,12 @@ __global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
             numeric_row_cta<VALUES, G, BA>(p, ba, row, acc, flg, s_wcnt);
         }
     }
+    if constexpr (RG != 0) {
+        constexpr int R = 32 / (RG ? RG : 32);
+        rg_light_rows<RG>(p, rg_base + (size_t)warp * R * p.W, nheavy + ((long long)blockIdx.x * nw + warp) * R, nrows,
+                          (long long)gridDim.x * nw * R, mark);
+        return;
+    }
     float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
     unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
     NumRowBody<VALUES, G, BA> body{p, ba, acc, flg, &p.hdr->err, 0, 0};
@@ -333,33 +522,45 @@ cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-size_t numeric_dense_smem(int W, int warps, bool values) {
-    return (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
+size_t numeric_dense_smem(int W, int warps, bool values, int rg) {
+    size_t b = (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
+    if (rg) b += (size_t)warps * (32 / rg) * 4 * (size_t)W;
+    return b;
 }
 
-template <bool VALUES, int G, bool PACKED>
+template <bool VALUES, int G, bool PACKED, int RG>
 static cudaError_t launch_one(const NumParams& p, int warps, int sms, cudaStream_t st) {
-    const void* k = (const void*)k_numeric<VALUES, G, PACKED>;
-    const size_t smem = numeric_dense_smem(p.W, warps, VALUES);
+    const void* k = (const void*)k_numeric<VALUES, G, PACKED, RG>;
+    const size_t smem = numeric_dense_smem(p.W, warps, VALUES, RG);
     cudaError_t e;
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     const int grid = persistent_grid(k, 32 * warps, smem, sms);
     count_launch();
-    k_numeric<VALUES, G, PACKED><<<grid, 32 * warps, smem, st>>>(p);
+    k_numeric<VALUES, G, PACKED, RG><<<grid, 32 * warps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <bool VALUES, bool PACKED>
+template <bool VALUES, bool PACKED, int RG>
 static cudaError_t launch_g(const NumParams& p, int G, int warps, int sms, cudaStream_t st) {
+    if (RG && G != 1 && G != 2) G = 1;  // with row groups only heavy rows use G
     switch (G) {
-        case 1: return launch_one<VALUES, 1, PACKED>(p, warps, sms, st);
-        case 4: return launch_one<VALUES, 4, PACKED>(p, warps, sms, st);
-        case 8: return launch_one<VALUES, 8, PACKED>(p, warps, sms, st);
-        case 16: return launch_one<VALUES, 16, PACKED>(p, warps, sms, st);
-        case 32: return launch_one<VALUES, 32, PACKED>(p, warps, sms, st);
-        default: return cudaErrorInvalidValue;
+        case 1: return launch_one<VALUES, 1, PACKED, RG>(p, warps, sms, st);
+        case 2:
+            if constexpr (VALUES && PACKED) return launch_one<VALUES, 2, PACKED, RG>(p, warps, sms, st);
+            else return launch_one<VALUES, 1, PACKED, RG>(p, warps, sms, st);
+        default:
+            if constexpr (RG == 0) {
+                switch (G) {
+                    case 4: return launch_one<VALUES, 4, PACKED, 0>(p, warps, sms, st);
+                    case 8: return launch_one<VALUES, 8, PACKED, 0>(p, warps, sms, st);
+                    case 16: return launch_one<VALUES, 16, PACKED, 0>(p, warps, sms, st);
+                    case 32: return launch_one<VALUES, 32, PACKED, 0>(p, warps, sms, st);
+                }
+            }
+            return cudaErrorInvalidValue;
     }
 }
 
@@ -373,11 +574,17 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
     const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
-    if (values) {
-        if (Bpk) return launch_g<true, true>(p, G, cfg.warps_per_cta, cfg.sms, st);
-        return launch_g<true, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
+    const int w = cfg.warps_per_cta;
+    if (values && Bpk) {  // row groups need the padded packed copy
+        switch (cfg.row_lanes) {
+            case 4: return launch_g<true, true, 4>(p, G, w, cfg.sms, st);
+            case 8: return launch_g<true, true, 8>(p, G, w, cfg.sms, st);
+            case 16: return launch_g<true, true, 16>(p, G, w, cfg.sms, st);
+            default: return launch_g<true, true, 0>(p, G, w, cfg.sms, st);
+        }
     }
-    return launch_g<false, false>(p, G, cfg.warps_per_cta, cfg.sms, st);
+    if (values) return launch_g<true, false, 0>(p, G, w, cfg.sms, st);
+    return launch_g<false, false, 0>(p, G, w, cfg.sms, st);
 }
 
 }  // namespace ts

@@ -272,6 +272,7 @@ struct SymVisit {
     unsigned* bm;  // bitmap words, or (FL) dpad occupancy bytes
     int d;
     unsigned long long* err;
+    long long nnzB;
     struct Item {
         int c;
     };
@@ -296,6 +297,26 @@ struct SymVisit {
     }
     __device__ __forceinline__ void step1(long long j, float, int, bool ok) {
         if (ok) mark(__ldg(Bi + j));
+    }
+    // quads: one 16-byte load of four columns (Bi is 16-byte aligned), or
+    // single loads for a quad that reaches past the end of B
+    __device__ __forceinline__ void quads(const Chunk& ch, int nv) {
+        quads_loaded(ch, nv, [&](long long qb, long long s, long long end, float) {
+            int c[4];
+            if (qb + 4 <= nnzB) {
+                const int4 v = __ldg(reinterpret_cast<const int4*>(Bi + qb));
+                c[0] = v.x;
+                c[1] = v.y;
+                c[2] = v.z;
+                c[3] = v.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = qb + u < end ? __ldg(Bi + qb + u) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (qb + u >= s && qb + u < end) mark(c[u]);
+        });
     }
 };
 
@@ -334,6 +355,7 @@ template <int G, bool FL, class Seg>
 __device__ __forceinline__ void sym_chunk(const SymParams& p, long long e0, int nv, SymVisit<FL>& vis,
                                           unsigned long long* err) {
     if constexpr (G == 1) expand_chunk(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
+    else if constexpr (G == 2) vis.quads(load_chunk(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, err), nv);
     else grouped_chunk<G>(e0, nv, p.Ai, (const float*)nullptr, p.nB, p.segB, vis, err);
 }
 
@@ -344,7 +366,7 @@ struct SymRowBody {
     unsigned* bm;
     unsigned long long* err;
     __device__ __forceinline__ void gather(int, long long a0, long long a1, const Chunk& ch0, int nv0, int) {
-        SymVisit<FL> vis{p.Bi, bm, p.d, err};
+        SymVisit<FL> vis{p.Bi, bm, p.d, err, p.segB.nnzB};
         expand_any<G>(ch0, nv0, a0, vis);
         for (long long e0 = a0 + 32; e0 < a1; e0 += 32) {
             const int nv = (int)(a1 - e0 < 32 ? a1 - e0 : 32);
@@ -396,7 +418,7 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         __shared__ int s_last;
         SplitItem it;
         while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
-            SymVisit<FL> vis{p.Bi, smem_u, p.d, err};
+            SymVisit<FL> vis{p.Bi, smem_u, p.d, err, p.segB.nnzB};
             for (long long e0 = it.e0 + 32LL * warp; e0 < it.e1; e0 += 32LL * nw)
                 sym_chunk<G, FL, SegWhole>(p, e0, (int)(it.e1 - e0 < 32 ? it.e1 - e0 : 32), vis, err);
             __syncthreads();
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
         if (is_split_row(mark, row, a1 - a0)) continue;
-        SymVisit<FL> vis{p.Bi, smem_u, p.d, err};
+        SymVisit<FL> vis{p.Bi, smem_u, p.d, err, p.segB.nnzB};
         for (long long e0 = a0 + 32LL * warp; e0 < a1; e0 += 32LL * nw)
             sym_chunk<G, FL, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
         __syncthreads();
@@ -508,8 +530,11 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)p.slot * cfg.warps_per_cta;
     const void* k;
-    switch (cfg.group) {
+    int group = cfg.group;
+    if (group == 2 && (reinterpret_cast<uintptr_t>(B.col) & 15)) group = 16;  // quads need aligned columns
+    switch (group) {
         case 1: k = fl ? (const void*)k_symbolic<1, true> : (const void*)k_symbolic<1, false>; break;
+        case 2: k = fl ? (const void*)k_symbolic<2, true> : (const void*)k_symbolic<2, false>; break;
         case 4: k = fl ? (const void*)k_symbolic<4, true> : (const void*)k_symbolic<4, false>; break;
         case 8: k = fl ? (const void*)k_symbolic<8, true> : (const void*)k_symbolic<8, false>; break;
         case 16: k = fl ? (const void*)k_symbolic<16, true> : (const void*)k_symbolic<16, false>; break;

@@ -43,7 +43,7 @@ def test_host_side_errors(lib):
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(Bbig), 0, None, ctypes.byref(h)) == N.TS_ERR_UNSUPPORTED
     bad_t = N.Tuning(0, 48, 0, 0, 0, 0, 0, 0, 0, 0, 0)
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bad_t), ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
-    for bad in ({"bwd_vec": 3}, {"accum": 4}, {"accum": N.ACC_COPIES, "col_tile": 4096 + 32}):
+    for bad in ({"bwd_group": 3}, {"group": 64}, {"row_lanes": 2}, {"accum": 4}, {"accum": N.ACC_COPIES, "col_tile": 4096 + 32}):
         bt = N.Tuning.from_dict(bad)
         assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bt), ctypes.byref(h)) \
             == N.TS_ERR_INVALID_ARG, bad
@@ -51,9 +51,9 @@ def test_host_side_errors(lib):
     t = N.Tuning()
     assert lib.ts_plan_get_tuning(h, ctypes.byref(t)) == N.TS_OK
     assert t.accum == N.ACC_DENSE and t.col_tile == 64 and t.warps_per_cta == 8
-    assert t.group in (1, 4, 8, 16, 32) and t.pack_b in (1, 2)
-    assert t.sym_group in (1, 4, 8, 16, 32) and t.bwd_group in (1, 4, 8, 16, 32)
-    assert t.bwd_vec in (1, 2)
+    assert t.group in (1, 2, 4, 8, 16, 32) and t.pack_b in (1, 2)
+    assert t.sym_group in (1, 2, 4, 8, 16, 32) and t.bwd_group in (1, 2, 4, 8, 16, 32)
+    assert t.row_lanes in (4, 8, 16, 32)
     sz = ctypes.c_size_t()
     assert lib.ts_workspace_size(h, ctypes.byref(sz)) == N.TS_OK and sz.value > 100 * 12
     # missing workspace and missing C row pointers are argument errors

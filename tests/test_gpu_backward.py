@@ -38,8 +38,8 @@ def _run(A, B, tuning=None, seed=1):
                                     {"warps_per_cta": 1}, {"group": 1}, {"group": 4}, {"group": 32},
                                     {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64},
                                     {"bwd_group": 1}, {"bwd_group": 4}, {"bwd_group": 32, "sym_group": 1},
-                                    {"bwd_vec": 2}, {"bwd_vec": 2, "bwd_group": 16}, {"bwd_vec": 1, "pack_b": 2},
-                                    {"bwd_vec": 1, "cta_min_flops": 1}, {"bwd_vec": 1, "warps_per_cta": 1}])
+                                    {"bwd_group": 16}, {"bwd_group": 2}, {"bwd_group": 2, "pack_b": 2},
+                                    {"bwd_group": 2, "cta_min_flops": 1}, {"bwd_group": 2, "warps_per_cta": 1}])
 def test_backward_matches_oracle(tuning):
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -48,8 +48,8 @@ def test_backward_matches_oracle(tuning):
     assert np.all(np.abs(dB - rB) <= REL * bB), np.max(np.abs(dB - rB) / np.maximum(bB, 1e-30))
 
 
-@pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}, {"bwd_vec": 2},
-                                    {"bwd_vec": 1, "cta_min_flops": 16}])
+@pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}, {"bwd_group": 16},
+                                    {"bwd_group": 2, "cta_min_flops": 16}])
 def test_backward_ragged_and_empty_rows(tuning):
     A, B = synth.er_product(n=3000, k=5, d=100, density=0.05, seed=51)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -68,7 +68,7 @@ def test_backward_unaligned_db_and_b_tail():
             break
     assert B.nnz % 4 != 0
     Ad, Bd = dev(A), dev(B)
-    plan = Plan(Ad, Bd)
+    plan = Plan(Ad, Bd, tuning={"bwd_group": 2})
     C = plan.forward(Ad, Bd)
     dC = synth.grad_output(C.nnz, 5)
     rp, col, _ = C.to_host()

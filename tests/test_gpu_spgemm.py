@@ -42,6 +42,10 @@ TUNINGS = [
     {"accum": ACC_COPIES, "group": 16}, {"accum": ACC_COPIES, "group": 32, "cta_min_flops": 1},
     {"accum": ACC_COPIES, "col_tile": 32}, {"accum": ACC_COPIES, "pack_b": 2, "warps_per_cta": 1},
     {"accum": ACC_COPIES, "group": 8, "cta_min_flops": 16, "warps_per_cta": 3},
+    {"group": 2}, {"sym_group": 2}, {"group": 2, "sym_group": 2, "cta_min_flops": 1},   # quads
+    {"group": 2, "pack_b": 2}, {"group": 2, "col_tile": 32}, {"sym_group": 2, "warps_per_cta": 1},
+    {"row_lanes": 4}, {"row_lanes": 8}, {"row_lanes": 16}, {"row_lanes": 4, "col_tile": 32},   # row groups
+    {"row_lanes": 4, "pack_b": 2}, {"row_lanes": 8, "cta_min_flops": 1 << 20, "warps_per_cta": 2},
 ]
 
 
@@ -59,7 +63,8 @@ def test_er_full_size(er_case, tuning):
 
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH},
-                                    {"stage": 2, "group": 1}, {"stage": 2, "group": 32}, {"accum": ACC_COPIES}])
+                                    {"stage": 2, "group": 1}, {"stage": 2, "group": 32}, {"accum": ACC_COPIES},
+                                    {"group": 2, "sym_group": 2}])
 def test_er_boolean(er_case, tuning):
     A, B = er_case
     C = spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=tuning)
@@ -72,7 +77,9 @@ def test_er_boolean(er_case, tuning):
                                     {"stage": 2, "group": 8}, {"stage": 2, "group": 32, "pack_b": 1},
                                     {"stage": 2, "pack_b": 1, "col_tile": 64}, {"col_tile": 64, "warps_per_cta": 2},
                                     {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "group": 8, "col_tile": 64},
-                                    {"accum": ACC_COPIES, "cta_min_flops": 128, "pack_b": 2}])
+                                    {"accum": ACC_COPIES, "cta_min_flops": 128, "pack_b": 2},
+                                    {"group": 2, "sym_group": 2}, {"group": 2, "col_tile": 64, "cta_min_flops": 128},
+                                    {"row_lanes": 4}, {"row_lanes": 8, "col_tile": 64}, {"row_lanes": 16, "group": 2}])
 def test_rmat_embedding_small(tuning):
     A, B = synth.rmat_embedding(scale=13, edge_factor=16, d=256, density=0.05, seed=31)
     C = spgemm(dev(A), dev(B), tuning=tuning)
@@ -117,7 +124,9 @@ def test_small_shapes_and_ragged_d(n, d):
     for t in (None, {"col_tile": 32}, {"cta_min_flops": 1}, {"accum": ACC_HASH, "hash_slots": 256},
               {"stage": 2, "group": 1}, {"stage": 2, "group": 4, "pack_b": 1},
               {"stage": 2, "group": 32, "cta_min_flops": 1}, {"warps_per_cta": 1}, {"accum": ACC_COPIES},
-              {"accum": ACC_COPIES, "group": 32, "cta_min_flops": 1}, {"accum": ACC_COPIES, "col_tile": 32}):
+              {"accum": ACC_COPIES, "group": 32, "cta_min_flops": 1}, {"accum": ACC_COPIES, "col_tile": 32},
+              {"group": 2, "sym_group": 2}, {"group": 2, "sym_group": 2, "cta_min_flops": 1},
+              {"row_lanes": 4}, {"row_lanes": 16, "col_tile": 32}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -138,7 +147,7 @@ def test_identity_is_exact():
     B.val = synth.normal(B.nnz, 8)
     I = CSR(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n, np.float32))
     for t in (None, {"col_tile": 32}, {"accum": ACC_HASH}, {"accum": ACC_COPIES},
-              {"accum": ACC_COPIES, "cta_min_flops": 1}):
+              {"accum": ACC_COPIES, "cta_min_flops": 1}, {"group": 2, "sym_group": 2}, {"row_lanes": 4}):
         rp, col, val = spgemm(dev(I), dev(B), tuning=t).to_host()
         np.testing.assert_array_equal(rp, B.rowptr)
         np.testing.assert_array_equal(col, B.col)
@@ -154,7 +163,9 @@ def test_hub_row_and_dense_b():
     B.val = synth.uniform(B.nnz, 12)
     for t in (None, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 2}, {"stage": 2, "group": 1},
               {"stage": 2, "group": 32}, {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "group": 8},
-              {"accum": ACC_COPIES, "cta_min_flops": 1 << 20}):
+              {"accum": ACC_COPIES, "cta_min_flops": 1 << 20}, {"group": 2, "sym_group": 2},
+              {"group": 2, "sym_group": 2, "cta_min_flops": 1 << 20}, {"row_lanes": 4},
+              {"row_lanes": 8, "cta_min_flops": 1 << 20}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
@@ -163,7 +174,7 @@ def embed_full():
     return synth.rmat_embedding()
 
 
-@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}])
+@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"group": 2, "sym_group": 2}, {"row_lanes": 4}])
 def test_embedding_full_size_sampled(embed_full, tuning):
     # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %
     A, B = embed_full
@@ -227,7 +238,9 @@ def test_autotune_keeps_results():
 
 @pytest.mark.parametrize("tuning", [None, {"col_tile": 256}, {"col_tile": 256, "stage": 2, "group": 1},
                                     {"stage": 2, "pack_b": 1}, {"stage": 2}, {"accum": ACC_COPIES},
-                                    {"accum": ACC_COPIES, "col_tile": 256}])
+                                    {"accum": ACC_COPIES, "col_tile": 256}, {"group": 2, "sym_group": 2},
+                                    {"group": 2, "sym_group": 2, "col_tile": 256}, {"row_lanes": 8},
+                                    {"row_lanes": 4, "col_tile": 256}])
 def test_split_rows_with_tiles(tuning):
     # rows longer than 1024 entries of A are cut into parts processed by
     # different blocks and merged through a staging row; with d = 1024 and
@@ -256,12 +269,12 @@ def test_more_long_rows_than_split_slots():
     B.val = synth.uniform(B.nnz, 77)
     rng2 = np.random.default_rng(1)
     rows = rng2.choice(n, 400, replace=False)
-    for t in (None, {"accum": ACC_COPIES}):
+    for t in (None, {"accum": ACC_COPIES}, {"row_lanes": 4}):
         compare_rows(spgemm(dev(A), dev(B), tuning=t), A, B, rows)
 
 
 @pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "cta_min_flops": 1},
-                                    {"accum": ACC_HASH}])
+                                    {"accum": ACC_HASH}, {"group": 2}, {"row_lanes": 4}])
 def test_nan_products_keep_their_columns(tuning):
     # NaN values of B (one of them with the copies kernel's empty-column bit
     # pattern) must give NaN entries at their columns, never drop them
@@ -278,3 +291,22 @@ def test_nan_products_keep_their_columns(tuning):
     assert nan.any()
     assert np.array_equal(np.isnan(val), nan)
     assert np.all(np.abs(val[~nan] - Cx[~nan]) <= 1e-5 * bound[~nan])
+
+
+@pytest.mark.parametrize("tuning", [{"group": 2, "sym_group": 2}, None])
+def test_unaligned_b_columns_and_b_tail(tuning):
+    # B's column array one int into a buffer (not 16-byte aligned: symbolic
+    # quads must not be used) and nnz(B) not a multiple of four (the last
+    # quads of B take single loads)
+    for seed in range(91, 110):
+        A, B = synth.er_product(n=1500, k=6, d=80, density=0.09, seed=seed)
+        if B.nnz % 4:
+            break
+    assert B.nnz % 4
+    Bd = dev(B)
+    buf = torch.zeros(B.nnz + 8, dtype=torch.int32, device="cuda")
+    buf[1:1 + B.nnz] = Bd.col
+    Bu = DeviceCSR(B.nrows, B.ncols, Bd.rowptr, buf[1:1 + B.nnz], Bd.val)
+    assert Bu.col.data_ptr() % 16 != 0
+    for Bx in (Bd, Bu):
+        compare_full(spgemm(dev(A), Bx, tuning=tuning), A, B)
