@@ -112,7 +112,9 @@ typedef struct ts_csr_desc {
  *  row_lanes      numeric pass (plus-times, pack_b = 1, dense accumulator):
  *                 lanes per light row.  32 = one warp per row; 4, 8 or 16 =
  *                 row groups, 32/row_lanes rows per warp in lockstep, each
- *                 with its own accumulator and no atomics.
+ *                 with its own accumulator and no atomics (4: four entries
+ *                 of B per lane, 8 and 16: two), in a kernel launched right
+ *                 behind the one for the heavy rows.
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.

@@ -176,13 +176,15 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.bwd_group = force.bwd_group ? force.bwd_group : auto_group(nB, nnzB, 2);
     t.stage = force.stage ? force.stage : 2;
     t.pack_b = force.pack_b ? force.pack_b : 1;
-    t.row_lanes = force.row_lanes ? force.row_lanes : 32;
+    // row groups of 8 lanes (pairs) where four rows' accumulators fit well
+    // (W <= 256); one warp per light row for wider tiles
+    t.row_lanes = force.row_lanes ? force.row_lanes : 0;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
     if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
         return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 2, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
-    if (t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 && t.row_lanes != 32)
+    if (t.row_lanes != 0 && t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 && t.row_lanes != 32)
         return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes must be 4, 8, 16 or 32");
     if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES)
         return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH or TS_ACC_COPIES");
@@ -191,6 +193,7 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
         return fail(TS_ERR_INVALID_ARG, "tuning: col_tile must be a multiple of 32 in [32, 4096]");
     if (t.col_tile > dpad) t.col_tile = (int)dpad;
+    if (t.row_lanes == 0) t.row_lanes = t.col_tile <= 256 ? 8 : 32;
     if (t.cta_min_flops < 1) return fail(TS_ERR_INVALID_ARG, "tuning: cta_min_flops must be >= 1");
     if (t.warps_per_cta < 1 || t.warps_per_cta > 8)
         return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 8]");
@@ -454,7 +457,7 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
         } else {
             LaunchCfg ncfg = cfg;
             if (ncfg.row_lanes != 32 &&
-                (!vals || !bpk || numeric_dense_smem(L.W, cfg.warps_per_cta, true, ncfg.row_lanes) > 220 * 1024))
+                (!vals || !bpk || numeric_light_smem(L.W, cfg.warps_per_cta, ncfg.row_lanes) > 220 * 1024))
                 ncfg.row_lanes = 32;  // row groups need the packed copy and room for their accumulators
             TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, ncfg,
                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),

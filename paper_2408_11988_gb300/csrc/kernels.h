@@ -102,7 +102,9 @@ cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, i
                                 bool values, const Sched& s, const LaunchCfg& cfg,
                                 const long long* Cp, int* Ci, float* Cx, long long nnzC,
                                 cudaStream_t st);
-size_t numeric_dense_smem(int W, int warps, bool values, int row_lanes = 0);
+size_t numeric_dense_smem(int W, int warps, bool values);
+// Dynamic shared memory of the row-group light-row kernel (0: bad row_lanes).
+size_t numeric_light_smem(int W, int warps, int row_lanes);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).

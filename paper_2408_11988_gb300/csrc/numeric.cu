@@ -285,41 +285,80 @@ struct NumRowBody {
 // the columns of one segment are distinct, so acc[c] += A(i,k) * B(k,c) is a
 // plain load and store, and __syncwarp between segments orders the updates
 // of one column made by different lanes.  A column no product reached holds
-// RG_EMPTY, a NaN bit pattern that no product or sum carries (a NaN product
-// is stored as the canonical NaN), so no occupancy flags are kept.  The R
-// rows advance in lockstep (consecutive rows of the schedule share a flop
-// class, so their lengths are close) and are read out together: lane l of a
-// slot takes four columns of every 4*RG-column block, so all 32 lanes work
-// in every read-out step.
+// RG_EMPTY, a signalling-NaN bit pattern: arithmetic never delivers a
+// signalling NaN (a NaN result is quiet), so no product or sum carries it and
+// no occupancy flags are kept.  The R rows advance in lockstep (consecutive
+// rows of the schedule share a flop class, so their lengths are close) and
+// are read out together: lane l of a slot takes four columns of every
+// 4*RG-column block, so all 32 lanes work in every read-out step.
 // ---------------------------------------------------------------------------
-constexpr unsigned RG_EMPTY = 0xFFBADBADu;
+constexpr unsigned RG_EMPTY = 0xFFBADBADu;  // exponent all ones, quiet bit clear
+static_assert((RG_EMPTY & 0x7F800000u) == 0x7F800000u && (RG_EMPTY & 0x00400000u) == 0 && (RG_EMPTY & 0x003FFFFFu),
+              "RG_EMPTY must be a signalling NaN");
 
-__device__ __forceinline__ void rg_add(float* acc, int c, float v, int d, int c0, int W, unsigned long long* err) {
-    const int lc = c - c0;
-    if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
-        unsigned x = __float_as_uint(v);
-        if (x == RG_EMPTY) x = 0x7FFFFFFFu;
-        const unsigned old = __float_as_uint(acc[lc]);
-        acc[lc] = old == RG_EMPTY ? __uint_as_float(x) : __uint_as_float(old) + __uint_as_float(x);
-    } else {
-        atomicOr(err, ERR_B_COL);
+// acc[lc] += v, lc already checked against [0, W) and d.
+__device__ __forceinline__ void rg_add(float* acc, int lc, float v) {
+    const float old = acc[lc];
+    acc[lc] = __float_as_uint(old) == RG_EMPTY ? v : old + v;
+}
+
+// A segment of B as a slot walks it: its first position rounded down to a
+// multiple of E (qbase), the positions to skip before the segment (lead),
+// the positions covered from qbase (span) and A's value a.  E consecutive
+// entries per lane (E = 4: two 16-byte loads; E = 2: one), lane gl taking
+// groups gl, gl + RG, ...
+struct RgSeg {
+    long long qbase;
+    int lead, span;
+    float a;
+};
+
+template <int E>
+__device__ __forceinline__ RgSeg rg_seg_of(long long s, int L, float a) {
+    RgSeg q;
+    q.qbase = s & ~(long long)(E - 1);
+    q.lead = (int)(s - q.qbase);
+    q.span = L > 0 ? q.lead + L : 0;
+    q.a = a;
+    return q;
+}
+
+// Loads of group q of a segment (entries qbase + E*q ...), if it exists.
+template <int E>
+__device__ __forceinline__ void rg_fetch(const int4* __restrict__ P4, const RgSeg& sg, int q, int4& v0, int4& v1) {
+    if (E * q < sg.span) {
+        const long long qb = sg.qbase + (long long)E * q;
+        v0 = __ldg(P4 + (qb >> 1));
+        if constexpr (E == 4) v1 = __ldg(P4 + (qb >> 1) + 1);
     }
 }
 
-// One segment [s, s + L) of B times a, walked by the RG lanes of a slot.
-template <int RG>
-__device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* acc, long long s, int L, float a,
-                                           int gl, int d, int c0, int W, unsigned long long* err) {
-    const long long qbase = s & ~3LL, qend = s + L;
-    const int nq = L > 0 ? (int)((qend - qbase + 3) >> 2) : 0;
-    for (int q = gl; q < nq; q += RG) {
-        const long long qb = qbase + 4LL * q;
-        const int4 v0 = __ldg(P4 + (qb >> 1)), v1 = __ldg(P4 + (qb >> 1) + 1);
-        const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
-        const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+// Accumulate group q of a segment from its loaded entries.
+template <int E>
+__device__ __forceinline__ void rg_apply(float* acc, const RgSeg& sg, int q, const int4& v0, const int4& v1, int Wd,
+                                         int c0, unsigned long long* err) {
+    const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
+    const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+    const int p0 = E * q;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (qb + u >= s && qb + u < qend) rg_add(acc, cs[u], a * __int_as_float(bs[u]), d, c0, W, err);
+    for (int u = 0; u < E; ++u) {
+        if (p0 + u >= sg.lead && p0 + u < sg.span) {
+            const int lc = cs[u] - c0;
+            if ((unsigned)lc < (unsigned)Wd) rg_add(acc, lc, sg.a * __int_as_float(bs[u]));
+            else atomicOr(err, ERR_B_COL);
+        }
+    }
+}
+
+// A whole segment whose first group (q = gl) is already loaded into v0/v1.
+template <int RG, int E>
+__device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* acc, const RgSeg& sg, int gl,
+                                           const int4& v0, const int4& v1, int Wd, int c0, unsigned long long* err) {
+    if (E * gl < sg.span) rg_apply<E>(acc, sg, gl, v0, v1, Wd, c0, err);
+    for (int q = gl + RG; E * q < sg.span; q += RG) {
+        int4 w0 = make_int4(0, 0, 0, 0), w1 = make_int4(0, 0, 0, 0);
+        rg_fetch<E>(P4, sg, q, w0, w1);
+        rg_apply<E>(acc, sg, q, w0, w1, Wd, c0, err);
     }
 }
 
@@ -328,6 +367,11 @@ template <int RG>
 __device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& out, long long out_end, int* Ci,
                                         float* Cx, unsigned long long* err) {
     const int gl = lane_id() % RG;
+    const long long r = out_end - out;
+    const int room = r < 0x7FFFFFFFLL ? (int)r : 0x7FFFFFFF;
+    int* ci = Ci + out;
+    float* cx = Cx + out;
+    int o = 0;  // entries of this slot's row written so far in this tile
     for (int base = 0; base < W; base += 4 * RG) {
         const int cb = base + 4 * gl;
         unsigned x[4] = {RG_EMPTY, RG_EMPTY, RG_EMPTY, RG_EMPTY};
@@ -346,19 +390,18 @@ __device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& ou
         const int cnt = __popc(f);
         int incl = cnt;
 #pragma unroll
-        for (int o = 1; o < RG; o <<= 1) {
-            const int t = __shfl_up_sync(FULL, incl, o, RG);
-            if (gl >= o) incl += t;
+        for (int k = 1; k < RG; k <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, k, RG);
+            if (gl >= k) incl += t;
         }
-        const int tot = __shfl_sync(FULL, incl, RG - 1, RG);
-        long long pos = out + incl - cnt;
-        out += tot;
+        int pos = o + incl - cnt;
+        o += __shfl_sync(FULL, incl, RG - 1, RG);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (f & (1u << i)) {
-                if (pos < out_end) {
-                    Ci[pos] = c0 + cb + i;
-                    Cx[pos] = __uint_as_float(x[i]);
+                if (pos < room) {
+                    ci[pos] = c0 + cb + i;
+                    cx[pos] = __uint_as_float(x[i]);
                 } else {
                     atomicOr(err, ERR_C_ROW);
                 }
@@ -366,18 +409,85 @@ __device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& ou
             }
         }
     }
+    out += o;
 }
 
 // Entry e of the slot's row (e < len): its segment of B in tile t and value.
-template <class Seg>
-__device__ __forceinline__ void rg_entry(const NumParams& p, const Seg& seg, long long ei, long long& s, int& L,
-                                         float& a, unsigned long long* err) {
-    const int k = __ldg(p.Ai + ei);
-    if ((unsigned)k < (unsigned)p.nB) {
-        seg(k, s, L);
+// Column index and value of entry ei of A (k = -1 past the row's end).
+__device__ __forceinline__ void rg_load_a(const NumParams& p, long long ei, bool ok, int& k, float& a) {
+    k = -1;
+    a = 0.0f;
+    if (ok) {
+        k = __ldg(p.Ai + ei);
         a = __ldg(p.Ax + ei);
-    } else {
-        atomicOr(err, ERR_A_COL);
+    }
+}
+
+// Segment of B's row k in the current tile (empty for k = -1; bad k is an
+// input error).
+template <class Seg>
+__device__ __forceinline__ void rg_seg(const NumParams& p, const Seg& seg, int k, bool ok, long long& s, int& L,
+                                       unsigned long long* err) {
+    s = 0;
+    L = 0;
+    if (!ok) return;
+    if ((unsigned)k < (unsigned)p.nB) seg(k, s, L);
+    else atomicOr(err, ERR_A_COL);
+}
+
+// Chunks of RG entries of every slot's row for tile t, software-pipelined:
+// while chunk c is accumulated, the segments of chunk c+1 (B's row pointers)
+// and the entries of chunk c+2 (A's columns and values) are loaded.
+template <int RG, class Seg>
+__device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, const int4* P4, float* acc, long long a0,
+                                        int len, int lmax, int c0, int Wd, unsigned long long* err) {
+    constexpr int E = RG == 4 ? 4 : 2;
+    const int lane = lane_id(), g = lane / RG, gl = lane % RG;
+    int k0, k1;
+    float x0, x1;
+    rg_load_a(p, a0 + gl, gl < len, k0, x0);
+    rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
+    long long s;
+    int L;
+    rg_seg(p, seg, k0, gl < len, s, L, err);
+    // segment pipeline: the next segment's description and first group
+    RgSeg nxt = rg_seg_of<E>(shfl64(s, g * RG), __shfl_sync(FULL, L, g * RG), __shfl_sync(FULL, x0, g * RG));
+    int4 n0 = make_int4(0, 0, 0, 0), n1 = make_int4(0, 0, 0, 0);
+    rg_fetch<E>(P4, nxt, gl, n0, n1);
+    for (int e = 0; e < lmax; e += RG) {
+        int k2;
+        float x2;
+        long long ns;
+        int nL;
+        rg_load_a(p, a0 + e + 2 * RG + gl, e + 2 * RG + gl < len, k2, x2);
+        rg_seg(p, seg, k1, e + RG + gl < len, ns, nL, err);
+        const int nu = lmax - e < RG ? lmax - e : RG;
+        for (int u = 0; u < nu; ++u) {
+            const RgSeg cur = nxt;
+            const int4 c0v = n0, c1v = n1;
+            // describe and start loading the segment after this one
+            long long s2 = 0;
+            int L2 = 0;
+            float a2 = 0.0f;
+            if (u + 1 < nu) {
+                s2 = shfl64(s, g * RG + u + 1);
+                L2 = __shfl_sync(FULL, L, g * RG + u + 1);
+                a2 = __shfl_sync(FULL, x0, g * RG + u + 1);
+            } else {  // first segment of the next chunk (empty past the rows' ends)
+                s2 = shfl64(ns, g * RG);
+                L2 = __shfl_sync(FULL, nL, g * RG);
+                a2 = __shfl_sync(FULL, x1, g * RG);
+            }
+            nxt = rg_seg_of<E>(s2, L2, a2);
+            rg_fetch<E>(P4, nxt, gl, n0, n1);
+            rg_segment<RG, E>(P4, acc, cur, gl, c0v, c1v, Wd, c0, err);
+            __syncwarp();
+        }
+        s = ns;
+        L = nL;
+        x0 = x1;
+        k1 = k2;
+        x1 = x2;
     }
 }
 
@@ -411,24 +521,9 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
         const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
         for (int t = 0; t < p.T; ++t) {
             const int c0 = t * p.W;
-            for (int e = 0; e < lmax; e += RG) {
-                long long s = 0;
-                int L = 0;
-                float a = 0.0f;
-                if (e + gl < len) {
-                    if (p.T == 1) rg_entry(p, SegWhole{p.Bp, p.nnzB, p.d}, a0 + e + gl, s, L, a, err);
-                    else rg_entry(p, SegTile{p.tp, p.T + 1, t, p.W}, a0 + e + gl, s, L, a, err);
-                }
-                const int nu = lmax - e < RG ? lmax - e : RG;
-                for (int u = 0; u < nu; ++u) {
-                    const int src = g * RG + u;
-                    const long long su = shfl64(s, src);
-                    const int Lu = __shfl_sync(FULL, L, src);
-                    const float au = __shfl_sync(FULL, a, src);
-                    rg_segment<RG>(P4, acc, su, Lu, au, gl, p.d, c0, p.W, err);
-                    __syncwarp();
-                }
-            }
+            const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
+            if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err);
+            else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err);
             rg_emit<RG>(acc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
             __syncwarp();
         }
@@ -436,20 +531,44 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
     }
 }
 
-template <bool VALUES, int G, bool PACKED, int RG>
-__global__ void __launch_bounds__(256, (RG ? 4 : 5)) k_numeric(NumParams p) {
+// Light rows only, in row groups; R = 32/RG accumulators of W floats per warp.
+// Launched behind k_numeric (which then skips light rows) with programmatic
+// dependent launch: its blocks may start while k_numeric's last blocks run.
+// Before exiting, each block waits for k_numeric to complete, so that work
+// queued after this kernel sees all of C.
+template <int RG>
+__global__ void __launch_bounds__(256, 4) k_numeric_light(NumParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_nheavy, s_nrows;
+    constexpr int R = 32 / RG;
+    const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
+    float* racc = reinterpret_cast<float*>(smem);
+    for (int i = tid; i < nw * R * p.W; i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    const long long* mark = p.s.stg_vals != nullptr ? p.s.flops : nullptr;
+    rg_light_rows<RG>(p, racc + (size_t)warp * R * p.W, s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
+                      (long long)gridDim.x * nw * R, mark);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <bool VALUES, int G, bool PACKED>
+__global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
+    // a light-row kernel launched behind this one may start on SMs this
+    // grid frees (the two touch disjoint rows of C)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     const int slot = VALUES ? 5 * p.W : p.W;  // bytes per warp: W floats + W flags
     for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
-    // row groups: R accumulators of W floats per warp after the block's flag region
-    float* rg_base = reinterpret_cast<float*>(smem + (size_t)nw * slot);
-    if (RG) {
-        for (int i = tid; i < nw * 32 / (RG ? RG : 1) * p.W; i += blockDim.x)
-            reinterpret_cast<unsigned*>(rg_base)[i] = RG_EMPTY;
-    }
+
     if (tid == 0) {
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -486,12 +605,7 @@ __global__ void __launch_bounds__(256, (RG ? 4 : 5)) k_numeric(NumParams p) {
             numeric_row_cta<VALUES, G, BA>(p, ba, row, acc, flg, s_wcnt);
         }
     }
-    if constexpr (RG != 0) {
-        constexpr int R = 32 / (RG ? RG : 32);
-        rg_light_rows<RG>(p, rg_base + (size_t)warp * R * p.W, nheavy + ((long long)blockIdx.x * nw + warp) * R, nrows,
-                          (long long)gridDim.x * nw * R, mark);
-        return;
-    }
+    if (p.skip_light) return;
     float* acc = reinterpret_cast<float*>(smem + (size_t)warp * slot);
     unsigned char* flg = smem + (size_t)warp * slot + (VALUES ? 4 * p.W : 0);
     NumRowBody<VALUES, G, BA> body{p, ba, acc, flg, &p.hdr->err, 0, 0};
@@ -522,46 +636,65 @@ cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-size_t numeric_dense_smem(int W, int warps, bool values, int rg) {
-    size_t b = (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
-    if (rg) b += (size_t)warps * (32 / rg) * 4 * (size_t)W;
-    return b;
+size_t numeric_dense_smem(int W, int warps, bool values) {
+    return (size_t)warps * (values ? 5 * (size_t)W : (size_t)W);
 }
 
-template <bool VALUES, int G, bool PACKED, int RG>
+size_t numeric_light_smem(int W, int warps, int rg) {
+    if (rg != 4 && rg != 8 && rg != 16) return 0;
+    return (size_t)warps * (32 / rg) * 4 * (size_t)W;
+}
+
+template <bool VALUES, int G, bool PACKED>
 static cudaError_t launch_one(const NumParams& p, int warps, int sms, cudaStream_t st) {
-    const void* k = (const void*)k_numeric<VALUES, G, PACKED, RG>;
-    const size_t smem = numeric_dense_smem(p.W, warps, VALUES, RG);
+    const void* k = (const void*)k_numeric<VALUES, G, PACKED>;
+    const size_t smem = numeric_dense_smem(p.W, warps, VALUES);
     cudaError_t e;
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     const int grid = persistent_grid(k, 32 * warps, smem, sms);
     count_launch();
-    k_numeric<VALUES, G, PACKED, RG><<<grid, 32 * warps, smem, st>>>(p);
+    k_numeric<VALUES, G, PACKED><<<grid, 32 * warps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <bool VALUES, bool PACKED, int RG>
+template <bool VALUES, bool PACKED>
 static cudaError_t launch_g(const NumParams& p, int G, int warps, int sms, cudaStream_t st) {
-    if (RG && G != 1 && G != 2) G = 1;  // with row groups only heavy rows use G
     switch (G) {
-        case 1: return launch_one<VALUES, 1, PACKED, RG>(p, warps, sms, st);
+        case 1: return launch_one<VALUES, 1, PACKED>(p, warps, sms, st);
         case 2:
-            if constexpr (VALUES && PACKED) return launch_one<VALUES, 2, PACKED, RG>(p, warps, sms, st);
-            else return launch_one<VALUES, 1, PACKED, RG>(p, warps, sms, st);
-        default:
-            if constexpr (RG == 0) {
-                switch (G) {
-                    case 4: return launch_one<VALUES, 4, PACKED, 0>(p, warps, sms, st);
-                    case 8: return launch_one<VALUES, 8, PACKED, 0>(p, warps, sms, st);
-                    case 16: return launch_one<VALUES, 16, PACKED, 0>(p, warps, sms, st);
-                    case 32: return launch_one<VALUES, 32, PACKED, 0>(p, warps, sms, st);
-                }
-            }
-            return cudaErrorInvalidValue;
+            if constexpr (VALUES && PACKED) return launch_one<VALUES, 2, PACKED>(p, warps, sms, st);
+            else return launch_one<VALUES, 1, PACKED>(p, warps, sms, st);
+        case 4: return launch_one<VALUES, 4, PACKED>(p, warps, sms, st);
+        case 8: return launch_one<VALUES, 8, PACKED>(p, warps, sms, st);
+        case 16: return launch_one<VALUES, 16, PACKED>(p, warps, sms, st);
+        case 32: return launch_one<VALUES, 32, PACKED>(p, warps, sms, st);
+        default: return cudaErrorInvalidValue;
     }
+}
+
+template <int RG>
+static cudaError_t launch_light(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    const void* k = (const void*)k_numeric_light<RG>;
+    const size_t smem = numeric_light_smem(p.W, warps, RG);
+    cudaError_t e;
+    if (smem == 0 || smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(persistent_grid(k, 32 * warps, smem, sms));
+    lc.blockDim = dim3(32 * warps);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&lc, k_numeric_light<RG>, p);
 }
 
 cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
@@ -575,16 +708,19 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
     const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
     const int w = cfg.warps_per_cta;
-    if (values && Bpk) {  // row groups need the padded packed copy
+    if (values && Bpk && cfg.row_lanes != 32) {  // row groups need the padded packed copy
+        NumParams ph = p;
+        ph.skip_light = 1;
+        if ((e = launch_g<true, true>(ph, G, w, cfg.sms, st))) return e;
         switch (cfg.row_lanes) {
-            case 4: return launch_g<true, true, 4>(p, G, w, cfg.sms, st);
-            case 8: return launch_g<true, true, 8>(p, G, w, cfg.sms, st);
-            case 16: return launch_g<true, true, 16>(p, G, w, cfg.sms, st);
-            default: return launch_g<true, true, 0>(p, G, w, cfg.sms, st);
+            case 4: return launch_light<4>(p, w, cfg.sms, st);
+            case 8: return launch_light<8>(p, w, cfg.sms, st);
+            case 16: return launch_light<16>(p, w, cfg.sms, st);
+            default: return cudaErrorInvalidValue;
         }
     }
-    if (values) return launch_g<true, false, 0>(p, G, w, cfg.sms, st);
-    return launch_g<false, false, 0>(p, G, w, cfg.sms, st);
+    if (values) return Bpk ? launch_g<true, true>(p, G, w, cfg.sms, st) : launch_g<true, false>(p, G, w, cfg.sms, st);
+    return launch_g<false, false>(p, G, w, cfg.sms, st);
 }
 
 }  // namespace ts

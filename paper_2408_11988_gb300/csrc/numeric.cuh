@@ -34,6 +34,7 @@ struct NumParams {
     long long nnzC;
     Sched s;
     long long item_cap;
+    int skip_light;  // 1: split and heavy rows only (light rows run in a kernel of their own)
 };
 
 inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
@@ -63,6 +64,7 @@ inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, i
     p.nnzC = nnzC;
     p.s = s;
     p.item_cap = split_item_capacity(A.nnz);
+    p.skip_light = 0;
     return p;
 }
 

@@ -11,8 +11,9 @@
 // update acc[c] += A(i,k) * B(k,c) is a plain load and store.  Between two
 // segments the warp synchronises (__syncwarp), which orders one lane's store
 // before another lane's load of the same column.  A column that no product
-// reached holds the NaN bit pattern PC_EMPTY, which no product or sum can
-// carry, so no occupancy flags are kept.
+// reached holds PC_EMPTY, a signalling-NaN bit pattern: arithmetic never
+// delivers a signalling NaN (a NaN result is quiet), so no product or sum
+// carries it and no occupancy flags are kept.
 //
 // At the end of a row the copies are combined column by column in a fixed
 // order (copy 0 first), the reached columns are written to C in ascending
@@ -27,8 +28,9 @@
 
 namespace ts {
 
-constexpr unsigned PC_EMPTY = 0xFFBADBADu;  // a NaN pattern: "no product yet"
-constexpr unsigned PC_QNAN = 0x7FFFFFFFu;
+constexpr unsigned PC_EMPTY = 0xFFBADBADu;  // "no product yet": exponent all ones, quiet bit clear
+static_assert((PC_EMPTY & 0x7F800000u) == 0x7F800000u && (PC_EMPTY & 0x00400000u) == 0 && (PC_EMPTY & 0x003FFFFFu),
+              "PC_EMPTY must be a signalling NaN");
 
 // Segment of B of one entry of A, as a group reads it.
 struct PcMeta {
@@ -50,10 +52,8 @@ __device__ __forceinline__ void pc_add(float* cp, int c, float v, int d, int c0,
                                        unsigned long long* err) {
     const int lc = c - c0;
     if ((unsigned)c < (unsigned)d && (unsigned)lc < (unsigned)W) {
-        unsigned x = f2u(v);
-        if (x == PC_EMPTY) x = PC_QNAN;  // a NaN product stays a NaN, never the marker
-        const unsigned old = f2u(cp[lc]);
-        cp[lc] = old == PC_EMPTY ? u2f(x) : u2f(old) + u2f(x);
+        const float old = cp[lc];
+        cp[lc] = f2u(old) == PC_EMPTY ? v : old + v;
     } else {
         atomicOr(err, ERR_B_COL);
     }
