@@ -56,7 +56,7 @@ WORKLOADS = {
 def _kernel_sources_hash():
     import hashlib
     h = hashlib.sha1()
-    for f in ("numeric.cu", "common.cuh", "staged.cuh", "layout.h"):
+    for f in ("numeric.cu", "numeric.cuh", "common.cuh", "staged.cuh", "layout.h"):
         with open(os.path.join(ROOT, "paper_2408_11988_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -324,7 +324,7 @@ def main():
                        "nnz_A": nnzA, "nnz_B": B.nnz, "nnz_C": nnzC, "products": F,
                        "tuning": plan.tuning, "l2": "inputs larger than L2 (A+B+C > 129 MB)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "hbm", "kernel": "numeric pass (k_numeric_dense)",
+            "roofline": {"bound": "hbm", "kernel": "numeric pass (k_numeric + k_numeric_light)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "bytes_per_launch": num_bytes, "traffic": _traffic(args.workload)},
