@@ -114,7 +114,9 @@ typedef struct ts_csr_desc {
  *                 row groups, 32/row_lanes rows per warp in lockstep, each
  *                 with its own accumulator and no atomics (4: four entries
  *                 of B per lane, 8 and 16: two), in a kernel launched right
- *                 behind the one for the heavy rows.
+ *                 behind the one for the heavy rows.  Any value but 32 also
+ *                 runs the symbolic pass's light rows in row groups of four
+ *                 lanes (d <= 512, B.col 16-byte aligned).
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.

@@ -203,7 +203,7 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
 }
 
 struct Layout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, tp = 0, bpk = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, total = 0;
     size_t split_rows = 0, split_done = 0, split_items = 0, stg_bits = 0, stg_vals = 0, stg_flags = 0;
     int dw = 0, dpad = 0;
     int W = 0, T = 1;
@@ -227,6 +227,7 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     L.perm = take(sizeof(int) * (size_t)n);
     L.partial = take(sizeof(long long) * scan_partial_count(n));
     L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
+    L.blen = take(sizeof(int) * (size_t)n);  // B has n rows
     L.dw = (int)((d + 31) / 32);
     L.dpad = 32 * L.dw;
     L.split_rows = take(sizeof(int) * MAX_SPLIT_ROWS);
@@ -261,6 +262,7 @@ static Sched carve(void* ws, const Layout& L) {
     s.perm = (int*)(b + L.perm);
     s.partial = (long long*)(b + L.partial);
     s.items = (long long*)(b + L.items);
+    s.blen = (int*)(b + L.blen);
     s.split_rows = (int*)(b + L.split_rows);
     s.split_done = (int*)(b + L.split_done);
     s.split_items = (long long*)(b + L.split_items);
@@ -702,7 +704,7 @@ extern "C" ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, voi
 static const long long MSBFS_MAX_D = 65536;
 
 struct BfsLayout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, newbits = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, newbits = 0, blen = 0, total = 0;
 };
 
 static BfsLayout bfs_layout(long long n, long long d, long long nnzA) {
@@ -720,6 +722,7 @@ static BfsLayout bfs_layout(long long n, long long d, long long nnzA) {
     // newbits before items: msbfs_emit finds it without knowing nnz(A)
     L.newbits = take(sizeof(unsigned) * (size_t)n * (size_t)((d + 31) / 32));
     L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
+    L.blen = take(sizeof(int) * (size_t)n);
     L.total = off;
     return L;
 }
@@ -776,6 +779,7 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     sc.perm = (int*)(b + L.perm);
     sc.partial = (long long*)(b + L.partial);
     sc.items = (long long*)(b + L.items);
+    sc.blen = (int*)(b + L.blen);
     unsigned* newbits = (unsigned*)(b + L.newbits);
     ts_tuning t{};
     resolve_tuning(d, ts_tuning{}, t);

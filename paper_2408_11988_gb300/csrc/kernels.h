@@ -25,6 +25,7 @@ struct Sched {
     int* perm = nullptr;         // non-empty rows, heaviest class first, int32[n]
     long long* partial = nullptr;// scan partial sums
     long long* items = nullptr;  // (row, chunk) work items of long rows for the flops pass
+    int* blen = nullptr;         // row lengths of B (clamped), for the flops pass, or nullptr
     // split rows (more than SPLIT_ENTRIES entries of A): row ids, completion
     // counters, (slot, part) work items and per-slot staging of partial rows
     int* split_rows = nullptr;        // [MAX_SPLIT_ROWS]

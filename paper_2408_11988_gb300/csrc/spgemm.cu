@@ -20,9 +20,31 @@ namespace ts {
 constexpr int SHORT_ROW = 32;
 constexpr int LONG_CHUNK = 256;
 
+// Row lengths of B clamped as SegWhole clamps them, as one int32 array: the
+// flops pass then reads one 4-byte word per entry of A from an array that
+// stays in L2 instead of two 8-byte row pointers.
+__global__ void __launch_bounds__(256) k_row_len(long long nB, SegWhole segB, int* __restrict__ blen) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nB;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long s0;
+        int len;
+        segB((int)k, s0, len);
+        blen[k] = len;
+    }
+}
+
+struct SegLen {
+    const int* __restrict__ blen;
+    __device__ __forceinline__ void operator()(int k, long long& start, int& len) const {
+        start = 0;
+        len = __ldg(blen + k);
+    }
+};
+
+template <class Seg>
 __global__ void __launch_bounds__(256) k_flops_rows(long long n, const long long* __restrict__ Ap,
                                                     const int* __restrict__ Ai, long long nnzA,
-                                                    SegWhole segB, int nB, long long* __restrict__ flops,
+                                                    Seg segB, int nB, long long* __restrict__ flops,
                                                     long long* __restrict__ items, long long item_cap,
                                                     WsHeader* hdr) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -68,9 +90,10 @@ __global__ void __launch_bounds__(256) k_flops_rows(long long n, const long long
     }
 }
 
+template <class Seg>
 __global__ void __launch_bounds__(256) k_flops_chunks(const long long* __restrict__ Ap,
                                                       const int* __restrict__ Ai, long long nnzA,
-                                                      SegWhole segB, int nB, long long* flops,
+                                                      Seg segB, int nB, long long* flops,
                                                       const long long* __restrict__ items,
                                                       long long item_cap, WsHeader* hdr) {
     const long long nitems_raw = *(volatile long long*)&hdr->scratch[0];
@@ -185,12 +208,26 @@ cudaError_t launch_row_flops(const DevCsr& A, const DevCsr& B, const Sched& s, c
     if (n == 0) return cudaSuccess;
     const SegWhole segB{B.rowptr, B.nnz, (int)B.ncols};
     const long long cap = flops_item_capacity(n, A.nnz);
-    count_launch();
-    k_flops_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A.rowptr, A.col, A.nnz, segB,
-                                                             (int)B.nrows, s.flops, s.items, cap, s.hdr);
-    count_launch();
-    k_flops_chunks<<<152 * 8, 256, 0, st>>>(A.rowptr, A.col, A.nnz, segB, (int)B.nrows, s.flops, s.items,
-                                            cap, s.hdr);
+    const unsigned rb = (unsigned)((n + 255) / 256);
+    if (s.blen && B.nrows > 0) {
+        long long lb = (B.nrows + 255) / 256;
+        if (lb > 152 * 16) lb = 152 * 16;
+        count_launch();
+        k_row_len<<<(unsigned)lb, 256, 0, st>>>(B.nrows, segB, s.blen);
+        const SegLen sl{s.blen};
+        count_launch();
+        k_flops_rows<<<rb, 256, 0, st>>>(n, A.rowptr, A.col, A.nnz, sl, (int)B.nrows, s.flops, s.items, cap, s.hdr);
+        count_launch();
+        k_flops_chunks<<<152 * 8, 256, 0, st>>>(A.rowptr, A.col, A.nnz, sl, (int)B.nrows, s.flops, s.items, cap,
+                                                s.hdr);
+    } else {
+        count_launch();
+        k_flops_rows<<<rb, 256, 0, st>>>(n, A.rowptr, A.col, A.nnz, segB, (int)B.nrows, s.flops, s.items, cap,
+                                         s.hdr);
+        count_launch();
+        k_flops_chunks<<<152 * 8, 256, 0, st>>>(A.rowptr, A.col, A.nnz, segB, (int)B.nrows, s.flops, s.items,
+                                                cap, s.hdr);
+    }
     return cudaGetLastError();
 }
 
@@ -336,6 +373,7 @@ struct SymParams {
     long long* Cp_next;
     Sched s;
     long long item_cap;
+    int skip_light;  // 1: split and heavy rows only (light rows run in k_symbolic_light)
 };
 
 // Count of the marks in words [w0, dw*8 or dw) of a warp's or block's
@@ -395,6 +433,9 @@ __device__ __forceinline__ int block_sum(int c, int* s_red) {
 
 template <int G, bool FL>
 __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
+    // a light-row kernel launched behind this one may start on SMs this grid
+    // frees (the two count disjoint rows)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];
@@ -476,10 +517,130 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     }
 
     // light rows: one warp per row, static round robin over the class order
+    if (p.skip_light) return;
     unsigned* bm = smem_u + warp * p.slot;
     SymRowBody<G, FL> body{p, bm, err};
     pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
                    p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body, mark);
+}
+
+
+// Light rows of the symbolic pass in row groups (byte marks, B.col 16-byte
+// aligned): R = 32/RG rows of the schedule per warp in lockstep, RG lanes per
+// row, each row with its own dpad occupancy bytes.  A slot walks the
+// segments B(k,:) of its row's entries in quads (one 16-byte load of four
+// columns, single loads for a quad that reaches past the end of B).  Marks
+// are plain byte stores of the value 1, so segments need no ordering among
+// themselves; two segments are loaded before either is marked.  The count of
+// a row is a popcount over its bytes, summed over the slot's lanes.
+// Launched behind k_symbolic with programmatic dependent launch; waits for
+// that grid before exiting.
+__device__ __forceinline__ void symrg_quad(const int* __restrict__ Bi, long long nnzB, long long qb, long long s,
+                                           long long end, int c[4]) {
+    if (qb + 4 <= nnzB) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(Bi + qb));
+        c[0] = v.x;
+        c[1] = v.y;
+        c[2] = v.z;
+        c[3] = v.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = qb + u < end ? __ldg(Bi + qb + u) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (qb + u < s || qb + u >= end) c[u] = -1;
+}
+
+__device__ __forceinline__ void symrg_mark(unsigned char* fl, const int c[4], int d, unsigned long long* err) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (c[u] >= 0) {
+            if (c[u] < d) fl[c[u]] = 1;
+            else atomicOr(err, ERR_B_COL);
+        }
+    }
+}
+
+template <int RG>
+__global__ void __launch_bounds__(256, 6) k_symbolic_light(SymParams p) {
+    extern __shared__ __align__(16) unsigned smem_u[];
+    __shared__ long long s_nheavy, s_nrows;
+    constexpr int R = 32 / RG;
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    const int g = lane / RG, gl = lane % RG;
+    const int slotw = 8 * p.dw;  // words of one row's dpad bytes
+    for (int i = tid; i < nw * R * slotw; i += blockDim.x) smem_u[i] = 0u;
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    unsigned* fw = smem_u + (size_t)(warp * R + g) * slotw;
+    unsigned char* fl = reinterpret_cast<unsigned char*>(fw);
+    unsigned long long* err = &p.hdr->err;
+    const long long* mark = p.s.flops;
+    const long long end = s_nrows, step = (long long)gridDim.x * nw * R;
+    const long long nnzB = p.segB.nnzB;
+    for (long long idx = s_nheavy + ((long long)blockIdx.x * nw + warp) * R; idx < end; idx += step) {
+        const long long my = idx + g;
+        long long a0 = 0, a1 = 0;
+        int row = -1;
+        if (my < end) {
+            row = __ldg(p.perm + my);
+            a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+            a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+            if (is_split_row(mark, row, a1 - a0)) {
+                a1 = a0;  // counted from its split parts
+                row = -1;
+            }
+        }
+        const int len = (int)(a1 - a0);
+        const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        for (int e = 0; e < lmax; e += RG) {
+            long long sg = 0;
+            int L = 0;
+            if (e + gl < len) {
+                const int k = __ldg(p.Ai + a0 + e + gl);
+                if ((unsigned)k < (unsigned)p.nB) p.segB(k, sg, L);
+                else atomicOr(err, ERR_A_COL);
+            }
+            const int nu = lmax - e < RG ? lmax - e : RG;
+            for (int u = 0; u < nu; u += 2) {
+                const long long s0 = shfl64(sg, g * RG + u);
+                const int L0 = __shfl_sync(FULL, L, g * RG + u);
+                const int u1 = u + 1 < nu ? u + 1 : u;
+                const long long s1 = shfl64(sg, g * RG + u1);
+                const int L1 = u + 1 < nu ? __shfl_sync(FULL, L, g * RG + u1) : 0;
+                const long long b0 = s0 & ~3LL, e0 = s0 + L0, b1 = s1 & ~3LL, e1 = s1 + L1;
+                const int n0 = L0 > 0 ? (int)((e0 - b0 + 3) >> 2) : 0;
+                const int n1 = L1 > 0 ? (int)((e1 - b1 + 3) >> 2) : 0;
+                const int nm = n0 > n1 ? n0 : n1;
+                for (int q = gl; q < nm; q += RG) {
+                    int c0[4] = {-1, -1, -1, -1}, c1[4] = {-1, -1, -1, -1};
+                    if (q < n0) symrg_quad(p.Bi, nnzB, b0 + 4LL * q, s0, e0, c0);
+                    if (q < n1) symrg_quad(p.Bi, nnzB, b1 + 4LL * q, s1, e1, c1);
+                    symrg_mark(fl, c0, p.d, err);
+                    symrg_mark(fl, c1, p.d, err);
+                }
+            }
+        }
+        __syncwarp();
+        int c = 0;
+        for (int w = 4 * gl; w < slotw; w += 4 * RG) {
+            uint4* q = reinterpret_cast<uint4*>(fw + w);
+            const uint4 v = *q;
+            c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            if (v.x | v.y | v.z | v.w) *q = make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int o = RG / 2; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o, RG);
+        if (row >= 0 && gl == 0) p.Cp_next[row] = c;
+        __syncwarp();
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 static std::atomic<long long> g_launches{0};
@@ -527,6 +688,7 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.Cp_next = Cp + 1;
     p.s = s;
     p.item_cap = item_cap;
+    p.skip_light = 0;
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)p.slot * cfg.warps_per_cta;
     const void* k;
@@ -543,11 +705,35 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     }
     if (threads > 256) return cudaErrorInvalidValue;
     if ((e = set_smem(k, smem))) return e;
+    // light rows in row groups of four lanes (quads; byte marks; aligned B.col;
+    // d up to 512: wider rows make the per-row byte count cost more than the
+    // groups save, measured at d = 1024)
+    constexpr int SRG = 4;
+    const bool rg = cfg.row_lanes != 32 && fl && d <= 512 && !(reinterpret_cast<uintptr_t>(B.col) & 15);
+    const size_t lsmem = sizeof(unsigned) * (size_t)8 * p.dw * (32 / SRG) * cfg.warps_per_cta;
+    const bool rg_ok = rg && lsmem <= 200 * 1024;
+    if (rg_ok) p.skip_light = 1;
     const int grid = persistent_grid(k, threads, smem, cfg.sms);
     void* args[] = {&p};
     count_launch();
     if ((e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st))) return e;
     if ((e = cudaGetLastError())) return e;
+    if (rg_ok) {
+        const void* kl = (const void*)k_symbolic_light<SRG>;
+        if ((e = set_smem(kl, lsmem))) return e;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(persistent_grid(kl, threads, lsmem, cfg.sms));
+        lc.blockDim = dim3(threads);
+        lc.dynamicSmemBytes = lsmem;
+        lc.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        count_launch();
+        if ((e = cudaLaunchKernelEx(&lc, k_symbolic_light<SRG>, p))) return e;
+    }
     return launch_scan_inplace(Cp + 1, n, s.partial, st);
 }
 

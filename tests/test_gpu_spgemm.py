@@ -46,6 +46,7 @@ TUNINGS = [
     {"group": 2, "pack_b": 2}, {"group": 2, "col_tile": 32}, {"sym_group": 2, "warps_per_cta": 1},
     {"row_lanes": 4}, {"row_lanes": 8}, {"row_lanes": 16}, {"row_lanes": 4, "col_tile": 32},   # row groups
     {"row_lanes": 4, "pack_b": 2}, {"row_lanes": 8, "cta_min_flops": 1 << 20, "warps_per_cta": 2},
+    {"row_lanes": 32}, {"row_lanes": 32, "sym_group": 16},   # one warp per light row in every pass
 ]
 
 
@@ -79,7 +80,8 @@ def test_er_boolean(er_case, tuning):
                                     {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "group": 8, "col_tile": 64},
                                     {"accum": ACC_COPIES, "cta_min_flops": 128, "pack_b": 2},
                                     {"group": 2, "sym_group": 2}, {"group": 2, "col_tile": 64, "cta_min_flops": 128},
-                                    {"row_lanes": 4}, {"row_lanes": 8, "col_tile": 64}, {"row_lanes": 16, "group": 2}])
+                                    {"row_lanes": 4}, {"row_lanes": 8, "col_tile": 64}, {"row_lanes": 16, "group": 2},
+                                    {"row_lanes": 32}])
 def test_rmat_embedding_small(tuning):
     A, B = synth.rmat_embedding(scale=13, edge_factor=16, d=256, density=0.05, seed=31)
     C = spgemm(dev(A), dev(B), tuning=tuning)
@@ -174,7 +176,8 @@ def embed_full():
     return synth.rmat_embedding()
 
 
-@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"group": 2, "sym_group": 2}, {"row_lanes": 4}])
+@pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"group": 2, "sym_group": 2}, {"row_lanes": 4},
+                                    {"row_lanes": 32}])
 def test_embedding_full_size_sampled(embed_full, tuning):
     # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %
     A, B = embed_full
