@@ -36,6 +36,7 @@ struct BwdParams {
     int cta_class;
     Sched s;
     long long item_cap;
+    int skip_light;  // 1: split and heavy rows only (light rows run in k_backward_light)
 };
 
 // Sum of v over the run of equal keys that starts at this lane (keys are
@@ -269,8 +270,143 @@ struct BwdRowBody {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Light rows of the backward in row groups (packed B, 16-byte aligned dB):
+// R = 32/RG rows of the schedule per warp in lockstep, RG lanes per row.  A
+// slot scatters its row of dC into its own dense row g (W = dpad floats),
+// then walks the segments B(k,:) of its row's entries two entries per lane
+// (one 16-byte load of the packed copy, starting at the even position at or
+// below the segment's first entry): each entry (k, j) reads g[col] once, adds
+// A(i,k) * dC(i,col) into dB with one 8-byte float atomic per lane (an entry
+// of the pair outside the segment adds 0; the last pair of B takes scalar
+// atomics) and B(k,j) * dC(i,col) into the entry's dA sum, reduced over the
+// slot's lanes.  g is only read while the segments are walked, so segments
+// need no ordering among themselves.  Launched behind k_backward with
+// programmatic dependent launch; waits for that grid before exiting.
+// ---------------------------------------------------------------------------
+template <int RG>
+__device__ __forceinline__ float bwdrg_segment(const BwdParams& p, const int4* __restrict__ P4, const float* g,
+                                               long long s, int L, float a, int gl, unsigned long long* err) {
+    const long long qbase = s & ~1LL, end = s + L;
+    const int span = L > 0 ? (int)(end - qbase) : 0;
+    float part = 0.0f;
+    for (int q = gl; 2 * q < span; q += RG) {
+        const long long qb = qbase + 2LL * q;
+        const int4 v = __ldg(P4 + (qb >> 1));
+        const int cs[2] = {v.x, v.z};
+        const int bs[2] = {v.y, v.w};
+        float t2[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (qb + u >= s && qb + u < end) {
+                const int c = cs[u];
+                if ((unsigned)c < (unsigned)p.d) {
+                    const float gc = g[c];
+                    t2[u] = a * gc;
+                    part += __int_as_float(bs[u]) * gc;
+                } else {
+                    atomicOr(err, ERR_B_COL);
+                }
+            }
+        }
+        if (p.dB) {
+            if (qb + 2 <= p.nnzB) {
+                atomicAdd(reinterpret_cast<float2*>(p.dB + qb), make_float2(t2[0], t2[1]));
+            } else {
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (qb + u >= s && qb + u < end) atomicAdd(p.dB + qb + u, t2[u]);
+            }
+        }
+    }
+    return part;
+}
+
+template <int RG>
+__global__ void __launch_bounds__(256, 5) k_backward_light(BwdParams p) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ long long s_nheavy, s_nrows;
+    constexpr int R = 32 / RG;
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    const int g = lane / RG, gl = lane % RG;
+    for (int i = tid; i < nw * R * p.dpad; i += blockDim.x) fsm[i] = 0.0f;
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    float* gr = fsm + (size_t)(warp * R + g) * p.dpad;
+    unsigned long long* err = &p.hdr->err;
+    const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);
+    const long long* mark = p.s.flops;
+    const long long end = s_nrows, step = (long long)gridDim.x * nw * R;
+    for (long long idx = s_nheavy + ((long long)blockIdx.x * nw + warp) * R; idx < end; idx += step) {
+        const long long my = idx + g;
+        long long a0 = 0, a1 = 0, c0 = 0, c1 = 0;
+        if (my < end) {
+            const int row = __ldg(p.perm + my);
+            a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+            a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+            if (is_split_row(mark, row, a1 - a0)) {
+                a1 = a0;  // done by split parts
+            } else {
+                c0 = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+                c1 = clampll(__ldg(p.Cp + row + 1), c0, p.nnzC);
+            }
+        }
+        // this slot's row of dC into g
+        for (long long e = c0 + gl; e < c1; e += RG) {
+            const int c = __ldg(p.Ci + e);
+            if ((unsigned)c < (unsigned)p.d) gr[c] = __ldg(p.dC + e);
+            else atomicOr(err, ERR_C_ROW);
+        }
+        __syncwarp();
+        const int len = (int)(a1 - a0);
+        const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        for (int e = 0; e < lmax; e += RG) {
+            long long sg = 0;
+            int L = 0;
+            float a = 0.0f;
+            if (e + gl < len) {
+                const int k = __ldg(p.Ai + a0 + e + gl);
+                if ((unsigned)k < (unsigned)p.nB) {
+                    SegWhole{p.Bp, p.nnzB, p.d}(k, sg, L);
+                    a = __ldg(p.Ax + a0 + e + gl);
+                } else {
+                    atomicOr(err, ERR_A_COL);
+                }
+            }
+            const int nu = lmax - e < RG ? lmax - e : RG;
+            float mine = 0.0f;  // dA of entry e + gl of this slot's row
+            for (int u = 0; u < nu; ++u) {
+                const int src = g * RG + u;
+                const long long su = shfl64(sg, src);
+                const int Lu = __shfl_sync(FULL, L, src);
+                const float au = __shfl_sync(FULL, a, src);
+                float part = bwdrg_segment<RG>(p, P4, gr, su, Lu, au, gl, err);
+#pragma unroll
+                for (int o = RG / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(FULL, part, o, RG);
+                if (gl == u) mine = part;
+            }
+            if (p.dA && e + gl < len) p.dA[a0 + e + gl] = mine;
+        }
+        __syncwarp();
+        for (long long e = c0 + gl; e < c1; e += RG) {
+            const int c = __ldg(p.Ci + e);
+            if ((unsigned)c < (unsigned)p.d) gr[c] = 0.0f;
+        }
+        __syncwarp();
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int G, bool PACKED>
 __global__ void __launch_bounds__(256, 5) k_backward(BwdParams p) {
+    // a light-row kernel launched behind this one may start on SMs this grid
+    // frees (the two handle disjoint rows; dB is only added to atomically)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) float fsm[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
@@ -311,6 +447,7 @@ __global__ void __launch_bounds__(256, 5) k_backward(BwdParams p) {
         if (is_split_row(mark, row, a1 - a0)) continue;
         backward_range_cta<G, BA>(p, ba, row, a0, a1, fsm, sdA);
     }
+    if (p.skip_light) return;
     float* g = fsm + (size_t)warp * p.dpad;
     BwdRowBody<G, BA> body{p, ba, g, sdA, &p.hdr->err, -1, 0, 0, 0, 0};
     pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
@@ -360,6 +497,7 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     p.cta_class = cfg.cta_class;
     p.s = s;
     p.item_cap = split_item_capacity(A.nnz);
+    p.skip_light = 0;
     int warps = cfg.warps_per_cta;
     if (warps > 8) return cudaErrorInvalidValue;
     size_t smem = backward_smem(d, warps);
@@ -384,10 +522,33 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
+    // light rows in row groups of eight lanes (pairs): packed B, aligned dB
+    constexpr int BRG = 8;
+    const size_t lsmem = sizeof(float) * (size_t)p.dpad * (32 / BRG) * warps;
+    const bool rg = cfg.row_lanes != 32 && pk && !(dB && (reinterpret_cast<uintptr_t>(dB) & 15)) && p.dpad <= 512 &&
+                    lsmem <= 200 * 1024;
+    if (rg) p.skip_light = 1;
     const int grid = persistent_grid(k, 32 * warps, smem, cfg.sms);
     void* args[] = {&p};
     count_launch();
-    return cudaLaunchKernel(k, dim3(grid), dim3(32 * warps), args, smem, st);
+    if ((e = cudaLaunchKernel(k, dim3(grid), dim3(32 * warps), args, smem, st))) return e;
+    if (!rg) return cudaSuccess;
+    const void* kl = (const void*)k_backward_light<BRG>;
+    if (lsmem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem)))
+        return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(persistent_grid(kl, 32 * warps, lsmem, cfg.sms));
+    lc.blockDim = dim3(32 * warps);
+    lc.dynamicSmemBytes = lsmem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&lc, k_backward_light<BRG>, p);
 }
 
 }  // namespace ts

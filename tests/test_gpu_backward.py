@@ -39,7 +39,8 @@ def _run(A, B, tuning=None, seed=1):
                                     {"pack_b": 1}, {"pack_b": 1, "group": 1, "cta_min_flops": 64},
                                     {"bwd_group": 1}, {"bwd_group": 4}, {"bwd_group": 32, "sym_group": 1},
                                     {"bwd_group": 16}, {"bwd_group": 2}, {"bwd_group": 2, "pack_b": 2},
-                                    {"bwd_group": 2, "cta_min_flops": 1}, {"bwd_group": 2, "warps_per_cta": 1}])
+                                    {"bwd_group": 2, "cta_min_flops": 1}, {"bwd_group": 2, "warps_per_cta": 1},
+                                    {"row_lanes": 32}, {"row_lanes": 8, "pack_b": 2}, {"row_lanes": 8, "warps_per_cta": 3}])
 def test_backward_matches_oracle(tuning):
     A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=50)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -49,7 +50,8 @@ def test_backward_matches_oracle(tuning):
 
 
 @pytest.mark.parametrize("tuning", [None, {"group": 1}, {"group": 8, "pack_b": 1}, {"bwd_group": 16},
-                                    {"bwd_group": 2, "cta_min_flops": 16}])
+                                    {"bwd_group": 2, "cta_min_flops": 16}, {"row_lanes": 32},
+                                    {"row_lanes": 8, "cta_min_flops": 1 << 20}])
 def test_backward_ragged_and_empty_rows(tuning):
     A, B = synth.er_product(n=3000, k=5, d=100, density=0.05, seed=51)
     rp, col, dC, dA, dB = _run(A, B, tuning)
@@ -68,7 +70,7 @@ def test_backward_unaligned_db_and_b_tail():
             break
     assert B.nnz % 4 != 0
     Ad, Bd = dev(A), dev(B)
-    plan = Plan(Ad, Bd, tuning={"bwd_group": 2})
+    plan = Plan(Ad, Bd, tuning={"bwd_group": 2, "row_lanes": 8})
     C = plan.forward(Ad, Bd)
     dC = synth.grad_output(C.nnz, 5)
     rp, col, _ = C.to_host()
@@ -168,7 +170,7 @@ def test_backward_split_rows():
     A = CSR(n, n, rowptr, col, synth.uniform(col.size, 81))
     B = synth.tall_skinny(n, d, 0.05, 82)
     B.val = synth.normal(B.nnz, 83)
-    for t in (None, {"group": 1}, {"pack_b": 1}):
+    for t in (None, {"group": 1}, {"pack_b": 1}, {"row_lanes": 32}):
         rp, ci, dC, dA, dB = _run(A, B, t, seed=4)
         rA, bA, rB, bB = oracle.backward(A, B, rp, ci, dC.astype(np.float64))
         assert np.all(np.abs(dA - rA) <= REL * bA)
