@@ -295,8 +295,14 @@ def main():
     value = flop_step * ws / (ms * 1e-3) / 1e9
 
     # roofline of the numeric pass: algorithmic bytes per launch / mean duration
+    # (A's row pointers, columns, values and B's row bounds once per column tile)
     n, nnzA = A.nrows, A.nnz
-    num_bytes = 16 * (n + 1) + 24 * nnzA + 8 * F + 8 * nnzC
+    tiles = 1
+    if plan.tuning.get("accum") != 2 and plan.tuning.get("col_tile"):
+        tiles = -(-B.ncols // int(plan.tuning["col_tile"]))
+    num_bytes = tiles * (16 * (n + 1) + 24 * nnzA) + 8 * F + 8 * nnzC
+    # compulsory bytes: every array of A, B and C touched once
+    comp_bytes = 8 * (n + 1) + 8 * nnzA + 8 * (B.nrows + 1) + 8 * B.nnz + 8 * (n + 1) + 8 * nnzC
     bwd_bytes = 16 * (n + 1) + 28 * nnzA + 8 * F + 8 * nnzC + 4 * B.nnz
     sym_bytes = 8 * (n + 1) + 20 * nnzA + 4 * F + 8 * n
     peak, peak_kind = _peaks()
@@ -317,7 +323,9 @@ def main():
             "metric": "TS-SpGEMM GFLOP/s (forward + backward, plus-times)" if want_bwd
             else "TS-SpGEMM GFLOP/s (forward, plus-times)",
             "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "ms_per_step_median": round(statistics.median([a + b + c for a, b, c in zip(sym, num, bwd)]), 4),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload + (f"@scale{args.scale}" if args.scale else ""),
                        "description": desc, "n": n, "d": B.ncols,
@@ -327,7 +335,9 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "numeric pass (k_numeric + k_numeric_light)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "bytes_per_launch": num_bytes, "traffic": _traffic(args.workload)},
+                         "bytes_per_launch": num_bytes, "traffic": _traffic(args.workload),
+                         "column_tiles": tiles, "compulsory_bytes": comp_bytes,
+                         "compulsory_frac": round(comp_bytes / (num_ms * 1e-3) / 1e9 / peak, 4)},
             "phases_ms": {"symbolic": round(statistics.mean(sym), 4), "numeric": round(num_ms, 4),
                           "backward": round(statistics.mean(bwd), 4) if want_bwd else None},
             "phase_roofline_frac": {
@@ -552,6 +562,7 @@ def run_msbfs(args, ws, rank, local, desc):
             "config": {"workload": "msbfs-s20", "description": desc, "n": A.nrows, "nnz_A": A.nnz,
                        "sources": len(src), "levels": r.products, "frontier_nnz": r.frontier_nnz,
                        "products": products, "parallelism": f"replicas x{ws}"},
+            "levels_per_s": round(r.products * ws / (ms * 1e-3), 1),
             "roofline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary(),
             "cpu_baseline": None}), flush=True)
     if dist:

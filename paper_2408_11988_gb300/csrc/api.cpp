@@ -449,9 +449,16 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
         const int cg = copies_group(plan->cur.group, plan->n, plan->nnzB);
         if (vals && plan->cur.accum == TS_ACC_COPIES &&
             numeric_copies_smem(L.W, cg, cfg.warps_per_cta) <= 227 * 1024) {
+            // light rows in row groups behind the copies kernel when they fit
+            const bool rg = cfg.row_lanes != 32 && bpk &&
+                            numeric_light_smem(L.W, cfg.warps_per_cta, cfg.row_lanes) <= 220 * 1024;
             TS_CUDA(launch_numeric_copies(dA, dB, plan->d, L.W, L.T, tp, bpk, cg, sc, cfg,
-                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st, rg),
                     fn);
+            if (rg)
+                TS_CUDA(launch_numeric_light_rows(dA, dB, plan->d, L.W, L.T, tp, bpk, sc, cfg,
+                                                  (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                        fn);
         } else if (plan->cur.stage == 1 && numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024 &&
                    (!vals || bpk || B->nnz == 0)) {
             TS_CUDA(launch_numeric_staged(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),

@@ -92,7 +92,7 @@ size_t numeric_staged_smem(int W, int warps, bool values);
 cudaError_t launch_numeric_copies(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                   const long long* tp, const int2* Bpk, int G, const Sched& s,
                                   const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool skip_light = false);
 // Dynamic shared memory of that pass (0 for an unsupported G).
 size_t numeric_copies_smem(int W, int G, int warps);
 // Packed (column, value bits) copy of B's entries.
@@ -104,6 +104,12 @@ cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, i
                                 const long long* Cp, int* Ci, float* Cx, long long nnzC,
                                 cudaStream_t st);
 size_t numeric_dense_smem(int W, int warps, bool values);
+// Light rows only, in row groups of cfg.row_lanes lanes (4, 8 or 16; packed
+// B), launched with programmatic dependent launch behind a numeric kernel
+// that skipped them.
+cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                      const long long* tp, const int2* Bpk, const Sched& s, const LaunchCfg& cfg,
+                                      const long long* Cp, int* Ci, float* Cx, long long nnzC, cudaStream_t st);
 // Dynamic shared memory of the row-group light-row kernel (0: bad row_lanes).
 size_t numeric_light_smem(int W, int warps, int row_lanes);
 size_t numeric_hash_smem(int slots, int warps, bool values);

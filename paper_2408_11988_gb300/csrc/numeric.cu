@@ -697,6 +697,20 @@ static cudaError_t launch_light(const NumParams& p, int warps, int sms, cudaStre
     return cudaLaunchKernelEx(&lc, k_numeric_light<RG>, p);
 }
 
+cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
+                                      const long long* tp, const int2* Bpk, const Sched& s, const LaunchCfg& cfg,
+                                      const long long* Cp, int* Ci, float* Cx, long long nnzC, cudaStream_t st) {
+    if (A.nrows == 0) return cudaSuccess;
+    if (!Bpk || W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
+    const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
+    switch (cfg.row_lanes) {
+        case 4: return launch_light<4>(p, cfg.warps_per_cta, cfg.sms, st);
+        case 8: return launch_light<8>(p, cfg.warps_per_cta, cfg.sms, st);
+        case 16: return launch_light<16>(p, cfg.warps_per_cta, cfg.sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                  const long long* tp, bool values, const int2* Bpk, int G,
                                  const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,

@@ -332,6 +332,7 @@ struct PcRowBody {
 
 template <int G, int U, bool PACKED>
 __global__ void __launch_bounds__(256, (G == 32 ? 3 : 4)) k_numeric_copies(NumParams p) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
     __shared__ long long s_item, s_nheavy, s_nrows;
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(256, (G == 32 ? 3 : 4)) k_numeric_copies(NumPa
             pc_row_cta<G, U, BA>(p, ba, row, smem, wbytes, s_wcnt);
         }
     }
+    if (p.skip_light) return;
     unsigned char* wsm = smem + (size_t)warp * wbytes;
     PcRowBody<G, U, BA> body{p, ba, reinterpret_cast<float*>(wsm),
                              reinterpret_cast<PcMeta*>(wsm + (size_t)NG * p.W * 4), &p.hdr->err, 0, 0};
@@ -407,7 +409,7 @@ static cudaError_t launch_pc(const NumParams& p, int warps, int sms, cudaStream_
 cudaError_t launch_numeric_copies(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                   const long long* tp, const int2* Bpk, int G, const Sched& s,
                                   const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool skip_light) {
     cudaError_t e;
     if (A.nrows == 0) return cudaSuccess;
     if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
@@ -415,7 +417,8 @@ cudaError_t launch_numeric_copies(const DevCsr& A, const DevCsr& B, long long d,
     const size_t smem = numeric_copies_smem(W, G, cfg.warps_per_cta);
     if (smem == 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
-    const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
+    NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
+    p.skip_light = skip_light ? 1 : 0;
     const int w = cfg.warps_per_cta, sms = cfg.sms;
     switch (G) {
         case 8: return Bpk ? launch_pc<8, true>(p, w, sms, st) : launch_pc<8, false>(p, w, sms, st);

@@ -47,6 +47,7 @@ TUNINGS = [
     {"row_lanes": 4}, {"row_lanes": 8}, {"row_lanes": 16}, {"row_lanes": 4, "col_tile": 32},   # row groups
     {"row_lanes": 4, "pack_b": 2}, {"row_lanes": 8, "cta_min_flops": 1 << 20, "warps_per_cta": 2},
     {"row_lanes": 32}, {"row_lanes": 32, "sym_group": 16},   # one warp per light row in every pass
+    {"accum": ACC_COPIES, "row_lanes": 32}, {"accum": ACC_COPIES, "row_lanes": 4, "group": 32},
 ]
 
 
