@@ -284,42 +284,79 @@ struct BwdRowBody {
 // need no ordering among themselves.  Launched behind k_backward with
 // programmatic dependent launch; waits for that grid before exiting.
 // ---------------------------------------------------------------------------
-template <int RG>
-__device__ __forceinline__ float bwdrg_segment(const BwdParams& p, const int4* __restrict__ P4, const float* g,
-                                               long long s, int L, float a, int gl, unsigned long long* err) {
-    const long long qbase = s & ~1LL, end = s + L;
-    const int span = L > 0 ? (int)(end - qbase) : 0;
+// A segment of B as a slot walks it in pairs: first position rounded down to
+// even (qbase), positions before the segment (lead), positions covered from
+// qbase (span), A's value a.
+struct BrgSeg {
+    long long qbase;
+    int lead, span;
+    float a;
+};
+
+__device__ __forceinline__ BrgSeg brg_seg_of(long long s, int L, float a) {
+    BrgSeg q;
+    q.qbase = s & ~1LL;
+    q.lead = (int)(s - q.qbase);
+    q.span = L > 0 ? q.lead + L : 0;
+    q.a = a;
+    return q;
+}
+
+__device__ __forceinline__ void brg_fetch(const int4* __restrict__ P4, const BrgSeg& sg, int q, int4& v) {
+    if (2 * q < sg.span) v = __ldg(P4 + ((sg.qbase >> 1) + q));
+}
+
+// Pair q of a segment (entries qbase + 2q, + 2q + 1): dB terms out, dA part back.
+__device__ __forceinline__ float brg_apply(const BwdParams& p, const BrgSeg& sg, int q, const int4& v, const float* g,
+                                           unsigned long long* err) {
+    const int cs[2] = {v.x, v.z};
+    const int bs[2] = {v.y, v.w};
+    float t2[2] = {0.0f, 0.0f};
     float part = 0.0f;
-    for (int q = gl; 2 * q < span; q += RG) {
-        const long long qb = qbase + 2LL * q;
-        const int4 v = __ldg(P4 + (qb >> 1));
-        const int cs[2] = {v.x, v.z};
-        const int bs[2] = {v.y, v.w};
-        float t2[2] = {0.0f, 0.0f};
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (qb + u >= s && qb + u < end) {
-                const int c = cs[u];
-                if ((unsigned)c < (unsigned)p.d) {
-                    const float gc = g[c];
-                    t2[u] = a * gc;
-                    part += __int_as_float(bs[u]) * gc;
-                } else {
-                    atomicOr(err, ERR_B_COL);
-                }
-            }
-        }
-        if (p.dB) {
-            if (qb + 2 <= p.nnzB) {
-                atomicAdd(reinterpret_cast<float2*>(p.dB + qb), make_float2(t2[0], t2[1]));
+    for (int u = 0; u < 2; ++u) {
+        const int pos = 2 * q + u;
+        if (pos >= sg.lead && pos < sg.span) {
+            const int c = cs[u];
+            if ((unsigned)c < (unsigned)p.d) {
+                const float gc = g[c];
+                t2[u] = sg.a * gc;
+                part += __int_as_float(bs[u]) * gc;
             } else {
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-                    if (qb + u >= s && qb + u < end) atomicAdd(p.dB + qb + u, t2[u]);
+                atomicOr(err, ERR_B_COL);
             }
         }
     }
+    if (p.dB) {
+        const long long qb = sg.qbase + 2LL * q;
+        if (qb + 2 <= p.nnzB) {
+            atomicAdd(reinterpret_cast<float2*>(p.dB + qb), make_float2(t2[0], t2[1]));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (2 * q + u >= sg.lead && 2 * q + u < sg.span) atomicAdd(p.dB + qb + u, t2[u]);
+        }
+    }
     return part;
+}
+
+// Entry ei of A: column k (-1 past the row) and value.
+__device__ __forceinline__ void brg_load_a(const BwdParams& p, long long ei, bool ok, int& k, float& a) {
+    k = -1;
+    a = 0.0f;
+    if (ok) {
+        k = __ldg(p.Ai + ei);
+        a = __ldg(p.Ax + ei);
+    }
+}
+
+__device__ __forceinline__ void brg_seg(const BwdParams& p, int k, bool ok, long long& s, int& L,
+                                        unsigned long long* err) {
+    s = 0;
+    L = 0;
+    if (!ok) return;
+    if ((unsigned)k < (unsigned)p.nB) SegWhole{p.Bp, p.nnzB, p.d}(k, s, L);
+    else atomicOr(err, ERR_A_COL);
 }
 
 template <int RG>
@@ -356,41 +393,68 @@ __global__ void __launch_bounds__(256, 5) k_backward_light(BwdParams p) {
                 c1 = clampll(__ldg(p.Cp + row + 1), c0, p.nnzC);
             }
         }
-        // this slot's row of dC into g
+        const int len = (int)(a1 - a0);
+        // first two chunks of A while dC is scattered
+        int k0, k1;
+        float x0, x1;
+        brg_load_a(p, a0 + gl, gl < len, k0, x0);
+        brg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
         for (long long e = c0 + gl; e < c1; e += RG) {
             const int c = __ldg(p.Ci + e);
             if ((unsigned)c < (unsigned)p.d) gr[c] = __ldg(p.dC + e);
             else atomicOr(err, ERR_C_ROW);
         }
+        long long sg;
+        int L;
+        brg_seg(p, k0, gl < len, sg, L, err);
         __syncwarp();
-        const int len = (int)(a1 - a0);
         const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        BrgSeg nxt = brg_seg_of(shfl64(sg, g * RG), __shfl_sync(FULL, L, g * RG), __shfl_sync(FULL, x0, g * RG));
+        int4 nv = make_int4(0, 0, 0, 0);
+        brg_fetch(P4, nxt, gl, nv);
         for (int e = 0; e < lmax; e += RG) {
-            long long sg = 0;
-            int L = 0;
-            float a = 0.0f;
-            if (e + gl < len) {
-                const int k = __ldg(p.Ai + a0 + e + gl);
-                if ((unsigned)k < (unsigned)p.nB) {
-                    SegWhole{p.Bp, p.nnzB, p.d}(k, sg, L);
-                    a = __ldg(p.Ax + a0 + e + gl);
-                } else {
-                    atomicOr(err, ERR_A_COL);
-                }
-            }
+            int k2;
+            float x2;
+            long long ns;
+            int nL;
+            brg_load_a(p, a0 + e + 2 * RG + gl, e + 2 * RG + gl < len, k2, x2);
+            brg_seg(p, k1, e + RG + gl < len, ns, nL, err);
             const int nu = lmax - e < RG ? lmax - e : RG;
             float mine = 0.0f;  // dA of entry e + gl of this slot's row
             for (int u = 0; u < nu; ++u) {
-                const int src = g * RG + u;
-                const long long su = shfl64(sg, src);
-                const int Lu = __shfl_sync(FULL, L, src);
-                const float au = __shfl_sync(FULL, a, src);
-                float part = bwdrg_segment<RG>(p, P4, gr, su, Lu, au, gl, err);
+                const BrgSeg cur = nxt;
+                const int4 cv = nv;
+                long long s2;
+                int L2;
+                float a2;
+                if (u + 1 < nu) {
+                    s2 = shfl64(sg, g * RG + u + 1);
+                    L2 = __shfl_sync(FULL, L, g * RG + u + 1);
+                    a2 = __shfl_sync(FULL, x0, g * RG + u + 1);
+                } else {
+                    s2 = shfl64(ns, g * RG);
+                    L2 = __shfl_sync(FULL, nL, g * RG);
+                    a2 = __shfl_sync(FULL, x1, g * RG);
+                }
+                nxt = brg_seg_of(s2, L2, a2);
+                brg_fetch(P4, nxt, gl, nv);
+                float part = 0.0f;
+                if (2 * gl < cur.span) part = brg_apply(p, cur, gl, cv, gr, err);
+                for (int q = gl + RG; 2 * q < cur.span; q += RG) {
+                    int4 w = make_int4(0, 0, 0, 0);
+                    brg_fetch(P4, cur, q, w);
+                    part += brg_apply(p, cur, q, w, gr, err);
+                }
 #pragma unroll
                 for (int o = RG / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(FULL, part, o, RG);
                 if (gl == u) mine = part;
             }
             if (p.dA && e + gl < len) p.dA[a0 + e + gl] = mine;
+            sg = ns;
+            L = nL;
+            x0 = x1;
+            k1 = k2;
+            x1 = x2;
         }
         __syncwarp();
         for (long long e = c0 + gl; e < c1; e += RG) {

@@ -79,6 +79,19 @@ __device__ __forceinline__ int owner_lane64(long long key, long long p) {
     return q;
 }
 
+// Ask L2 for the line holding p (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of the packed entries [s, s + L) of B (two 128-byte lines
+// cover a segment of up to 16 entries).
+__device__ __forceinline__ void prefetch_segment(const int2* P, long long s, int L) {
+    if (L <= 0) return;
+    prefetch_l2(P + s);
+    if (L > 8) prefetch_l2(P + s + 16);
+}
+
 __device__ __forceinline__ long long clampll(long long v, long long lo, long long hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }

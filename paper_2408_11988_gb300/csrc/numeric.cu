@@ -461,6 +461,7 @@ __device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, cons
         int nL;
         rg_load_a(p, a0 + e + 2 * RG + gl, e + 2 * RG + gl < len, k2, x2);
         rg_seg(p, seg, k1, e + RG + gl < len, ns, nL, err);
+        prefetch_segment(p.Bpk, ns, nL);  // the next chunk's rows of B into L2
         const int nu = lmax - e < RG ? lmax - e : RG;
         for (int u = 0; u < nu; ++u) {
             const RgSeg cur = nxt;
