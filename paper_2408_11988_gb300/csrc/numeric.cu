@@ -333,32 +333,35 @@ __device__ __forceinline__ void rg_fetch(const int4* __restrict__ P4, const RgSe
     }
 }
 
-// Accumulate group q of a segment from its loaded entries.
+// Accumulate group q of a segment from its loaded entries, without branches:
+// a position outside the segment, or a column outside the tile (an input
+// error, reported through `bad`), is added into the slot's spare column W,
+// which is never read out.
 template <int E>
 __device__ __forceinline__ void rg_apply(float* acc, const RgSeg& sg, int q, const int4& v0, const int4& v1, int Wd,
-                                         int c0, unsigned long long* err) {
+                                         int W, int c0, bool& bad) {
     const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
     const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
     const int p0 = E * q;
 #pragma unroll
     for (int u = 0; u < E; ++u) {
-        if (p0 + u >= sg.lead && p0 + u < sg.span) {
-            const int lc = cs[u] - c0;
-            if ((unsigned)lc < (unsigned)Wd) rg_add(acc, lc, sg.a * __int_as_float(bs[u]));
-            else atomicOr(err, ERR_B_COL);
-        }
+        const bool in_seg = p0 + u >= sg.lead && p0 + u < sg.span;
+        const int lc = cs[u] - c0;
+        const bool ok = (unsigned)lc < (unsigned)Wd;
+        bad |= in_seg && !ok;
+        rg_add(acc, in_seg && ok ? lc : W, sg.a * __int_as_float(bs[u]));
     }
 }
 
 // A whole segment whose first group (q = gl) is already loaded into v0/v1.
 template <int RG, int E>
 __device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* acc, const RgSeg& sg, int gl,
-                                           const int4& v0, const int4& v1, int Wd, int c0, unsigned long long* err) {
-    if (E * gl < sg.span) rg_apply<E>(acc, sg, gl, v0, v1, Wd, c0, err);
+                                           const int4& v0, const int4& v1, int Wd, int W, int c0, bool& bad) {
+    if (E * gl < sg.span) rg_apply<E>(acc, sg, gl, v0, v1, Wd, W, c0, bad);
     for (int q = gl + RG; E * q < sg.span; q += RG) {
         int4 w0 = make_int4(0, 0, 0, 0), w1 = make_int4(0, 0, 0, 0);
         rg_fetch<E>(P4, sg, q, w0, w1);
-        rg_apply<E>(acc, sg, q, w0, w1, Wd, c0, err);
+        rg_apply<E>(acc, sg, q, w0, w1, Wd, W, c0, bad);
     }
 }
 
@@ -440,7 +443,7 @@ __device__ __forceinline__ void rg_seg(const NumParams& p, const Seg& seg, int k
 // and the entries of chunk c+2 (A's columns and values) are loaded.
 template <int RG, class Seg>
 __device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, const int4* P4, float* acc, long long a0,
-                                        int len, int lmax, int c0, int Wd, unsigned long long* err) {
+                                        int len, int lmax, int c0, int Wd, unsigned long long* err, bool& bad) {
     constexpr int E = RG == 4 ? 4 : 2;
     const int lane = lane_id(), g = lane / RG, gl = lane % RG;
     int k0, k1;
@@ -481,7 +484,7 @@ __device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, cons
             }
             nxt = rg_seg_of<E>(s2, L2, a2);
             rg_fetch<E>(P4, nxt, gl, n0, n1);
-            rg_segment<RG, E>(P4, acc, cur, gl, c0v, c1v, Wd, c0, err);
+            rg_segment<RG, E>(P4, acc, cur, gl, c0v, c1v, Wd, p.W, c0, bad);
             __syncwarp();
         }
         s = ns;
@@ -500,8 +503,9 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
     static_assert(RG >= 4 && RG <= 16 && 32 % RG == 0, "lanes per row");
     const int lane = lane_id(), g = lane / RG, gl = lane % RG;
     const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);
-    float* acc = racc + g * p.W;
+    float* acc = racc + g * (p.W + 4);  // W columns and a spare
     unsigned long long* err = &p.hdr->err;
+    bool bad = false;
     for (long long idx = idx0; idx < end; idx += step) {
         const long long my = idx + g;
         long long a0 = 0, a1 = 0, out = 0, out_end = 0;
@@ -523,16 +527,17 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
         for (int t = 0; t < p.T; ++t) {
             const int c0 = t * p.W;
             const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
-            if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err);
-            else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err);
+            if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+            else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             rg_emit<RG>(acc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
             __syncwarp();
         }
         if (active && gl == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
     }
+    if (bad) atomicOr(err, ERR_B_COL);
 }
 
-// Light rows only, in row groups; R = 32/RG accumulators of W floats per warp.
+// Light rows only, in row groups; R = 32/RG accumulators of W + 4 floats per warp.
 // Launched behind k_numeric (which then skips light rows) with programmatic
 // dependent launch: its blocks may start while k_numeric's last blocks run.
 // Before exiting, each block waits for k_numeric to complete, so that work
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(256, 4) k_numeric_light(NumParams p) {
     constexpr int R = 32 / RG;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     float* racc = reinterpret_cast<float*>(smem);
-    for (int i = tid; i < nw * R * p.W; i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
+    for (int i = tid; i < nw * R * (p.W + 4); i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
     if (tid == 0) {
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(256, 4) k_numeric_light(NumParams p) {
     }
     __syncthreads();
     const long long* mark = p.s.stg_vals != nullptr ? p.s.flops : nullptr;
-    rg_light_rows<RG>(p, racc + (size_t)warp * R * p.W, s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
+    rg_light_rows<RG>(p, racc + (size_t)warp * R * (p.W + 4), s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
                       (long long)gridDim.x * nw * R, mark);
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -643,7 +648,7 @@ size_t numeric_dense_smem(int W, int warps, bool values) {
 
 size_t numeric_light_smem(int W, int warps, int rg) {
     if (rg != 4 && rg != 8 && rg != 16) return 0;
-    return (size_t)warps * (32 / rg) * 4 * (size_t)W;
+    return (size_t)warps * (32 / rg) * 4 * ((size_t)W + 4);  // W columns and a spare per row
 }
 
 template <bool VALUES, int G, bool PACKED>
