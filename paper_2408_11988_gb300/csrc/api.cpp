@@ -711,7 +711,7 @@ extern "C" ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, voi
 static const long long MSBFS_MAX_D = 65536;
 
 struct BfsLayout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, newbits = 0, blen = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, newbits = 0, blen = 0, fbits = 0, total = 0;
 };
 
 static BfsLayout bfs_layout(long long n, long long d, long long nnzA) {
@@ -730,6 +730,8 @@ static BfsLayout bfs_layout(long long n, long long d, long long nnzA) {
     L.newbits = take(sizeof(unsigned) * (size_t)n * (size_t)((d + 31) / 32));
     L.items = take(sizeof(long long) * (size_t)flops_item_capacity(n, nnzA));
     L.blen = take(sizeof(int) * (size_t)n);
+    const int dwp = msbfs_pull_words((int)std::min<long long>(d, 1 << 20));
+    if (dwp) L.fbits = take(sizeof(unsigned) * (size_t)n * (size_t)dwp);  // frontier bitmap, pull form
     L.total = off;
     return L;
 }
@@ -791,8 +793,9 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     ts_tuning t{};
     resolve_tuning(d, ts_tuning{}, t);
     LaunchCfg cfg = cfg_of(t);
+    unsigned* fbits = L.fbits ? (unsigned*)(b + L.fbits) : nullptr;
     TS_CUDA(launch_msbfs_step(dev(A), dev(F), (int)d, visited, levels, level, sc, newbits,
-                              (long long*)F_next->rowptr, cfg, st),
+                              (long long*)F_next->rowptr, cfg, st, fbits),
             fn);
     long long tot = 0;
     TS_CUDA(cudaMemcpyAsync(&tot, (long long*)F_next->rowptr + n, sizeof tot, cudaMemcpyDeviceToHost, st), fn);

@@ -123,9 +123,12 @@ size_t backward_smem(long long d, int warps);
 // Multi-source BFS (Alg. 3) levels.
 cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, int* levels,
                               long long* rp, int* col, cudaStream_t st);
+// fbits: workspace for the frontier as a bitmap (n x msbfs_pull_words(d)
+// words); with it and d <= 256 the pull form runs, else the list form.
 cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned* S, int* levels,
                               int level, const Sched& s, unsigned* newbits, long long* rp_next,
-                              const LaunchCfg& cfg, cudaStream_t st);
+                              const LaunchCfg& cfg, cudaStream_t st, unsigned* fbits = nullptr);
+int msbfs_pull_words(int d);
 cudaError_t launch_msbfs_emit(long long n, int d, const unsigned* newbits, const long long* rp,
                               int* col, long long cap, WsHeader* hdr, cudaStream_t st);
 

@@ -208,6 +208,178 @@ __global__ void k_msbfs_init_cols(long long n, int d, int dw, const int* __restr
     levels[(long long)v * d + s] = 0;
 }
 
+
+// ---------------------------------------------------------------------------
+// Pull expansion with the frontier as a bitmap (the dense-frontier form of
+// Alg. 3's N = A * F): F is first written as DWP words per row (d <= 256,
+// DWP = dw rounded up to a power of two), then row v ORs the bitmap rows of
+// its neighbours, one load of DWP words per entry of A, instead of gathering
+// each neighbour's list of frontier columns.  The cost per entry no longer
+// grows with the frontier's density.  The OR, the visited mask, the level
+// write and the new-bit words are those of the list form.
+// ---------------------------------------------------------------------------
+template <int DWP>
+__global__ void __launch_bounds__(256) k_frontier_bits(long long n, int d, const long long* __restrict__ Fp,
+                                                       long long nnzF, const int* __restrict__ Fi,
+                                                       unsigned* __restrict__ fb, unsigned long long* err) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        unsigned w[DWP];
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) w[m] = 0u;
+        const long long s = clampll(__ldg(Fp + v), 0, nnzF), e = clampll(__ldg(Fp + v + 1), s, nnzF);
+        for (long long j = s; j < e; ++j) {
+            const int c = __ldg(Fi + j);
+            if ((unsigned)c < (unsigned)d) {
+#pragma unroll
+                for (int m = 0; m < DWP; ++m) w[m] |= (c >> 5) == m ? 1u << (c & 31) : 0u;
+            } else {
+                atomicOr(err, ERR_B_COL);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) fb[v * DWP + m] = w[m];
+    }
+}
+
+// OR of the frontier bitmap rows of entries [e0, e1) of A, lane-strided.
+template <int DWP>
+__device__ __forceinline__ void pull_or(const BfsParams& p, const unsigned* __restrict__ fb, long long e0,
+                                        long long e1, int t0, int nt, unsigned acc[DWP], unsigned long long* err) {
+    for (long long e = e0 + t0; e < e1; e += nt) {
+        const int u = __ldg(p.Ai + e);
+        if ((unsigned)u >= (unsigned)p.nF) {
+            atomicOr(err, ERR_A_COL);
+            continue;
+        }
+        const unsigned* r = fb + (long long)u * DWP;
+        if constexpr (DWP >= 4) {
+#pragma unroll
+            for (int m = 0; m < DWP; m += 4) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4*>(r + m));
+                acc[m] |= x.x;
+                acc[m + 1] |= x.y;
+                acc[m + 2] |= x.z;
+                acc[m + 3] |= x.w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < DWP; ++m) acc[m] |= __ldg(r + m);
+        }
+    }
+}
+
+// Settle row `row` from the OR of its neighbours (all lanes of the warp hold
+// the full OR): new = N and not S; S |= new; new bits stored for the
+// read-out; levels written, lane l taking bit l of every word.  Returns the
+// number of new bits (all lanes).
+template <int DWP>
+__device__ __forceinline__ int pull_settle(const BfsParams& p, long long row, const unsigned acc[DWP]) {
+    const int lane = lane_id();
+    int c = 0;
+#pragma unroll
+    for (int m = 0; m < DWP; ++m) {
+        if (m >= p.dw) break;
+        const int bits = p.d - 32 * m;
+        const unsigned valid = bits >= 32 ? FULL : ((1u << bits) - 1u);
+        const unsigned old = __ldg(p.S + row * p.dw + m);
+        const unsigned nw = acc[m] & ~old & valid;
+        if (lane == 0) {
+            p.newbits[row * p.dw + m] = nw;
+            if (nw) p.S[row * p.dw + m] = old | nw;
+        }
+        if ((nw >> lane) & 1u) p.levels[row * p.d + 32 * m + lane] = p.level;
+        c += __popc(nw);
+    }
+    return c;
+}
+
+template <int DWP>
+__global__ void __launch_bounds__(256) k_msbfs_pull(BfsParams p, const unsigned* __restrict__ fb) {
+    __shared__ long long s_item, s_nheavy, s_nrows;
+    __shared__ unsigned s_or[DWP];
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    if (tid == 0) {
+        long long nh = 0, nr = 0;
+        for (int c = 1; c < NUM_CLASSES; ++c) {
+            nr += p.hdr->hist[c];
+            if (c >= p.cta_class) nh += p.hdr->hist[c];
+        }
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    if (tid < DWP) s_or[tid] = 0u;
+    __syncthreads();
+    const long long nheavy = s_nheavy, nrows = s_nrows;
+    unsigned long long* err = &p.hdr->err;
+    // heavy rows: the block's threads split the row's entries
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const int row = p.perm[h];
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        unsigned acc[DWP];
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) acc[m] = 0u;
+        pull_or<DWP>(p, fb, a0, a1, tid, blockDim.x, acc, err);
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) {
+            const unsigned x = __reduce_or_sync(FULL, acc[m]);
+            if (lane == 0 && x) atomicOr(&s_or[m], x);
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int m = 0; m < DWP; ++m) acc[m] = s_or[m];
+            const int c = pull_settle<DWP>(p, row, acc);
+            if (lane == 0) p.cnt_next[row] = c;
+        }
+        __syncthreads();
+        if (tid < DWP) s_or[tid] = 0u;
+    }
+    // light rows: one warp per row
+    for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
+         idx += (long long)gridDim.x * nw) {
+        const int row = p.perm[idx];
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        unsigned acc[DWP];
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) acc[m] = 0u;
+        pull_or<DWP>(p, fb, a0, a1, lane, 32, acc, err);
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) acc[m] = __reduce_or_sync(FULL, acc[m]);
+        const int c = pull_settle<DWP>(p, row, acc);
+        if (lane == 0) p.cnt_next[row] = c;
+    }
+}
+
+template <int DWP>
+static cudaError_t launch_pull(const BfsParams& p, const DevCsr& F, unsigned* fb, const LaunchCfg& cfg,
+                               cudaStream_t st) {
+    const long long n = F.nrows;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    count_launch();
+    k_frontier_bits<DWP><<<(unsigned)blocks, 256, 0, st>>>(n, p.d, F.rowptr, F.nnz, F.col, fb, &p.hdr->err);
+    const int threads = 32 * cfg.warps_per_cta;
+    const int grid = persistent_grid((const void*)k_msbfs_pull<DWP>, threads, 0, cfg.sms);
+    count_launch();
+    k_msbfs_pull<DWP><<<grid, threads, 0, st>>>(p, fb);
+    return cudaGetLastError();
+}
+
+// Words per bitmap row of the pull form (0: list form only, d > 256).
+int msbfs_pull_words(int d) {
+    const int dw = (d + 31) / 32;
+    if (dw > 8) return 0;
+    return dw <= 1 ? 1 : (dw <= 2 ? 2 : (dw <= 4 ? 4 : 8));
+}
+
 cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, int* levels,
                               long long* rp, int* col, cudaStream_t st) {
     cudaError_t e;
@@ -223,7 +395,7 @@ cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, i
 
 cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned* S, int* levels, int level,
                               const Sched& s, unsigned* newbits, long long* rp_next, const LaunchCfg& cfg,
-                              cudaStream_t st) {
+                              cudaStream_t st, unsigned* fbits) {
     cudaError_t e;
     const long long n = A.nrows;
     if ((e = launch_row_flops(A, F, s, st))) return e;
@@ -252,6 +424,17 @@ cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned*
     p.perm = s.perm;
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
+    const int dwp = msbfs_pull_words(d);
+    if (fbits && dwp) {
+        switch (dwp) {
+            case 1: e = launch_pull<1>(p, F, fbits, cfg, st); break;
+            case 2: e = launch_pull<2>(p, F, fbits, cfg, st); break;
+            case 4: e = launch_pull<4>(p, F, fbits, cfg, st); break;
+            default: e = launch_pull<8>(p, F, fbits, cfg, st); break;
+        }
+        if (e) return e;
+        return launch_scan_inplace(rp_next + 1, n, s.partial, st);
+    }
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)dw * cfg.warps_per_cta;
     if (smem > 48 * 1024 &&

@@ -14,7 +14,10 @@ from paper_2408_11988_gb300 import DeviceCSR
 from paper_2408_11988_gb300.msbfs import msbfs
 
 
-@pytest.mark.parametrize("scale,ef,d", [(10, 8, 128), (12, 16, 128), (9, 4, 40), (8, 2, 1)])
+# d up to 256 runs the bitmap pull form (1, 2, 4 or 8 words per row), d above
+# it the list form
+@pytest.mark.parametrize("scale,ef,d", [(10, 8, 128), (12, 16, 128), (9, 4, 40), (8, 2, 1), (10, 8, 200),
+                                        (9, 8, 300), (10, 6, 64), (9, 8, 33), (11, 16, 256)])
 def test_msbfs_matches_oracle(scale, ef, d):
     A = synth.rmat(scale, ef, 60 + scale, symmetrize=True)
     src = synth.sources(A, d, 61)
