@@ -543,7 +543,7 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
 // Before exiting, each block waits for k_numeric to complete, so that work
 // queued after this kernel sees all of C.
 template <int RG>
-__global__ void __launch_bounds__(256, 4) k_numeric_light(NumParams p) {
+__global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_nheavy, s_nrows;
     constexpr int R = 32 / RG;
