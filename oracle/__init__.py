@@ -58,6 +58,7 @@ def _L():
                 "oracle_spgemm_count": (i64, [i64, p, p, p, p, p, i64, p]),
                 "oracle_spgemm": (ci, [i64, ci, p, p, p, p, p, p, p, i64, p, p, p, p]),
                 "oracle_msbfs": (i64, [i64, p, p, i64, p, p, p, i64]),
+                "oracle_msbfs_parents": (i64, [i64, p, p, i64, p, p, p, p, i64]),
                 "oracle_backward": (ci, [i64, i64, p, p, p, i64, p, p, p, p, p, p, p, p, p, p]),
                 "oracle_backward_dA_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
                 "oracle_backward_dB_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
@@ -135,6 +136,23 @@ def msbfs(A, sources: np.ndarray, maxlev: int = 4096):
     if prods < 0:
         raise RuntimeError(f"oracle_msbfs failed ({prods})")
     return levels, int(prods), fnnz[: prods + 1].copy()
+
+
+def msbfs_parents(A, sources: np.ndarray, maxlev: int = 4096):
+    """Alg. 3 with the (sel2nd, min) semiring (BFS-tree variant, Sec. IV):
+    returns (levels int32[n, d], parents int32[n, d], products, frontier nnz
+    per level).  Dense n x d working arrays: small inputs only."""
+    n = A.nrows
+    src = _i32(sources)
+    d = len(src)
+    levels = np.empty((n, d), dtype=np.int32)
+    parents = np.empty((n, d), dtype=np.int32)
+    fnnz = np.zeros(maxlev, dtype=np.int64)
+    prods = _L().oracle_msbfs_parents(n, _p(_i64(A.rowptr)), _p(_i32(A.col)), d, _p(src), _p(levels),
+                                      _p(parents), _p(fnnz), maxlev)
+    if prods < 0:
+        raise RuntimeError(f"oracle_msbfs_parents failed ({prods})")
+    return levels, parents, int(prods), fnnz[: prods + 1].copy()
 
 
 def bfs_levels(A, source: int) -> np.ndarray:

@@ -16,7 +16,13 @@
  *  - in the boolean (or, select2nd) semiring a stored entry of A means
  *    "true", so the product keeps B's truth value and the sum is OR;
  *  - BFS levels: sources are level 0, a vertex first entering the frontier
- *    of source s at iteration t gets level t, unreached is -1.
+ *    of source s at iteration t gets level t, unreached is -1;
+ *  - BFS parents with the (sel2nd, min) semiring (Sec. IV, the BFS-tree
+ *    variant of Alg. 3): a frontier entry (u, s) carries the value u, the
+ *    product of a stored A(v,u) with it selects that value and the sum is
+ *    the minimum, so a newly reached (v, s) gets as parent the smallest
+ *    neighbour u of v in the frontier of s; a source is its own parent,
+ *    unreached is -1.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -185,6 +191,78 @@ int64_t oracle_msbfs(int64_t n, const int64_t* Ap, const int32_t* Ai, int64_t d,
     }
 done:
     free(S); free(Fp); free(Np); free(cnt); free(Fi); free(Ni);
+    return products;
+}
+
+/*
+ * Alg. 3 with the (sel2nd, min) semiring: the frontier F holds, for each
+ * (u, s) in it, the value u; N(v, s) = min over the stored A(v, u) with
+ * (u, s) in F of F(u, s); the new frontier is N minus S with each entry's
+ * value reset to its own row index, and the value N(v, s) of a new entry is
+ * v's parent in the BFS tree of source s.  Dense n x d arrays (small inputs
+ * only).  Returns the number of products (iterations) or < 0 on failure.
+ */
+int64_t oracle_msbfs_parents(int64_t n, const int64_t* Ap, const int32_t* Ai, int64_t d, const int32_t* src,
+                             int32_t* levels, int32_t* parents, int64_t* frontier_nnz, int64_t maxlev) {
+    const int64_t nd = n * d > 0 ? n * d : 1;
+    int32_t* F = (int32_t*)malloc((size_t)nd * sizeof(int32_t)); /* frontier values, -1 = absent */
+    int32_t* N = (int32_t*)malloc((size_t)nd * sizeof(int32_t));
+    unsigned char* S = (unsigned char*)calloc((size_t)nd, 1);
+    int64_t products = -1;
+    if (!F || !N || !S) goto done;
+    for (int64_t t = 0; t < n * d; ++t) {
+        levels[t] = -1;
+        parents[t] = -1;
+        F[t] = -1;
+    }
+    for (int64_t s = 0; s < d; ++s) {
+        const int64_t v = src[s];
+        F[v * d + s] = (int32_t)v;
+        S[v * d + s] = 1;
+        levels[v * d + s] = 0;
+        parents[v * d + s] = (int32_t)v;
+    }
+    if (maxlev < 1) { products = -2; goto done; }
+    int64_t fn = 0;
+    for (int64_t t = 0; t < n * d; ++t) fn += F[t] >= 0;
+    frontier_nnz[0] = fn;
+    products = 0;
+    int64_t level = 0;
+    while (fn > 0) {
+        ++level;
+        /* N = A (sel2nd, min) F */
+        for (int64_t t = 0; t < n * d; ++t) N[t] = -1;
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t e = Ap[v]; e < Ap[v + 1]; ++e) {
+                const int64_t u = Ai[e];
+                for (int64_t s = 0; s < d; ++s) {
+                    const int32_t f = F[u * d + s];
+                    if (f < 0) continue;                 /* no stored frontier entry */
+                    int32_t* x = &N[v * d + s];
+                    if (*x < 0 || f < *x) *x = f;       /* sel2nd, then min */
+                }
+            }
+        ++products;
+        /* F = N \ S with values reset to the row index; parents and levels
+         * of the new entries; S = S | N */
+        fn = 0;
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t s = 0; s < d; ++s) {
+                const int64_t t = v * d + s;
+                F[t] = -1;
+                if (N[t] >= 0 && !S[t]) {
+                    F[t] = (int32_t)v;
+                    parents[t] = N[t];
+                    levels[t] = (int32_t)level;
+                    ++fn;
+                }
+                if (N[t] >= 0) S[t] = 1;
+            }
+        if (level >= maxlev) { products = -2; goto done; }
+        frontier_nnz[level] = fn;
+    }
+done:
+    free(F); free(N); free(S);
     return products;
 }
 

@@ -209,6 +209,66 @@ def test_msbfs_matches_queue_bfs(kind):
     assert fnnz.sum() == int((levels >= 0).sum())
 
 
+def test_msbfs_parents_golden():
+    g = json.load(open(os.path.join(GOLDEN, "alg3_parents_small.json")))
+    A = undirected(g["n"], g["edges_undirected"])
+    levels, parents, prods, fnnz = oracle.msbfs_parents(A, np.array(g["sources"]))
+    np.testing.assert_array_equal(levels, np.array(g["levels"]))
+    np.testing.assert_array_equal(parents, np.array(g["parents"]))
+    assert prods == g["products"]
+    # the same graph's levels from the (or, select2nd) Alg. 3
+    lv2, prods2, _ = oracle.msbfs(A, np.array(g["sources"]))
+    np.testing.assert_array_equal(lv2, levels)
+    assert prods2 == prods
+
+
+def check_bfs_tree(A, srcs, levels, parents):
+    """The BFS-tree definition, checked edge by edge without the oracle:
+    a source is its own parent, an unreached vertex has -1, and any other
+    vertex's parent is its smallest neighbour one level closer."""
+    for si, s in enumerate(srcs):
+        ref = queue_bfs(A, int(s))
+        np.testing.assert_array_equal(levels[:, si], ref)
+        for v in range(A.nrows):
+            nb = A.col[A.rowptr[v]:A.rowptr[v + 1]]
+            if ref[v] < 0:
+                assert parents[v, si] == -1
+            elif v == s:
+                assert parents[v, si] == s
+            else:
+                closer = [int(u) for u in nb if ref[u] == ref[v] - 1]
+                assert closer and parents[v, si] == min(closer), (v, si)
+
+
+@pytest.mark.parametrize("kind", ["rmat", "er", "chain", "directed"])
+def test_msbfs_parents_are_min_bfs_tree(kind):
+    if kind == "rmat":
+        A = synth.rmat(8, 8, 23, symmetrize=True)
+    elif kind == "er":
+        A0 = synth.er(200, 3, 24)
+        A = undirected(200, list(zip(np.repeat(np.arange(200), 3).tolist(), A0.col.tolist())))
+    elif kind == "chain":
+        A = undirected(30, [(i, i + 1) for i in range(29)] + [(0, 29)])
+    else:
+        A = synth.rmat(7, 6, 25)  # directed: the pull follows A's rows (a BFS over A^T)
+    srcs = synth.sources(A, 16, 6)
+    levels, parents, prods, fnnz = oracle.msbfs_parents(A, srcs)
+    if kind == "directed":
+        lv2, _, _ = oracle.msbfs(A, srcs)
+        np.testing.assert_array_equal(levels, lv2)
+        # parent p of v: stored A(v, p), level one less, smallest such
+        for si in range(len(srcs)):
+            for v in range(A.nrows):
+                if levels[v, si] > 0:
+                    nb = A.col[A.rowptr[v]:A.rowptr[v + 1]]
+                    closer = [int(u) for u in nb if levels[u, si] == levels[v, si] - 1]
+                    assert parents[v, si] == min(closer)
+    else:
+        check_bfs_tree(A, srcs, levels, parents)
+    assert prods == int(levels.max()) + 1
+    assert fnnz.sum() == int((levels >= 0).sum())
+
+
 def test_backward_matches_dense_formulas_and_finite_differences():
     rng = np.random.default_rng(5)
     n, d = 30, 12
