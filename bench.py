@@ -50,6 +50,9 @@ WORKLOADS = {
                    "as one CUDA-graph replay", None, None, True),
     "msbfs-s20": ("multi-source BFS, R-MAT scale 20, edge factor 16, symmetrised, 128 sources, "
                   "(or, select2nd) iterated to an empty frontier", None, None, False),
+    "msbfs-parents-s20": ("multi-source BFS with BFS-tree parents, R-MAT scale 20, edge factor 16, "
+                          "symmetrised, 128 sources, (sel2nd, min) iterated to an empty frontier",
+                          None, None, False),
 }
 
 
@@ -221,7 +224,7 @@ def main():
         return run_reference(args, ws, rank, desc, want_bwd)
     if args.workload == "batched-64":
         return run_batched(args, ws, rank, local, desc)
-    if args.workload == "msbfs-s20":
+    if args.workload in ("msbfs-s20", "msbfs-parents-s20"):
         return run_msbfs(args, ws, rank, local, desc)
 
     import torch
@@ -537,8 +540,9 @@ def run_msbfs(args, ws, rank, local, desc):
     A, src = synth.msbfs_graph(seed=synth.BASE_SEED + 2 + 1000 * rank)
     Ad = DeviceCSR.from_host(A, with_values=False)
     s = torch.as_tensor(src)
+    par = args.workload == "msbfs-parents-s20"
     for _ in range(args.warmup):
-        r = msbfs(Ad, s)
+        r = msbfs(Ad, s, parents=par)
     torch.cuda.synchronize()
     deg = np.diff(A.rowptr)
     lev = r.levels.cpu().numpy()
@@ -548,18 +552,19 @@ def run_msbfs(args, ws, rank, local, desc):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.steps):
-            r = msbfs(Ad, s)
+            r = msbfs(Ad, s, parents=par)
         b.record()
         torch.cuda.synchronize()
     launches = N.lib().ts_kernel_launches() - l0
     ms = _max_over_ranks(dist, a.elapsed_time(b) / args.steps)
     if rank == 0:
         print(json.dumps({
-            "metric": "multi-source BFS boolean products/s", "value": round(products * ws / (ms * 1e-3), 1),
+            "metric": "multi-source BFS (sel2nd, min) products/s" if par else "multi-source BFS boolean products/s",
+            "value": round(products * ws / (ms * 1e-3), 1),
             "unit": "products/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "msbfs-s20", "description": desc, "n": A.nrows, "nnz_A": A.nnz,
+            "config": {"workload": args.workload, "description": desc, "n": A.nrows, "nnz_A": A.nnz,
                        "sources": len(src), "levels": r.products, "frontier_nnz": r.frontier_nnz,
                        "products": products, "parallelism": f"replicas x{ws}"},
             "levels_per_s": round(r.products * ws / (ms * 1e-3), 1),

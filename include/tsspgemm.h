@@ -281,6 +281,32 @@ TS_API ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t
                      int32_t* levels, int32_t level, const ts_csr_desc* F_next,
                      int64_t F_next_capacity, int64_t* nnz_next_host, void* ws, size_t ws_bytes,
                      void* stream);
+/*
+ * BFS-tree variant of the level step (paper Sec. IV: Alg. 3 with the
+ * (sel2nd, min) semiring, used when the BFS tree is to be reconstructed): the
+ * same step as msbfs_step, and in addition parents[v*d + s] = the smallest
+ * neighbour u of v (a stored A(v,u)) that is in the frontier of source s, for
+ * every (v, s) that enters the frontier at this level.  parents: device
+ * int32[n*d], vertex-major like levels, caller-owned; entries of vertices not
+ * reached at this level are left untouched.  Requires d <= 256 (the bitmap
+ * pull form of the step); larger d returns TS_ERR_UNSUPPORTED.  Other
+ * arguments, errors and synchronisation as msbfs_step.
+ */
+TS_API ts_status msbfs_step_parents(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
+                                    int32_t* levels, int32_t* parents, int32_t level,
+                                    const ts_csr_desc* F_next, int64_t F_next_capacity,
+                                    int64_t* nnz_next_host, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Parents before the first step: parents[v*d + s] = -1 everywhere, and
+ * parents[src[s]*d + s] = src[s] (a source is its own parent).  sources_dev:
+ * device int32[d]; parents: device int32[n*d].  d <= 256.  Stream-ordered,
+ * no synchronisation.  Errors: TS_ERR_INVALID_ARG, TS_ERR_UNSUPPORTED,
+ * TS_ERR_CUDA.
+ */
+TS_API ts_status msbfs_init_parents(int64_t n, int64_t d, const int32_t* sources_dev, int32_t* parents,
+                                    void* stream);
+
 /* Writes F_next->col from the state a TS_ERR_CAPACITY msbfs_step left in ws. */
 TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, void* ws,
                      size_t ws_bytes, void* stream);

@@ -91,6 +91,9 @@ _SIGS = {
     "msbfs_step": (c_int32, [P(CsrDesc), P(CsrDesc), c_void_p, c_void_p, c_int32, P(CsrDesc),
                              c_int64, P(c_int64), c_void_p, c_size_t, c_void_p]),
     "msbfs_emit": (c_int32, [P(CsrDesc), c_int64, c_void_p, c_size_t, c_void_p]),
+    "msbfs_step_parents": (c_int32, [P(CsrDesc), P(CsrDesc), c_void_p, c_void_p, c_void_p, c_int32, P(CsrDesc),
+                                     c_int64, P(c_int64), c_void_p, c_size_t, c_void_p]),
+    "msbfs_init_parents": (c_int32, [c_int64, c_int64, c_void_p, c_void_p, c_void_p]),
     "ts_batched_plan_create": (c_int32, [c_int32, P(CsrDesc), P(CsrDesc), c_int32, P(Tuning),
                                          P(c_void_p)]),
     "ts_batched_plan_destroy": (c_int32, [c_void_p]),

@@ -760,11 +760,9 @@ extern "C" ts_status msbfs_init(int64_t n, int64_t d, const int32_t* sources_dev
     return ok();
 }
 
-extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
-                                int32_t* levels, int32_t level, const ts_csr_desc* F_next,
-                                int64_t F_next_capacity, int64_t* nnz_next_host, void* ws,
-                                size_t ws_bytes, void* stream) {
-    const char* fn = "msbfs_step";
+static ts_status bfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited, int32_t* levels,
+                          int32_t* parents, int32_t level, const ts_csr_desc* F_next, int64_t F_next_capacity,
+                          int64_t* nnz_next_host, void* ws, size_t ws_bytes, void* stream, const char* fn) {
     ts_status s;
     if ((s = check_desc(A, "A", false)) != TS_OK) return s;
     if ((s = check_desc(F, "F", false)) != TS_OK) return s;
@@ -794,8 +792,9 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     resolve_tuning(d, ts_tuning{}, t);
     LaunchCfg cfg = cfg_of(t);
     unsigned* fbits = L.fbits ? (unsigned*)(b + L.fbits) : nullptr;
+    if (parents && !fbits) return fail(TS_ERR_UNSUPPORTED, "%s: parents need d <= 256", fn);
     TS_CUDA(launch_msbfs_step(dev(A), dev(F), (int)d, visited, levels, level, sc, newbits,
-                              (long long*)F_next->rowptr, cfg, st, fbits),
+                              (long long*)F_next->rowptr, cfg, st, fbits, parents),
             fn);
     long long tot = 0;
     TS_CUDA(cudaMemcpyAsync(&tot, (long long*)F_next->rowptr + n, sizeof tot, cudaMemcpyDeviceToHost, st), fn);
@@ -810,6 +809,33 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
     TS_CUDA(launch_msbfs_emit(n, (int)d, newbits, (const long long*)F_next->rowptr, F_next->col,
                               F_next_capacity, sc.hdr, st),
             fn);
+    return ok();
+}
+
+extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
+                                int32_t* levels, int32_t level, const ts_csr_desc* F_next,
+                                int64_t F_next_capacity, int64_t* nnz_next_host, void* ws,
+                                size_t ws_bytes, void* stream) {
+    return bfs_step(A, F, visited, levels, nullptr, level, F_next, F_next_capacity, nnz_next_host, ws, ws_bytes,
+                    stream, "msbfs_step");
+}
+
+extern "C" ts_status msbfs_step_parents(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t* visited,
+                                        int32_t* levels, int32_t* parents, int32_t level,
+                                        const ts_csr_desc* F_next, int64_t F_next_capacity,
+                                        int64_t* nnz_next_host, void* ws, size_t ws_bytes, void* stream) {
+    if (!parents) return fail(TS_ERR_INVALID_ARG, "msbfs_step_parents: parents is NULL");
+    return bfs_step(A, F, visited, levels, parents, level, F_next, F_next_capacity, nnz_next_host, ws, ws_bytes,
+                    stream, "msbfs_step_parents");
+}
+
+extern "C" ts_status msbfs_init_parents(int64_t n, int64_t d, const int32_t* sources_dev, int32_t* parents,
+                                        void* stream) {
+    const char* fn = "msbfs_init_parents";
+    if (n < 0 || d < 1 || !sources_dev || !parents) return fail(TS_ERR_INVALID_ARG, "%s: bad argument", fn);
+    if (n > INT32_MAX) return fail(TS_ERR_UNSUPPORTED, "%s: n >= 2^31", fn);
+    if (d > 256) return fail(TS_ERR_UNSUPPORTED, "%s: parents need d <= 256", fn);
+    TS_CUDA(launch_msbfs_init_parents(n, (int)d, sources_dev, parents, (cudaStream_t)stream), fn);
     return ok();
 }
 

@@ -127,8 +127,10 @@ cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, i
 // words); with it and d <= 256 the pull form runs, else the list form.
 cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned* S, int* levels,
                               int level, const Sched& s, unsigned* newbits, long long* rp_next,
-                              const LaunchCfg& cfg, cudaStream_t st, unsigned* fbits = nullptr);
+                              const LaunchCfg& cfg, cudaStream_t st, unsigned* fbits = nullptr,
+                              int* parents = nullptr);
 int msbfs_pull_words(int d);
+cudaError_t launch_msbfs_init_parents(long long n, int d, const int* src, int* parents, cudaStream_t st);
 cudaError_t launch_msbfs_emit(long long n, int d, const unsigned* newbits, const long long* rp,
                               int* col, long long cap, WsHeader* hdr, cudaStream_t st);
 

@@ -59,6 +59,7 @@ struct BfsParams {
     int level;
     unsigned* newbits;
     long long* cnt_next;  // F_next.rowptr + 1
+    int* parents;         // int32[n][d] BFS-tree parents (pull form only), or nullptr
     const int* perm;
     WsHeader* hdr;
     int cta_class;
@@ -274,16 +275,19 @@ __device__ __forceinline__ void pull_or(const BfsParams& p, const unsigned* __re
 // read-out; levels written, lane l taking bit l of every word.  Returns the
 // number of new bits (all lanes).
 template <int DWP>
-__device__ __forceinline__ int pull_settle(const BfsParams& p, long long row, const unsigned acc[DWP]) {
+__device__ __forceinline__ int pull_settle(const BfsParams& p, long long row, const unsigned acc[DWP],
+                                           unsigned nws[DWP]) {
     const int lane = lane_id();
     int c = 0;
 #pragma unroll
     for (int m = 0; m < DWP; ++m) {
-        if (m >= p.dw) break;
+        nws[m] = 0u;
+        if (m >= p.dw) continue;
         const int bits = p.d - 32 * m;
         const unsigned valid = bits >= 32 ? FULL : ((1u << bits) - 1u);
         const unsigned old = __ldg(p.S + row * p.dw + m);
         const unsigned nw = acc[m] & ~old & valid;
+        nws[m] = nw;
         if (lane == 0) {
             p.newbits[row * p.dw + m] = nw;
             if (nw) p.S[row * p.dw + m] = old | nw;
@@ -292,6 +296,55 @@ __device__ __forceinline__ int pull_settle(const BfsParams& p, long long row, co
         c += __popc(nw);
     }
     return c;
+}
+
+// Parents of the new bits of `row` (the (sel2nd, min) semiring of the
+// BFS-tree variant: the smallest neighbour in the frontier of each source).
+// A's row is ascending, so the neighbours are scanned 32 at a time in order
+// and each still-open bit goes to the first lane whose frontier row holds it
+// (an exclusive prefix OR over the lanes); the scan stops once every new bit
+// has its parent.  One warp, all lanes converged; rem is warp-uniform.
+template <int DWP>
+__device__ __forceinline__ void pull_parents(const BfsParams& p, const unsigned* __restrict__ fb, long long row,
+                                             long long a0, long long a1, unsigned rem[DWP]) {
+    const int lane = lane_id();
+    unsigned open = 0u;
+#pragma unroll
+    for (int m = 0; m < DWP; ++m) open |= rem[m];
+    for (long long e0 = a0; e0 < a1 && open; e0 += 32) {
+        const long long e = e0 + lane;
+        int u = -1;
+        unsigned hit[DWP];
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) hit[m] = 0u;
+        if (e < a1) {
+            u = __ldg(p.Ai + e);
+            if ((unsigned)u < (unsigned)p.nF) {
+#pragma unroll
+                for (int m = 0; m < DWP; ++m) hit[m] = __ldg(fb + (long long)u * DWP + m) & rem[m];
+            }
+        }
+        open = 0u;
+#pragma unroll
+        for (int m = 0; m < DWP; ++m) {
+            unsigned incl = hit[m];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl |= t;
+            }
+            unsigned excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0u;
+            unsigned mine = hit[m] & ~excl;
+            while (mine) {
+                const int b = __ffs(mine) - 1;
+                mine &= mine - 1;
+                p.parents[row * p.d + 32 * m + b] = u;
+            }
+            rem[m] &= ~__shfl_sync(FULL, incl, 31);
+            open |= rem[m];
+        }
+    }
 }
 
 template <int DWP>
@@ -335,8 +388,10 @@ __global__ void __launch_bounds__(256) k_msbfs_pull(BfsParams p, const unsigned*
         if (warp == 0) {
 #pragma unroll
             for (int m = 0; m < DWP; ++m) acc[m] = s_or[m];
-            const int c = pull_settle<DWP>(p, row, acc);
+            unsigned nws[DWP];
+            const int c = pull_settle<DWP>(p, row, acc, nws);
             if (lane == 0) p.cnt_next[row] = c;
+            if (p.parents) pull_parents<DWP>(p, fb, row, a0, a1, nws);
         }
         __syncthreads();
         if (tid < DWP) s_or[tid] = 0u;
@@ -353,8 +408,10 @@ __global__ void __launch_bounds__(256) k_msbfs_pull(BfsParams p, const unsigned*
         pull_or<DWP>(p, fb, a0, a1, lane, 32, acc, err);
 #pragma unroll
         for (int m = 0; m < DWP; ++m) acc[m] = __reduce_or_sync(FULL, acc[m]);
-        const int c = pull_settle<DWP>(p, row, acc);
+        unsigned nws[DWP];
+        const int c = pull_settle<DWP>(p, row, acc, nws);
         if (lane == 0) p.cnt_next[row] = c;
+        if (p.parents) pull_parents<DWP>(p, fb, row, a0, a1, nws);
     }
 }
 
@@ -380,6 +437,23 @@ int msbfs_pull_words(int d) {
     return dw <= 1 ? 1 : (dw <= 2 ? 2 : (dw <= 4 ? 4 : 8));
 }
 
+// parents = -1, and each source its own parent in its column.
+__global__ void k_msbfs_init_parents(long long n, int d, const int* __restrict__ src, int* parents) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d) return;
+    const int v = src[s];
+    if (v < 0 || (long long)v >= n) return;
+    parents[(long long)v * d + s] = v;
+}
+
+cudaError_t launch_msbfs_init_parents(long long n, int d, const int* src, int* parents, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(parents, 0xFF, sizeof(int) * (size_t)n * d, st))) return e;
+    count_launch();
+    k_msbfs_init_parents<<<(d + 127) / 128, 128, 0, st>>>(n, d, src, parents);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, int* levels,
                               long long* rp, int* col, cudaStream_t st) {
     cudaError_t e;
@@ -395,7 +469,7 @@ cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, i
 
 cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned* S, int* levels, int level,
                               const Sched& s, unsigned* newbits, long long* rp_next, const LaunchCfg& cfg,
-                              cudaStream_t st, unsigned* fbits) {
+                              cudaStream_t st, unsigned* fbits, int* parents) {
     cudaError_t e;
     const long long n = A.nrows;
     if ((e = launch_row_flops(A, F, s, st))) return e;
@@ -421,10 +495,12 @@ cudaError_t launch_msbfs_step(const DevCsr& A, const DevCsr& F, int d, unsigned*
     p.level = level;
     p.newbits = newbits;
     p.cnt_next = rp_next + 1;
+    p.parents = parents;
     p.perm = s.perm;
     p.hdr = s.hdr;
     p.cta_class = cfg.cta_class;
     const int dwp = msbfs_pull_words(d);
+    if (parents && !(fbits && dwp)) return cudaErrorInvalidValue;  // parents: pull form only
     if (fbits && dwp) {
         switch (dwp) {
             case 1: e = launch_pull<1>(p, F, fbits, cfg, st); break;

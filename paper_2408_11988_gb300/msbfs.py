@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import ctypes
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional
 
 import torch
 
@@ -16,10 +16,14 @@ class BfsResult:
     levels: torch.Tensor          # int32[n, d], -1 = unreached
     products: int                 # TS-SpGEMM products computed (loop iterations)
     frontier_nnz: List[int] = field(default_factory=list)  # nnz(F) entering each iteration
+    parents: Optional[torch.Tensor] = None  # int32[n, d] BFS-tree parents (with parents=True)
 
 
-def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream=None) -> BfsResult:
-    """Levels of every vertex from each of the d sources (columns)."""
+def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream=None,
+          parents: bool = False) -> BfsResult:
+    """Levels of every vertex from each of the d sources (columns); with
+    parents=True also the BFS tree of each source by the (sel2nd, min)
+    semiring (the smallest neighbour on the previous level; d <= 256)."""
     dev = A.rowptr.device
     n = A.nrows
     src = sources.to(device=dev, dtype=torch.int32).contiguous()
@@ -43,6 +47,10 @@ def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream
     st = _stream(stream)
     f0 = F.desc()
     N.call("msbfs_init", n, d, _ptr(src), _ptr(visited), _ptr(levels), ctypes.byref(f0), st)
+    par = None
+    if parents:
+        par = torch.empty(n * d, dtype=torch.int32, device=dev)
+        N.call("msbfs_init_parents", n, d, _ptr(src), _ptr(par), st)
     F.nnz_ = d
     sizes = [d]
     products = 0
@@ -52,9 +60,14 @@ def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream
         level += 1
         fd, gd = F.desc(), G.desc()
         nnz = ctypes.c_int64(0)
-        status = N.lib().msbfs_step(ctypes.byref(Ad), ctypes.byref(fd), _ptr(visited), _ptr(levels),
-                                    level, ctypes.byref(gd), G.col.numel(), ctypes.byref(nnz),
-                                    _ptr(ws), ws.numel(), st)
+        if par is None:
+            status = N.lib().msbfs_step(ctypes.byref(Ad), ctypes.byref(fd), _ptr(visited), _ptr(levels),
+                                        level, ctypes.byref(gd), G.col.numel(), ctypes.byref(nnz),
+                                        _ptr(ws), ws.numel(), st)
+        else:
+            status = N.lib().msbfs_step_parents(ctypes.byref(Ad), ctypes.byref(fd), _ptr(visited),
+                                                _ptr(levels), _ptr(par), level, ctypes.byref(gd),
+                                                G.col.numel(), ctypes.byref(nnz), _ptr(ws), ws.numel(), st)
         if status == N.TS_ERR_CAPACITY:
             G.col = torch.empty(int(nnz.value), dtype=torch.int32, device=dev)
             gd = G.desc()
@@ -65,4 +78,4 @@ def msbfs(A: DeviceCSR, sources: torch.Tensor, max_levels: int = 1 << 20, stream
         G.nnz_ = int(nnz.value)
         sizes.append(G.nnz)
         F, G = G, F
-    return BfsResult(levels.view(n, d), products, sizes)
+    return BfsResult(levels.view(n, d), products, sizes, None if par is None else par.view(n, d))

@@ -68,5 +68,16 @@ def test_host_side_errors(lib):
     assert lib.ts_plan_destroy(h) == N.TS_OK
     assert lib.msbfs_workspace_size(10, 30, 0, ctypes.byref(sz)) == N.TS_ERR_INVALID_ARG
     assert lib.msbfs_workspace_size(10, 30, 128, ctypes.byref(sz)) == N.TS_OK
+    # parents: the bitmap pull form only (d <= 256); caught on the host
+    A2 = N.CsrDesc(10, 10, 0, 8, None, None)
+    F2 = N.CsrDesc(10, 300, 0, 8, None, None)
+    nn = ctypes.c_int64()
+    assert lib.msbfs_step_parents(ctypes.byref(A2), ctypes.byref(F2), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                  ctypes.c_void_p(256), 1, ctypes.byref(F2), 0, ctypes.byref(nn),
+                                  ctypes.c_void_p(256), 1 << 30, None) == N.TS_ERR_UNSUPPORTED
+    assert lib.msbfs_step_parents(ctypes.byref(A2), ctypes.byref(F2), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                  None, 1, ctypes.byref(F2), 0, ctypes.byref(nn),
+                                  ctypes.c_void_p(256), 1 << 30, None) == N.TS_ERR_INVALID_ARG
+    assert lib.msbfs_init_parents(10, 300, ctypes.c_void_p(256), ctypes.c_void_p(256), None) == N.TS_ERR_UNSUPPORTED
     assert N.status_string(N.TS_ERR_CAPACITY) == "TS_ERR_CAPACITY"
     assert lib.ts_version() >= 100

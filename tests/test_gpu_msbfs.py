@@ -52,3 +52,49 @@ def test_msbfs_full_size_sampled_sources():
     maxlev = int(lev.max())
     assert r.products == maxlev + 1
     assert r.frontier_nnz[-1] == 0 and sum(r.frontier_nnz) == int((lev >= 0).sum())
+
+
+@pytest.mark.parametrize("scale,ef,d", [(10, 8, 128), (9, 4, 40), (8, 2, 1), (10, 8, 200), (10, 6, 64),
+                                        (11, 16, 256)])
+def test_msbfs_parents_match_oracle(scale, ef, d):
+    # the BFS-tree variant, (sel2nd, min): parents are integers, bit-exact
+    A = synth.rmat(scale, ef, 70 + scale, symmetrize=True)
+    src = synth.sources(A, d, 71)
+    r = msbfs(DeviceCSR.from_host(A, with_values=False), torch.as_tensor(src), parents=True)
+    lev, par, prods, fnnz = oracle.msbfs_parents(A, src)
+    np.testing.assert_array_equal(r.levels.cpu().numpy(), lev)
+    np.testing.assert_array_equal(r.parents.cpu().numpy(), par)
+    assert r.products == prods
+
+
+def test_msbfs_parents_directed_and_hubs():
+    # directed graph (pull over A's rows) with a hub row taken by a whole block
+    A = synth.rmat(11, 24, 72)
+    src = synth.sources(A, 96, 73)
+    r = msbfs(DeviceCSR.from_host(A, with_values=False), torch.as_tensor(src), parents=True)
+    lev, par, prods, _ = oracle.msbfs_parents(A, src)
+    np.testing.assert_array_equal(r.levels.cpu().numpy(), lev)
+    np.testing.assert_array_equal(r.parents.cpu().numpy(), par)
+
+
+def test_msbfs_parents_full_size_sampled():
+    # full-size workload: for 4 sources every reached vertex's parent is its
+    # smallest neighbour one level closer (checked against a queue BFS)
+    A, src = synth.msbfs_graph()
+    r = msbfs(DeviceCSR.from_host(A, with_values=False), torch.as_tensor(src), parents=True)
+    lev = r.levels.cpu().numpy()
+    par = r.parents.cpu().numpy()
+    rp, col = A.rowptr, A.col
+    for s in (0, 37, 90, 127):
+        ref = oracle.bfs_levels(A, int(src[s]))
+        np.testing.assert_array_equal(lev[:, s], ref)
+        reached = np.nonzero(ref > 0)[0]
+        p = par[reached, s]
+        assert np.all(ref[p] == ref[reached] - 1)
+        # p is a neighbour, and no smaller neighbour is one level closer
+        for v, pv in zip(reached[::997], p[::997]):
+            nb = col[rp[v]:rp[v + 1]]
+            closer = nb[ref[nb] == ref[v] - 1]
+            assert pv == closer.min()
+        assert par[int(src[s]), s] == int(src[s])
+        assert np.all(par[ref < 0, s] == -1)
