@@ -63,6 +63,9 @@ def _L():
                 "oracle_backward_dA_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
                 "oracle_backward_dB_rows": (ci, [i64, p, p, p, p, p, p, p, p, p, i64, p, p]),
                 "oracle_bfs_levels": (i64, [i64, p, p, ctypes.c_int32, p]),
+                "oracle_f2v_topk": (ci, [i64, i64, i64, p, p, p]),
+                "oracle_f2v_step": (ci, [i64, p, p, i64, i64, p, p, i64, i64, p, i64, ctypes.c_double,
+                                         p, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -153,6 +156,35 @@ def msbfs_parents(A, sources: np.ndarray, maxlev: int = 4096):
     if prods < 0:
         raise RuntimeError(f"oracle_msbfs_parents failed ({prods})")
     return levels, parents, int(prods), fnnz[: prods + 1].copy()
+
+
+def f2v_step(A, Z, r0: int, b: int, neg: np.ndarray, s: int, lr: float, k: int):
+    """Sparse Force2Vec step on rows [r0, r0+b) (paper Sec. IV, sparse
+    embedding; readings in oracle.c).  Z: CSR with exactly k entries per row.
+    Returns (U[b, d] float64, Ubound[b, d], Ncol[b, k], Nval[b, k])."""
+    d = Z.ncols
+    U = np.empty((max(b, 1), d), dtype=np.float64)
+    Ub = np.empty_like(U)
+    Ncol = np.empty((max(b, 1), k), dtype=np.int32)
+    Nval = np.empty((max(b, 1), k), dtype=np.float64)
+    st = _L().oracle_f2v_step(A.nrows, _p(_i64(A.rowptr)), _p(_i32(A.col)), d, k, _p(_i32(Z.col)),
+                              _p(_f64(Z.val)), r0, b, _p(_i32(neg)), s, float(lr), _p(U), _p(Ub),
+                              _p(Ncol), _p(Nval))
+    if st != 0:
+        raise RuntimeError("oracle_f2v_step failed")
+    return U[:b], Ub[:b], Ncol[:b], Nval[:b]
+
+
+def f2v_topk(U: np.ndarray, k: int):
+    """The k entries of largest magnitude of each row of U (ties: smaller
+    column), ascending columns: (Ncol[rows, k], Nval[rows, k])."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rows, d = U.shape
+    Ncol = np.empty((max(rows, 1), k), dtype=np.int32)
+    Nval = np.empty((max(rows, 1), k), dtype=np.float64)
+    if _L().oracle_f2v_topk(rows, d, k, _p(U), _p(Ncol), _p(Nval)) != 0:
+        raise MemoryError("oracle_f2v_topk")
+    return Ncol[:rows], Nval[:rows]
 
 
 def bfs_levels(A, source: int) -> np.ndarray:

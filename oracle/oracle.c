@@ -415,3 +415,87 @@ int64_t oracle_bfs_levels(int64_t n, const int64_t* Ap, const int32_t* Ai, int32
     free(queue);
     return maxlev;
 }
+
+/*
+ * Sparse Force2Vec step (paper Sec. IV, "Distributed sparse embedding"), for
+ * the minibatch of rows [r0, r0 + b) of the embedding Z (n x d, exactly k
+ * stored entries per row, Zp[i] = k*i).  Readings (the paper names the
+ * parts, not the formulas): row i's neighbours in A carry +1 and its s
+ * negative samples neg[(i-r0)*s + t] carry -1 (each occurrence one term);
+ * x_ij = z_i . z_j; an attractive term weighs z_j by (1 - sigmoid(x_ij)), a
+ * repulsive one by -sigmoid(x_ij) (the gradient of the usual
+ * negative-sampling objective with respect to z_i); G_i = sum of the
+ * weighted z_j (the TS-SpGEMM W * Z); U_i = z_i + lr * G_i; the new row keeps
+ * the k entries of U_i of largest magnitude (ties: smaller column first).
+ * All rows of the batch use the old Z (synchronous SGD).
+ *
+ * Outputs: U[b*d] (dense, double), Ub[b*d] (per entry: |z_i(c)|*2^-24 +
+ * lr * sum over terms of (|w| + S_ij/4 + 1) * |z_j(c)| with S_ij = sum of
+ * |z_i||z_j| over shared columns -- the scale of the FP32 error of U(c)),
+ * and the sparsified rows Ncol[b*k] (ascending) / Nval[b*k].
+ * Returns 0 or -1 on allocation failure.
+ */
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+int oracle_f2v_topk(int64_t rows, int64_t d, int64_t k, const double* U, int32_t* Ncol, double* Nval) {
+    /* the k columns of largest |U|, ties to the smaller column; emitted ascending */
+    unsigned char* keep = (unsigned char*)malloc((size_t)(d > 0 ? d : 1));
+    if (!keep) return -1;
+    for (int64_t r = 0; r < rows; ++r) {
+        const double* u = U + r * d;
+        for (int64_t c = 0; c < d; ++c) {
+            int64_t rank = 0; /* entries ranked before c */
+            for (int64_t e = 0; e < d; ++e) {
+                const double a = fabs(u[e]), x = fabs(u[c]);
+                if (a > x || (a == x && e < c)) ++rank;
+            }
+            keep[c] = rank < k;
+        }
+        int64_t o = 0;
+        for (int64_t c = 0; c < d; ++c)
+            if (keep[c]) {
+                Ncol[r * k + o] = (int32_t)c;
+                Nval[r * k + o] = u[c];
+                ++o;
+            }
+    }
+    free(keep);
+    return 0;
+}
+
+int oracle_f2v_step(int64_t n, const int64_t* Ap, const int32_t* Ai, int64_t d, int64_t k, const int32_t* Zcol,
+                    const double* Zval, int64_t r0, int64_t b, const int32_t* neg, int64_t s, double lr,
+                    double* U, double* Ub, int32_t* Ncol, double* Nval) {
+    double* zi = (double*)calloc((size_t)(d > 0 ? d : 1), sizeof(double));
+    if (!zi) return -1;
+    for (int64_t r = 0; r < b; ++r) {
+        const int64_t i = r0 + r;
+        for (int64_t c = 0; c < d; ++c) zi[c] = 0.0;
+        for (int64_t t = 0; t < k; ++t) zi[Zcol[i * k + t]] = Zval[i * k + t];
+        double* u = U + r * d;
+        double* ub = Ub + r * d;
+        for (int64_t c = 0; c < d; ++c) {
+            u[c] = zi[c];
+            ub[c] = fabs(zi[c]) * 5.9604644775390625e-8;
+        }
+        const int64_t nA = Ap[i + 1] - Ap[i];
+        for (int64_t t = 0; t < nA + s; ++t) {
+            const int attract = t < nA;
+            const int64_t j = attract ? Ai[Ap[i] + t] : neg[r * s + (t - nA)];
+            double x = 0.0, S = 0.0;
+            for (int64_t q = 0; q < k; ++q) {
+                const int32_t c = Zcol[j * k + q];
+                x += zi[c] * Zval[j * k + q];
+                S += fabs(zi[c] * Zval[j * k + q]);
+            }
+            const double w = attract ? 1.0 - sigmoid(x) : -sigmoid(x);
+            for (int64_t q = 0; q < k; ++q) {
+                const int32_t c = Zcol[j * k + q];
+                u[c] += lr * w * Zval[j * k + q];
+                ub[c] += lr * (fabs(w) + S / 4.0 + 1.0) * fabs(Zval[j * k + q]);
+            }
+        }
+    }
+    free(zi);
+    return oracle_f2v_topk(b, d, k, U, Ncol, Nval);
+}

@@ -232,3 +232,26 @@ def batched_instances(count: int = 64, seed: int = BASE_SEED + 4, log2n_lo: floa
         B.val = uniform(B.nnz, s + 303)
         out.append((A, B))
     return out
+
+
+def sparse_embedding(n: int, d: int, k: int, seed: int, scale: float = 0.1) -> CSR:
+    """n x d embedding with exactly k distinct uniform columns per row and
+    values scale * N(0,1) (a sparse Force2Vec starting point)."""
+    Z = er(n, k, seed, ncols=d)
+    Z.val = (normal(Z.nnz, seed + 1) * np.float32(scale)).astype(np.float32)
+    return Z
+
+
+def negatives(b: int, s: int, n: int, seed: int) -> np.ndarray:
+    """b*s negative-sample vertex ids, uniform on [0, n) (24-bit draws)."""
+    u = uniform(b * s, seed).astype(np.float64)
+    return np.minimum((u * n).astype(np.int64), n - 1).astype(np.int32)
+
+
+def force2vec_inputs(scale: int = 20, edge_factor: int = 16, d: int = 128, k: int = 26,
+                     seed: int = BASE_SEED + 6):
+    """Symmetrised pattern-only R-MAT graph and its sparse starting embedding
+    (d = 128, 80 % sparse: k = 26 entries per row)."""
+    A = rmat(scale, edge_factor, seed, symmetrize=True)
+    Z = sparse_embedding(A.nrows, d, k, seed + 11)
+    return A, Z

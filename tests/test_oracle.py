@@ -321,3 +321,100 @@ def test_backward_sampled_rows_match_full():
     sB, _ = oracle.backward_dB_rows(A, B, Cp, Ci, dC, krows)
     ref = np.concatenate([dB[B.rowptr[k]:B.rowptr[k + 1]] for k in krows])
     np.testing.assert_allclose(sB, ref, rtol=1e-12, atol=1e-12)
+
+
+# --- sparse Force2Vec step (paper Sec. IV, sparse embedding) --------------
+
+def _dense_rows(Z):
+    D = np.zeros((Z.nrows, Z.ncols))
+    for i in range(Z.nrows):
+        D[i, Z.col[Z.rowptr[i]:Z.rowptr[i + 1]]] = Z.val[Z.rowptr[i]:Z.rowptr[i + 1]]
+    return D
+
+
+def test_f2v_topk_golden():
+    g = json.load(open(os.path.join(GOLDEN, "f2v_topk_small.json")))
+    U = np.array(g["U"], dtype=np.float64)
+    cols, vals = oracle.f2v_topk(U, g["k"])
+    np.testing.assert_array_equal(cols, np.array(g["cols"]))
+    np.testing.assert_array_equal(vals, np.array(g["vals"], dtype=np.float64))
+
+
+def test_f2v_topk_extremes():
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=(5, 16))
+    cols, vals = oracle.f2v_topk(U, 16)          # k = d keeps the whole row
+    np.testing.assert_array_equal(cols, np.tile(np.arange(16), (5, 1)))
+    np.testing.assert_array_equal(vals, U)
+    cols, _ = oracle.f2v_topk(U, 1)              # k = 1: the argmax of |U|
+    np.testing.assert_array_equal(cols[:, 0], np.argmax(np.abs(U), axis=1))
+
+
+def test_f2v_zero_rate_is_identity():
+    A = synth.rmat(8, 8, 41, symmetrize=True)
+    Z = synth.sparse_embedding(A.nrows, 32, 6, 42)
+    neg = synth.negatives(50, 4, A.nrows, 43)
+    U, Ub, ncol, nval = oracle.f2v_step(A, Z, 10, 50, neg, 4, 0.0, 6)
+    D = _dense_rows(Z)
+    np.testing.assert_array_equal(U, D[10:60])
+    # the k stored entries are nonzero, so they are exactly the k largest in magnitude
+    np.testing.assert_array_equal(ncol, Z.col.reshape(-1, 6)[10:60])
+    np.testing.assert_array_equal(nval, Z.val.reshape(-1, 6)[10:60].astype(np.float64))
+
+
+def test_f2v_gradient_is_derivative_of_the_objective():
+    # G_i = (U_i - z_i) / lr must be the gradient, with respect to z_i, of
+    # L_i(z) = sum over neighbours j of log sigmoid(z . z_j)
+    #        + sum over negatives q of log sigmoid(-z . z_q)
+    # (the other endpoints held at their old values); central differences
+    A = synth.rmat(8, 6, 44, symmetrize=True)
+    n, d, k, s, lr = A.nrows, 24, 5, 3, 0.5
+    Z = synth.sparse_embedding(n, d, k, 45, scale=0.7)
+    r0, b = 20, 12
+    neg = synth.negatives(b, s, n, 46)
+    U, _, _, _ = oracle.f2v_step(A, Z, r0, b, neg, s, lr, k)
+    D = _dense_rows(Z)
+    logsig = lambda x: -np.log1p(np.exp(-x))
+    for r in range(b):
+        i = r0 + r
+        nb = A.col[A.rowptr[i]:A.rowptr[i + 1]]
+        ng = neg[r * s:(r + 1) * s]
+
+        def L(z):
+            return sum(logsig(z @ D[j]) for j in nb) + sum(logsig(-(z @ D[q])) for q in ng)
+
+        G = (U[r] - D[i]) / lr
+        h = 1e-6
+        for c in range(d):
+            e = np.zeros(d)
+            e[c] = h
+            fd = (L(D[i] + e) - L(D[i] - e)) / (2 * h)
+            assert abs(G[c] - fd) <= 1e-6 * (1 + abs(fd)), (r, c, G[c], fd)
+
+
+def test_f2v_duplicate_negatives_and_self_terms():
+    # a negative equal to a neighbour, or repeated, or the row itself, is one
+    # more term of its own: compare with the per-term sum written with numpy
+    A = synth.rmat(7, 4, 47, symmetrize=True)
+    n, d, k, s, lr = A.nrows, 16, 4, 4, 0.3
+    Z = synth.sparse_embedding(n, d, k, 48, scale=0.5)
+    D = _dense_rows(Z)
+    r0, b = 5, 6
+    neg = synth.negatives(b, s, n, 49)
+    for r in range(b):
+        i = r0 + r
+        nb = A.col[A.rowptr[i]:A.rowptr[i + 1]]
+        neg[r * s] = i
+        if nb.size:
+            neg[r * s + 1] = nb[0]
+        neg[r * s + 2] = neg[r * s + 3]
+    U, _, _, _ = oracle.f2v_step(A, Z, r0, b, neg, s, lr, k)
+    sig = lambda x: 1.0 / (1.0 + np.exp(-x))
+    for r in range(b):
+        i = r0 + r
+        g = np.zeros(d)
+        for j in A.col[A.rowptr[i]:A.rowptr[i + 1]]:
+            g += (1 - sig(D[i] @ D[j])) * D[j]
+        for q in neg[r * s:(r + 1) * s]:
+            g -= sig(D[i] @ D[q]) * D[q]
+        np.testing.assert_allclose(U[r], D[i] + lr * g, rtol=1e-12, atol=1e-13)
