@@ -282,6 +282,32 @@ TS_API ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint32_t
                      int64_t F_next_capacity, int64_t* nnz_next_host, void* ws, size_t ws_bytes,
                      void* stream);
 /*
+ * Sparse Force2Vec minibatch step (paper Sec. IV, "Distributed sparse
+ * embedding": attractive and repulsive forces through TS-SpGEMM, SGD, then
+ * sparsification keeping the largest entries).  For the rows [r0, r0 + b) of
+ * the sparse embedding Z (n x d, exactly k entries per row, Z.rowptr[i] =
+ * k*i, values float32), with A (n x n, pattern; values ignored):
+ *   W(r, j) = npos - (npos + nneg) * sigmoid(z_i . z_j)   (i = r0 + r),
+ *     npos = [A(i, j) stored], nneg = occurrences of j in the row's s
+ *     negative samples neg[r*s .. r*s+s) (device int32, vertex ids);
+ *   G = W * Z (this library's plus-times TS-SpGEMM);
+ *   U_i = z_i + lr * G_r;  new row i = the k entries of U_i of largest
+ *     magnitude (ties: smaller column), ascending columns.
+ * Every row of the batch is computed from the old Z; the new rows then
+ * overwrite Z's batch rows in place (Z.col and Z.val are written).  U_out:
+ * optional device float32[b*d] receiving the dense U before sparsification
+ * (NULL: not written).  ws: f2v_workspace_size bytes, 256-byte aligned.
+ * Synchronises `stream`.  Errors: TS_ERR_INVALID_ARG (shapes, batch range,
+ * NULL), TS_ERR_UNSUPPORTED (d > 4096, k > d, s > 32, n >= 2^31),
+ * TS_ERR_WORKSPACE_TOO_SMALL, TS_ERR_BAD_CSR (device checks: columns out of
+ * range, Z not k entries per row), TS_ERR_CUDA.
+ */
+TS_API ts_status f2v_workspace_size(int64_t n, int64_t d, int64_t nnz_A, int64_t b, int32_t s, int32_t k,
+                                    size_t* bytes);
+TS_API ts_status f2v_step(const ts_csr_desc* A, const ts_csr_desc* Z, int64_t r0, int64_t b, const int32_t* neg,
+                          int32_t s, float lr, int32_t k, float* U_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * BFS-tree variant of the level step (paper Sec. IV: Alg. 3 with the
  * (sel2nd, min) semiring, used when the BFS tree is to be reconstructed): the
  * same step as msbfs_step, and in addition parents[v*d + s] = the smallest

@@ -429,9 +429,11 @@ int64_t oracle_bfs_levels(int64_t n, const int64_t* Ap, const int32_t* Ai, int32
  * the k entries of U_i of largest magnitude (ties: smaller column first).
  * All rows of the batch use the old Z (synchronous SGD).
  *
- * Outputs: U[b*d] (dense, double), Ub[b*d] (per entry: |z_i(c)|*2^-24 +
+ * Outputs: U[b*d] (dense, double), Ub[b*d] (per entry: |z_i(c)| +
  * lr * sum over terms of (|w| + S_ij/4 + 1) * |z_j(c)| with S_ij = sum of
- * |z_i||z_j| over shared columns -- the scale of the FP32 error of U(c)),
+ * |z_i||z_j| over shared columns -- the sum of the magnitudes that U(c)
+ * adds up, with the weights' sensitivity to their dot products (the
+ * sigmoid's slope is at most 1/4) and to their own rounding (the 1)),
  * and the sparsified rows Ncol[b*k] (ascending) / Nval[b*k].
  * Returns 0 or -1 on allocation failure.
  */
@@ -476,7 +478,7 @@ int oracle_f2v_step(int64_t n, const int64_t* Ap, const int32_t* Ai, int64_t d, 
         double* ub = Ub + r * d;
         for (int64_t c = 0; c < d; ++c) {
             u[c] = zi[c];
-            ub[c] = fabs(zi[c]) * 5.9604644775390625e-8;
+            ub[c] = fabs(zi[c]);
         }
         const int64_t nA = Ap[i + 1] - Ap[i];
         for (int64_t t = 0; t < nA + s; ++t) {

@@ -94,6 +94,9 @@ _SIGS = {
     "msbfs_step_parents": (c_int32, [P(CsrDesc), P(CsrDesc), c_void_p, c_void_p, c_void_p, c_int32, P(CsrDesc),
                                      c_int64, P(c_int64), c_void_p, c_size_t, c_void_p]),
     "msbfs_init_parents": (c_int32, [c_int64, c_int64, c_void_p, c_void_p, c_void_p]),
+    "f2v_workspace_size": (c_int32, [c_int64, c_int64, c_int64, c_int64, c_int32, c_int32, P(c_size_t)]),
+    "f2v_step": (c_int32, [P(CsrDesc), P(CsrDesc), c_int64, c_int64, c_void_p, c_int32, ctypes.c_float, c_int32,
+                           c_void_p, c_void_p, c_size_t, c_void_p]),
     "ts_batched_plan_create": (c_int32, [c_int32, P(CsrDesc), P(CsrDesc), c_int32, P(Tuning),
                                          P(c_void_p)]),
     "ts_batched_plan_destroy": (c_int32, [c_void_p]),

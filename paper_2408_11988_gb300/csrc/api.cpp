@@ -682,6 +682,131 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     return s == TS_OK ? ok() : s;
 }
 
+
+// ---------------------------------------------------------------------------
+// sparse Force2Vec minibatch step (paper Sec. IV, sparse embedding)
+// ---------------------------------------------------------------------------
+struct F2vLayout {
+    Layout inner;  // schedule and SpGEMM regions for the b x n by n x d product
+    size_t inner_off = 0, Wp = 0, Wcol = 0, Wmult = 0, Wval = 0, Gp = 0, Gc = 0, Gv = 0, Sc = 0, Sv = 0, total = 0;
+    long long wcap = 0, gcap = 0;
+};
+
+static ts_tuning f2v_tuning(long long d, long long n, long long nnzZ) {
+    ts_tuning t{};
+    ts_tuning force{};
+    force.col_tile = (int32_t)round_up(d, 32);  // one tile: G's rows are at most d wide
+    resolve_tuning(d, force, t, n, nnzZ);
+    return t;
+}
+
+static F2vLayout f2v_layout(long long n, long long d, long long nnzA, long long b, long long s, long long k) {
+    F2vLayout F;
+    F.wcap = nnzA + b * s;
+    F.gcap = b * round_up(d, 32);
+    const ts_tuning t = f2v_tuning(d, n, n * k);
+    F.inner = plan_layout(n, d, t, F.wcap, n * k);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    F.inner_off = take(F.inner.total);
+    F.Wp = take(sizeof(long long) * (size_t)(b + 1));
+    F.Wcol = take(sizeof(int) * (size_t)F.wcap);
+    F.Wmult = take(sizeof(int) * (size_t)F.wcap);
+    F.Wval = take(sizeof(float) * (size_t)F.wcap);
+    F.Gp = take(sizeof(long long) * (size_t)(b + 1));
+    F.Gc = take(sizeof(int) * (size_t)F.gcap);
+    F.Gv = take(sizeof(float) * (size_t)F.gcap);
+    F.Sc = take(sizeof(int) * (size_t)(b * k));
+    F.Sv = take(sizeof(float) * (size_t)(b * k));
+    F.total = off;
+    return F;
+}
+
+extern "C" ts_status f2v_workspace_size(int64_t n, int64_t d, int64_t nnz_A, int64_t b, int32_t s, int32_t k,
+                                        size_t* bytes) {
+    if (!bytes || n < 0 || d < 1 || nnz_A < 0 || b < 0 || s < 0 || k < 1)
+        return fail(TS_ERR_INVALID_ARG, "f2v_workspace_size: bad argument");
+    if (d > 4096 || k > d || s > 32) return fail(TS_ERR_UNSUPPORTED, "f2v_workspace_size: need k <= d <= 4096, s <= 32");
+    *bytes = f2v_layout(n, d, nnz_A, b, s, k).total;
+    return ok();
+}
+
+extern "C" ts_status f2v_step(const ts_csr_desc* A, const ts_csr_desc* Z, int64_t r0, int64_t b,
+                              const int32_t* neg, int32_t s, float lr, int32_t k, float* U_out, void* ws,
+                              size_t ws_bytes, void* stream) {
+    const char* fn = "f2v_step";
+    ts_status st_;
+    if ((st_ = check_desc(A, "A", false)) != TS_OK) return st_;
+    if ((st_ = check_desc(Z, "Z", true)) != TS_OK) return st_;
+    const long long n = A->nrows, d = Z->ncols;
+    if (A->ncols != n || Z->nrows != n) return fail(TS_ERR_INVALID_ARG, "%s: A must be n x n and Z n x d", fn);
+    if (n > INT32_MAX) return fail(TS_ERR_UNSUPPORTED, "%s: n >= 2^31", fn);
+    if (d > 4096 || k < 1 || k > d || s < 0 || s > 32)
+        return fail(TS_ERR_UNSUPPORTED, "%s: need 1 <= k <= d <= 4096 and 0 <= s <= 32", fn);
+    if (Z->nnz != n * (long long)k) return fail(TS_ERR_INVALID_ARG, "%s: Z must hold exactly k entries per row", fn);
+    if (r0 < 0 || b < 0 || r0 + b > n) return fail(TS_ERR_INVALID_ARG, "%s: batch rows outside Z", fn);
+    if (s > 0 && b > 0 && !neg) return fail(TS_ERR_INVALID_ARG, "%s: negatives are NULL", fn);
+    const F2vLayout F = f2v_layout(n, d, A->nnz, b, s, k);
+    if (!ws || ws_bytes < F.total)
+        return fail(TS_ERR_WORKSPACE_TOO_SMALL, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, F.total);
+    if (((uintptr_t)ws) & 255) return fail(TS_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
+    if (b == 0) return ok();
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    const Sched sc = carve(w + F.inner_off, F.inner);
+    long long* Wp = (long long*)(w + F.Wp);
+    int* Wcol = (int*)(w + F.Wcol);
+    int* Wmult = (int*)(w + F.Wmult);
+    float* Wval = (float*)(w + F.Wval);
+    long long* Gp = (long long*)(w + F.Gp);
+    int* Gc = (int*)(w + F.Gc);
+    float* Gv = (float*)(w + F.Gv);
+    const ts_tuning t = f2v_tuning(d, n, n * k);
+    const LaunchCfg cfg = cfg_of(t);
+    const DevCsr dA = dev(A), dZ = dev(Z);
+    // 1. W's pattern (neighbours and negatives merged) and the Z layout check
+    TS_CUDA(cudaMemsetAsync(sc.hdr, 0, sizeof(WsHeader), st), fn);
+    TS_CUDA(launch_f2v_check(dZ, k, sc.hdr, st), fn);
+    TS_CUDA(launch_f2v_pattern(dA, r0, b, neg, s, Wp, sc.partial, sc.hdr, st), fn);
+    TS_CUDA(launch_f2v_fill(dA, r0, b, neg, s, Wp, Wcol, Wmult, sc.hdr, st), fn);
+    // 2. weights on W's pattern
+    TS_CUDA(launch_f2v_weights(dZ, k, r0, b, Wp, Wcol, Wmult, Wval, cfg.sms, sc.hdr, st), fn);
+    // errors so far live in the header the schedule is about to reset
+    unsigned long long err0 = 0;
+    TS_CUDA(cudaMemcpyAsync(&err0, &sc.hdr->err, sizeof err0, cudaMemcpyDeviceToHost, st), fn);
+    // 3. G = W * Z (b x n by n x d), the library's TS-SpGEMM passes
+    DevCsr dW;
+    dW.nrows = b;
+    dW.ncols = n;
+    dW.nnz = F.wcap;
+    dW.rowptr = Wp;
+    dW.col = Wcol;
+    dW.val = Wval;
+    TS_CUDA(launch_row_schedule(dW, dZ, sc, Gp, st), fn);
+    LaunchCfg scfg = cfg;
+    scfg.group = t.sym_group;
+    TS_CUDA(launch_symbolic(dW, dZ, d, sc, scfg, Gp, st), fn);
+    int2* bpk = (int2*)((char*)(w + F.inner_off) + F.inner.bpk);
+    TS_CUDA(launch_pack_b(dZ, bpk, st), fn);
+    TS_CUDA(launch_numeric_dense(dW, dZ, d, F.inner.W, F.inner.T, nullptr, true, bpk, t.group, sc, cfg, Gp, Gc, Gv,
+                                 F.gcap, st),
+            fn);
+    // 4-5. update, top-k, commit into Z's batch rows
+    TS_CUDA(launch_f2v_update(dZ, k, r0, b, Gp, Gc, Gv, lr, U_out, (int*)(w + F.Sc), (float*)(w + F.Sv), cfg.sms,
+                              sc.hdr, st),
+            fn);
+    unsigned long long err1 = 0;
+    TS_CUDA(cudaMemcpyAsync(&err1, &sc.hdr->err, sizeof err1, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (err0 | err1)
+        return fail(TS_ERR_BAD_CSR, "%s: device checks failed (flags 0x%llx)", fn, (unsigned long long)(err0 | err1));
+    return ok();
+}
+
 // ---------------------------------------------------------------------------
 // validation
 // ---------------------------------------------------------------------------

@@ -162,6 +162,21 @@ cudaError_t launch_batch_gather_dc(const InstDesc* inst, int count, long long ma
 cudaError_t launch_batch_scatter_grads(const InstDesc* inst, int count, long long max_work, const float* dA,
                                        const float* dB, cudaStream_t st);
 
+// Sparse Force2Vec step (force2vec.cu): W's pattern (count + scan, fill),
+// the Z layout check, the weights on W's pattern, and update + top-k +
+// commit into Z's batch rows.
+cudaError_t launch_f2v_pattern(const DevCsr& A, long long r0, long long b, const int* neg, int s, long long* Wp,
+                               long long* partial, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_f2v_fill(const DevCsr& A, long long r0, long long b, const int* neg, int s, const long long* Wp,
+                            int* Wcol, int* Wmult, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_f2v_check(const DevCsr& Z, int k, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_f2v_weights(const DevCsr& Z, int k, long long r0, long long b, const long long* Wp,
+                               const int* Wcol, const int* Wmult, float* Wval, int sms, WsHeader* hdr,
+                               cudaStream_t st);
+cudaError_t launch_f2v_update(const DevCsr& Z, int k, long long r0, long long b, const long long* Gp, const int* Gc,
+                              const float* Gv, float lr, float* U_out, int* Sc, float* Sv, int sms, WsHeader* hdr,
+                              cudaStream_t st);
+
 // CSR validation; writes the first bad row (or -1) into *bad (device).
 cudaError_t launch_validate(const DevCsr& M, long long* bad, cudaStream_t st);
 
