@@ -50,6 +50,9 @@ WORKLOADS = {
                    "as one CUDA-graph replay", None, None, True),
     "msbfs-s20": ("multi-source BFS, R-MAT scale 20, edge factor 16, symmetrised, 128 sources, "
                   "(or, select2nd) iterated to an empty frontier", None, None, False),
+    "force2vec-s20": ("sparse Force2Vec epoch: R-MAT scale 20, edge factor 16, symmetrised; embedding "
+                      "1048576x128 with 26 entries per row (80% sparse), 5 negatives per row, lr 0.02, "
+                      "minibatches of 65536 rows", None, None, False),
     "msbfs-parents-s20": ("multi-source BFS with BFS-tree parents, R-MAT scale 20, edge factor 16, "
                           "symmetrised, 128 sources, (sel2nd, min) iterated to an empty frontier",
                           None, None, False),
@@ -226,6 +229,8 @@ def main():
         return run_batched(args, ws, rank, local, desc)
     if args.workload in ("msbfs-s20", "msbfs-parents-s20"):
         return run_msbfs(args, ws, rank, local, desc)
+    if args.workload == "force2vec-s20":
+        return run_force2vec(args, ws, rank, local, desc)
 
     import torch
     torch.cuda.set_device(local)
@@ -574,10 +579,114 @@ def run_msbfs(args, ws, rank, local, desc):
         dist.destroy_process_group()
 
 
+def run_force2vec(args, ws, rank, local, desc):
+    """One step = one epoch of the sparse Force2Vec training (every row once,
+    minibatches of 65536 consecutive rows).  products = multiplications of
+    the force products W * Z (per row: (degree + negatives) * k)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2408_11988_gb300 import DeviceCSR
+    from paper_2408_11988_gb300 import _native as N
+    from paper_2408_11988_gb300.force2vec import Force2Vec
+    dist = _dist_setup(ws, local)
+    k, s, lr, batch = 26, 5, 0.02, 65536
+    A, Z = synth.force2vec_inputs(seed=synth.BASE_SEED + 6 + 1000 * rank)
+    n = A.nrows
+    Ad, Zd = DeviceCSR.from_host(A, with_values=False), DeviceCSR.from_host(Z)
+    neg = torch.as_tensor(synth.negatives(n, s, n, synth.BASE_SEED + 7 + 1000 * rank), device="cuda")
+    f = Force2Vec(Ad, Zd, k, negatives=s, lr=lr, batch=batch)
+    products = int((np.diff(A.rowptr) + s).sum()) * k
+    for _ in range(args.warmup):
+        f.epoch(neg)
+    torch.cuda.synchronize()
+    l0 = N.lib().ts_kernel_launches()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            mb = f.epoch(neg)
+        b.record()
+        torch.cuda.synchronize()
+    launches = N.lib().ts_kernel_launches() - l0
+    ms = _max_over_ranks(dist, a.elapsed_time(b) / args.steps)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "sparse Force2Vec embedding rows/s", "value": round(n * ws / (ms * 1e-3), 1),
+            "unit": "rows/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "force2vec-s20", "description": desc, "n": n, "nnz_A": A.nnz, "d": Z.ncols,
+                       "k": k, "negatives": s, "lr": lr, "batch": batch, "minibatches": mb,
+                       "products": products, "parallelism": f"replicas x{ws}"},
+            "force_product_gflops": round(2.0 * products * ws / (ms * 1e-3) / 1e9, 3),
+            "ms_per_minibatch": round(ms / mb, 4),
+            "roofline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "cpu_baseline": None}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _reference_other(args, ws, desc):
+    """Reference arm (the FP64 oracle, one host core) for the BFS, Force2Vec
+    and batched workloads, on bounded samples: 4 of the 128 BFS sources, a
+    4096-row Force2Vec minibatch, the largest batched instance."""
+    import oracle
+    import synth
+    import numpy as np
+    vals, sample, unit, metric = [], "", "", ""
+    for it in range(args.warmup + args.steps):
+        if args.workload in ("msbfs-s20", "msbfs-parents-s20"):
+            A, src = synth.msbfs_graph()
+            src = src[:4]
+            t0 = time.perf_counter()
+            if args.workload == "msbfs-s20":
+                lev, _, _ = oracle.msbfs(A, src)
+            else:
+                lev, _, _, _ = oracle.msbfs_parents(A, src)
+            t = time.perf_counter() - t0
+            deg = np.diff(A.rowptr)
+            v = float((deg[:, None] * (lev >= 0)).sum()) / t
+            unit = "products/s"
+            metric = ("multi-source BFS (sel2nd, min) products/s" if args.workload == "msbfs-parents-s20"
+                      else "multi-source BFS boolean products/s")
+            sample = f"4 of the 128 sources of the R-MAT scale-20 graph, {t:.1f} s single-threaded"
+        elif args.workload == "force2vec-s20":
+            A, Z = synth.force2vec_inputs()
+            b, s = 4096, 5
+            neg = synth.negatives(b, s, A.nrows, synth.BASE_SEED + 7)
+            t0 = time.perf_counter()
+            oracle.f2v_step(A, Z, 0, b, neg, s, 0.02, 26)
+            t = time.perf_counter() - t0
+            v, unit, metric = b / t, "rows/s", "sparse Force2Vec embedding rows/s"
+            sample = f"one minibatch of {b} rows of the scale-20 graph, {t:.1f} s single-threaded"
+        else:  # batched-64: the largest instance, forward + backward
+            inst = synth.batched_instances()
+            A, B = max(inst, key=lambda ab: ab[0].nnz)
+            r = cpu_baseline(A, B, True, target_s=6.0)
+            v, unit, metric = r["value"], "GFLOP/s", "TS-SpGEMM GFLOP/s (batched forward + backward, plus-times)"
+            sample = "largest instance: " + r["sample"]
+        if it >= args.warmup:
+            vals.append(v)
+    v = statistics.mean(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": round(v, 4), "unit": unit, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc},
+        "cpu_baseline": {"value": round(v, 4), "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
 def run_reference(args, ws, rank, desc, want_bwd):
     """The oracle (FP64, one host core) timed on a bounded sample per step."""
     if rank != 0:
         return
+    if args.workload in ("msbfs-s20", "msbfs-parents-s20", "force2vec-s20", "batched-64"):
+        return _reference_other(args, ws, desc)
     A, B = make_inputs(args.workload)
     import oracle  # noqa: F401
     for _ in range(args.warmup):

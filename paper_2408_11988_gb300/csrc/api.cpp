@@ -688,7 +688,8 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
 // ---------------------------------------------------------------------------
 struct F2vLayout {
     Layout inner;  // schedule and SpGEMM regions for the b x n by n x d product
-    size_t inner_off = 0, Wp = 0, Wcol = 0, Wmult = 0, Wval = 0, Gp = 0, Gc = 0, Gv = 0, Sc = 0, Sv = 0, total = 0;
+    size_t inner_off = 0, Wp = 0, Wcol = 0, Wmult = 0, Wrow = 0, Wval = 0, newmask = 0, Gp = 0, Gc = 0, Gv = 0;
+    size_t Sc = 0, Sv = 0, total = 0;
     long long wcap = 0, gcap = 0;
 };
 
@@ -716,7 +717,9 @@ static F2vLayout f2v_layout(long long n, long long d, long long nnzA, long long 
     F.Wp = take(sizeof(long long) * (size_t)(b + 1));
     F.Wcol = take(sizeof(int) * (size_t)F.wcap);
     F.Wmult = take(sizeof(int) * (size_t)F.wcap);
+    F.Wrow = take(sizeof(int) * (size_t)F.wcap);
     F.Wval = take(sizeof(float) * (size_t)F.wcap);
+    F.newmask = take(sizeof(unsigned) * (size_t)(b > 0 ? b : 1));
     F.Gp = take(sizeof(long long) * (size_t)(b + 1));
     F.Gc = take(sizeof(int) * (size_t)F.gcap);
     F.Gv = take(sizeof(float) * (size_t)F.gcap);
@@ -761,7 +764,9 @@ extern "C" ts_status f2v_step(const ts_csr_desc* A, const ts_csr_desc* Z, int64_
     long long* Wp = (long long*)(w + F.Wp);
     int* Wcol = (int*)(w + F.Wcol);
     int* Wmult = (int*)(w + F.Wmult);
+    int* Wrow = (int*)(w + F.Wrow);
     float* Wval = (float*)(w + F.Wval);
+    unsigned* newmask = (unsigned*)(w + F.newmask);
     long long* Gp = (long long*)(w + F.Gp);
     int* Gc = (int*)(w + F.Gc);
     float* Gv = (float*)(w + F.Gv);
@@ -771,10 +776,10 @@ extern "C" ts_status f2v_step(const ts_csr_desc* A, const ts_csr_desc* Z, int64_
     // 1. W's pattern (neighbours and negatives merged) and the Z layout check
     TS_CUDA(cudaMemsetAsync(sc.hdr, 0, sizeof(WsHeader), st), fn);
     TS_CUDA(launch_f2v_check(dZ, k, sc.hdr, st), fn);
-    TS_CUDA(launch_f2v_pattern(dA, r0, b, neg, s, Wp, sc.partial, sc.hdr, st), fn);
-    TS_CUDA(launch_f2v_fill(dA, r0, b, neg, s, Wp, Wcol, Wmult, sc.hdr, st), fn);
+    TS_CUDA(launch_f2v_pattern(dA, r0, b, neg, s, Wp, newmask, sc.partial, sc.hdr, st), fn);
+    TS_CUDA(launch_f2v_fill(dA, r0, b, neg, s, Wp, newmask, Wcol, Wmult, Wrow, st), fn);
     // 2. weights on W's pattern
-    TS_CUDA(launch_f2v_weights(dZ, k, r0, b, Wp, Wcol, Wmult, Wval, cfg.sms, sc.hdr, st), fn);
+    TS_CUDA(launch_f2v_weights(dZ, k, r0, b, Wp, Wcol, Wmult, Wrow, Wval, st), fn);
     // errors so far live in the header the schedule is about to reset
     unsigned long long err0 = 0;
     TS_CUDA(cudaMemcpyAsync(&err0, &sc.hdr->err, sizeof err0, cudaMemcpyDeviceToHost, st), fn);

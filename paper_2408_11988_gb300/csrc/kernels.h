@@ -166,13 +166,12 @@ cudaError_t launch_batch_scatter_grads(const InstDesc* inst, int count, long lon
 // the Z layout check, the weights on W's pattern, and update + top-k +
 // commit into Z's batch rows.
 cudaError_t launch_f2v_pattern(const DevCsr& A, long long r0, long long b, const int* neg, int s, long long* Wp,
-                               long long* partial, WsHeader* hdr, cudaStream_t st);
+                               unsigned* newmask, long long* partial, WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_f2v_fill(const DevCsr& A, long long r0, long long b, const int* neg, int s, const long long* Wp,
-                            int* Wcol, int* Wmult, WsHeader* hdr, cudaStream_t st);
+                            const unsigned* newmask, int* Wcol, int* Wmult, int* Wrow, cudaStream_t st);
 cudaError_t launch_f2v_check(const DevCsr& Z, int k, WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_f2v_weights(const DevCsr& Z, int k, long long r0, long long b, const long long* Wp,
-                               const int* Wcol, const int* Wmult, float* Wval, int sms, WsHeader* hdr,
-                               cudaStream_t st);
+                               const int* Wcol, const int* Wmult, const int* Wrow, float* Wval, cudaStream_t st);
 cudaError_t launch_f2v_update(const DevCsr& Z, int k, long long r0, long long b, const long long* Gp, const int* Gc,
                               const float* Gv, float lr, float* U_out, int* Sc, float* Sv, int sms, WsHeader* hdr,
                               cudaStream_t st);
