@@ -79,5 +79,14 @@ def test_host_side_errors(lib):
                                   None, 1, ctypes.byref(F2), 0, ctypes.byref(nn),
                                   ctypes.c_void_p(256), 1 << 30, None) == N.TS_ERR_INVALID_ARG
     assert lib.msbfs_init_parents(10, 300, ctypes.c_void_p(256), ctypes.c_void_p(256), None) == N.TS_ERR_UNSUPPORTED
+    # Force2Vec limits, caught on the host
+    sz2 = ctypes.c_size_t()
+    assert lib.f2v_workspace_size(100, 64, 800, 10, 5, 8, ctypes.byref(sz2)) == N.TS_OK and sz2.value > 0
+    assert lib.f2v_workspace_size(100, 64, 800, 10, 5, 65, ctypes.byref(sz2)) == N.TS_ERR_UNSUPPORTED  # k > d
+    assert lib.f2v_workspace_size(100, 64, 800, 10, 33, 8, ctypes.byref(sz2)) == N.TS_ERR_UNSUPPORTED  # s > 32
+    Zbad = N.CsrDesc(100, 64, 799, 8, 8, 8)  # not k = 8 entries per row
+    Af = N.CsrDesc(100, 100, 0, 8, None, None)
+    assert lib.f2v_step(ctypes.byref(Af), ctypes.byref(Zbad), 0, 10, ctypes.c_void_p(256), 5, ctypes.c_float(0.1), 8,
+                        None, ctypes.c_void_p(256), sz2.value, None) == N.TS_ERR_INVALID_ARG
     assert N.status_string(N.TS_ERR_CAPACITY) == "TS_ERR_CAPACITY"
     assert lib.ts_version() >= 100
