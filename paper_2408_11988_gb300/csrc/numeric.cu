@@ -365,57 +365,43 @@ __device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* a
     }
 }
 
-// Read-out of tile c0 of every slot (all lanes converged).
+// Read-out of tile c0 of every slot (all lanes converged), in stripes of RG
+// columns: lane l of a slot takes column l of every stripe, so that the
+// entries one store instruction writes are consecutive positions of the
+// row in C (coalesced) and a stripe's offsets come from one ballot.  A slot's
+// output offsets are 32-bit (a row holds at most d entries); a row that
+// would pass its end in C stores nothing more and is reported by the caller
+// (out != out_end).
 template <int RG>
 __device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& out, long long out_end, int* Ci,
-                                        float* Cx, unsigned long long* err) {
-    const int gl = lane_id() % RG;
+                                        float* Cx, unsigned long long*) {
+    const int lane = lane_id(), gl = lane % RG;
+    const unsigned smask = (RG == 32 ? FULL : ((1u << RG) - 1u)) << (lane - gl);  // this slot's lanes
+    const unsigned below = smask & lanemask_lt();
     const long long r = out_end - out;
     const int room = r < 0x7FFFFFFFLL ? (int)r : 0x7FFFFFFF;
     int* ci = Ci + out;
     float* cx = Cx + out;
     int o = 0;  // entries of this slot's row written so far in this tile
-    for (int base = 0; base < W; base += 4 * RG) {
-        const int cb = base + 4 * gl;
-        unsigned x[4] = {RG_EMPTY, RG_EMPTY, RG_EMPTY, RG_EMPTY};
-        unsigned f = 0;
-        if (cb < W) {
-            uint4* q = reinterpret_cast<uint4*>(acc + cb);
-            const uint4 v = *q;
-            x[0] = v.x;
-            x[1] = v.y;
-            x[2] = v.z;
-            x[3] = v.w;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) f |= (x[i] != RG_EMPTY ? 1u : 0u) << i;
-            if (f) *q = make_uint4(RG_EMPTY, RG_EMPTY, RG_EMPTY, RG_EMPTY);
-        }
-        const int cnt = __popc(f);
-        int incl = cnt;
-#pragma unroll
-        for (int k = 1; k < RG; k <<= 1) {
-            const int t = __shfl_up_sync(FULL, incl, k, RG);
-            if (gl >= k) incl += t;
-        }
-        int pos = o + incl - cnt;
-        o += __shfl_sync(FULL, incl, RG - 1, RG);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (f & (1u << i)) {
-                if (pos < room) {
-                    ci[pos] = c0 + cb + i;
-                    cx[pos] = __uint_as_float(x[i]);
-                } else {
-                    atomicOr(err, ERR_C_ROW);
-                }
-                ++pos;
+#pragma unroll 4
+    for (int base = 0; base < W; base += RG) {
+        const int c = base + gl;
+        const unsigned x = __float_as_uint(acc[c]);
+        const bool take = x != RG_EMPTY;
+        const unsigned bal = __ballot_sync(FULL, take);
+        if (take) {
+            const int pos = o + __popc(bal & below);
+            if (pos < room) {
+                ci[pos] = c0 + c;
+                cx[pos] = __uint_as_float(x);
             }
+            acc[c] = __uint_as_float(RG_EMPTY);
         }
+        o += __popc(bal & smask);
     }
     out += o;
 }
 
-// Entry e of the slot's row (e < len): its segment of B in tile t and value.
 // Column index and value of entry ei of A (k = -1 past the row's end).
 __device__ __forceinline__ void rg_load_a(const NumParams& p, long long ei, bool ok, int& k, float& a) {
     k = -1;
@@ -503,7 +489,7 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
     static_assert(RG >= 4 && RG <= 16 && 32 % RG == 0, "lanes per row");
     const int lane = lane_id(), g = lane / RG, gl = lane % RG;
     const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);
-    float* acc = racc + g * (p.W + 4);  // W columns and a spare
+    float* acc = racc + g * (p.W + 8);  // W columns, a spare and padding
     unsigned long long* err = &p.hdr->err;
     bool bad = false;
     for (long long idx = idx0; idx < end; idx += step) {
@@ -537,7 +523,7 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
     if (bad) atomicOr(err, ERR_B_COL);
 }
 
-// Light rows only, in row groups; R = 32/RG accumulators of W + 4 floats per warp.
+// Light rows only, in row groups; R = 32/RG accumulators of W + 8 floats per warp.
 // Launched behind k_numeric (which then skips light rows) with programmatic
 // dependent launch: its blocks may start while k_numeric's last blocks run.
 // Before exiting, each block waits for k_numeric to complete, so that work
@@ -549,7 +535,7 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     constexpr int R = 32 / RG;
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     float* racc = reinterpret_cast<float*>(smem);
-    for (int i = tid; i < nw * R * (p.W + 4); i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
+    for (int i = tid; i < nw * R * (p.W + 8); i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
     if (tid == 0) {
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -558,7 +544,7 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     }
     __syncthreads();
     const long long* mark = p.s.stg_vals != nullptr ? p.s.flops : nullptr;
-    rg_light_rows<RG>(p, racc + (size_t)warp * R * (p.W + 4), s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
+    rg_light_rows<RG>(p, racc + (size_t)warp * R * (p.W + 8), s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
                       (long long)gridDim.x * nw * R, mark);
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -648,7 +634,7 @@ size_t numeric_dense_smem(int W, int warps, bool values) {
 
 size_t numeric_light_smem(int W, int warps, int rg) {
     if (rg != 4 && rg != 8 && rg != 16) return 0;
-    return (size_t)warps * (32 / rg) * 4 * ((size_t)W + 4);  // W columns and a spare per row
+    return (size_t)warps * (32 / rg) * 4 * ((size_t)W + 8);  // W columns, a spare, padding per row
 }
 
 template <bool VALUES, int G, bool PACKED>
