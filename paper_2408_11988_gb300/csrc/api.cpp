@@ -466,7 +466,7 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
         } else {
             LaunchCfg ncfg = cfg;
             if (ncfg.row_lanes != 32 &&
-                (!vals || !bpk || numeric_light_smem(L.W, cfg.warps_per_cta, ncfg.row_lanes) > 220 * 1024))
+                (!vals || !bpk || numeric_rgcta_smem(L.W, cfg.warps_per_cta, ncfg.row_lanes) > 220 * 1024))
                 ncfg.row_lanes = 32;  // row groups need the packed copy and room for their accumulators
             TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, ncfg,
                                          (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),

@@ -112,6 +112,7 @@ cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long lon
                                       const long long* Cp, int* Ci, float* Cx, long long nnzC, cudaStream_t st);
 // Dynamic shared memory of the row-group light-row kernel (0: bad row_lanes).
 size_t numeric_light_smem(int W, int warps, int row_lanes);
+size_t numeric_rgcta_smem(int W, int warps, int row_lanes);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).

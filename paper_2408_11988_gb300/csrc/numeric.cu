@@ -549,6 +549,158 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Split parts and heavy rows in row groups.  The block's S = warps * 32/RG
+// slots share one item (a part of a split row, or a heavy row): each slot
+// takes a contiguous share of the item's A entries and accumulates it into
+// its own dense accumulator exactly as a light row (no atomics: within a
+// slot one segment of B is in flight at a time).  The block then sums the
+// S accumulators column by column (a column no slot reached stays
+// RG_EMPTY) and resets them, and the sum is read out (heavy row) or added
+// into the row's staging slot (split part).
+// ---------------------------------------------------------------------------
+template <int RG>
+__device__ __forceinline__ void rgcta_tile(const NumParams& p, const int4* P4, float* racc, long long e0,
+                                           long long e1, int t, bool& bad) {
+    constexpr int R = 32 / RG;
+    const int S = (blockDim.x >> 5) * R, slot = warp_id() * R + lane_id() / RG;
+    const long long n = e1 - e0, q = n / S, r = n % S;
+    const long long a0 = e0 + q * slot + (slot < r ? slot : r);
+    const int len = (int)(q + (slot < r ? 1 : 0));
+    const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+    float* acc = racc + (size_t)slot * (p.W + 8);
+    const int c0 = t * p.W;
+    const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
+    unsigned long long* err = &p.hdr->err;
+    if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+    else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+}
+
+// Column c of the S slots summed (RG_EMPTY if no slot reached it); every
+// slot's column is reset.  Called by one thread per column after a barrier.
+__device__ __forceinline__ unsigned rgcta_sum(float* racc, int ld, int S, int c) {
+    unsigned x = RG_EMPTY;
+#pragma unroll 8
+    for (int k = 0; k < S; ++k) {
+        float* a = racc + (size_t)k * ld + c;
+        const unsigned y = __float_as_uint(*a);
+        if (y != RG_EMPTY) {
+            x = x == RG_EMPTY ? y : __float_as_uint(__uint_as_float(x) + __uint_as_float(y));
+            *a = __uint_as_float(RG_EMPTY);
+        }
+    }
+    return x;
+}
+
+// Block-wide read-out of a heavy row's tile from the summed columns held in
+// sum[0..W) (reset to RG_EMPTY); wcnt has W/32 + 1 entries.
+__device__ __forceinline__ void rgcta_emit(float* sum, int W, int c0, long long& out, long long out_end, int* Ci,
+                                           float* Cx, int* wcnt, unsigned long long* err) {
+    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    const int words = W >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int w = warp; w < words; w += nw) {
+        const unsigned bal = __ballot_sync(FULL, __float_as_uint(sum[w * 32 + lane]) != RG_EMPTY);
+        if (lane == 0) wcnt[w] = __popc(bal);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int tot = warp_excl_scan_smem(wcnt, words);
+        if (lane == 0) wcnt[words] = tot;
+    }
+    __syncthreads();
+    for (int w = warp; w < words; w += nw) {
+        const int c = w * 32 + lane;
+        const unsigned x = __float_as_uint(sum[c]);
+        const bool f = x != RG_EMPTY;
+        const unsigned bal = __ballot_sync(FULL, f);
+        if (f) {
+            const long long pos = out + wcnt[w] + __popc(bal & lt);
+            if (pos < out_end) {
+                Ci[pos] = c0 + c;
+                Cx[pos] = __uint_as_float(x);
+            } else {
+                atomicOr(err, ERR_C_ROW);
+            }
+            sum[c] = __uint_as_float(RG_EMPTY);
+        }
+    }
+    out += wcnt[words];
+    __syncthreads();
+}
+
+// Split parts, then heavy rows, in row groups (plus-times, padded packed B).
+// Shared memory: S accumulators of W + 8 floats (the slots), then W floats
+// for the summed tile.  Launched ahead of k_numeric_light, which takes the
+// light rows.
+template <int RG>
+__global__ void __launch_bounds__(256, 5) k_numeric_rgcta(NumParams p) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
+    __shared__ long long s_item, s_nheavy;
+    __shared__ int s_last;
+    constexpr int R = 32 / RG;
+    const int tid = threadIdx.x, S = (blockDim.x >> 5) * R, ld = p.W + 8;
+    float* racc = reinterpret_cast<float*>(smem);
+    float* sum = racc + (size_t)S * ld;
+    for (int i = tid; i < S * ld + p.W; i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
+    if (tid == 0) {
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+    }
+    __syncthreads();
+    const long long nheavy = s_nheavy;
+    const int4* P4 = reinterpret_cast<const int4*>(p.Bpk);
+    unsigned long long* err = &p.hdr->err;
+    bool bad = false;
+    const bool split_ok = p.s.stg_vals != nullptr;
+    const long long* mark = split_ok ? p.s.flops : nullptr;
+    const long long nitems = split_ok ? min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap) : 0;
+    SplitItem it;
+    while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
+        float* sv = p.s.stg_vals + (size_t)it.slot * p.s.dpad;
+        unsigned char* sf = p.s.stg_flags + (size_t)it.slot * p.s.dpad;
+        for (int t = 0; t < p.T; ++t) {
+            rgcta_tile<RG>(p, P4, racc, it.e0, it.e1, t, bad);
+            __syncthreads();
+            for (int c = tid; c < p.W; c += blockDim.x) {
+                const unsigned x = rgcta_sum(racc, ld, S, c);
+                if (x != RG_EMPTY) {
+                    atomicAdd(sv + t * p.W + c, __uint_as_float(x));
+                    sf[t * p.W + c] = 1;
+                }
+            }
+            __syncthreads();
+        }
+        if (!split_part_done(p.s, it.slot, it.nsub, &s_last)) continue;
+        split_row_readout<true>(p, it, s_wcnt);
+    }
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const int row = p.perm[h];
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        if (mark && is_split_row(mark, row, a1 - a0)) continue;
+        long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+        const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+        for (int t = 0; t < p.T; ++t) {
+            rgcta_tile<RG>(p, P4, racc, a0, a1, t, bad);
+            __syncthreads();
+            for (int c = tid; c < p.W; c += blockDim.x) sum[c] = __uint_as_float(rgcta_sum(racc, ld, S, c));
+            __syncthreads();
+            rgcta_emit(sum, p.W, t * p.W, out, out_end, p.Ci, p.Cx, s_wcnt, err);
+        }
+        if (out != out_end && tid == 0) atomicOr(err, ERR_C_ROW);
+    }
+    if (bad) atomicOr(err, ERR_B_COL);
+}
+
 template <bool VALUES, int G, bool PACKED>
 __global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
     // a light-row kernel launched behind this one may start on SMs this
@@ -637,6 +789,26 @@ size_t numeric_light_smem(int W, int warps, int rg) {
     return (size_t)warps * (32 / rg) * 4 * ((size_t)W + 8);  // W columns, a spare, padding per row
 }
 
+size_t numeric_rgcta_smem(int W, int warps, int rg) {
+    if (rg != 4 && rg != 8 && rg != 16) return 0;
+    return numeric_light_smem(W, warps, rg) + 4 * (size_t)W;  // the slots, then the summed tile
+}
+
+template <int RG>
+static cudaError_t launch_rgcta(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    const void* k = (const void*)k_numeric_rgcta<RG>;
+    const size_t smem = numeric_rgcta_smem(p.W, warps, RG);
+    cudaError_t e;
+    if (smem == 0 || smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid(k, 32 * warps, smem, sms);
+    count_launch();
+    k_numeric_rgcta<RG><<<grid, 32 * warps, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <bool VALUES, int G, bool PACKED>
 static cudaError_t launch_one(const NumParams& p, int warps, int sms, cudaStream_t st) {
     const void* k = (const void*)k_numeric<VALUES, G, PACKED>;
@@ -715,13 +887,16 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
     const int w = cfg.warps_per_cta;
     if (values && Bpk && cfg.row_lanes != 32) {  // row groups need the padded packed copy
-        NumParams ph = p;
-        ph.skip_light = 1;
-        if ((e = launch_g<true, true>(ph, G, w, cfg.sms, st))) return e;
         switch (cfg.row_lanes) {
-            case 4: return launch_light<4>(p, w, cfg.sms, st);
-            case 8: return launch_light<8>(p, w, cfg.sms, st);
-            case 16: return launch_light<16>(p, w, cfg.sms, st);
+            case 4:
+                if ((e = launch_rgcta<4>(p, w, cfg.sms, st))) return e;
+                return launch_light<4>(p, w, cfg.sms, st);
+            case 8:
+                if ((e = launch_rgcta<8>(p, w, cfg.sms, st))) return e;
+                return launch_light<8>(p, w, cfg.sms, st);
+            case 16:
+                if ((e = launch_rgcta<16>(p, w, cfg.sms, st))) return e;
+                return launch_light<16>(p, w, cfg.sms, st);
             default: return cudaErrorInvalidValue;
         }
     }
