@@ -365,41 +365,46 @@ __device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* a
     }
 }
 
-// Read-out of tile c0 of every slot (all lanes converged), in stripes of RG
-// columns: lane l of a slot takes column l of every stripe, so that the
-// entries one store instruction writes are consecutive positions of the
-// row in C (coalesced) and a stripe's offsets come from one ballot.  A slot's
-// output offsets are 32-bit (a row holds at most d entries); a row that
-// would pass its end in C stores nothing more and is reported by the caller
-// (out != out_end).
+// Read-out of tile c0 of every slot (all lanes converged): the warp reads
+// the slots out one after another, lane l taking column l of every 32-column
+// stripe, so that each store instruction writes consecutive positions of one
+// row of C (whole sectors) and a stripe's offsets come from one ballot.  A
+// slot's output offsets are 32-bit (a row holds at most d entries); a row
+// that would pass its end in C stores nothing more and is reported by the
+// caller (out != out_end).
 template <int RG>
-__device__ __forceinline__ void rg_emit(float* acc, int W, int c0, long long& out, long long out_end, int* Ci,
+__device__ __forceinline__ void rg_emit(float* racc, int W, int c0, long long& out, long long out_end, int* Ci,
                                         float* Cx, unsigned long long*) {
-    const int lane = lane_id(), gl = lane % RG;
-    const unsigned smask = (RG == 32 ? FULL : ((1u << RG) - 1u)) << (lane - gl);  // this slot's lanes
-    const unsigned below = smask & lanemask_lt();
-    const long long r = out_end - out;
-    const int room = r < 0x7FFFFFFFLL ? (int)r : 0x7FFFFFFF;
-    int* ci = Ci + out;
-    float* cx = Cx + out;
-    int o = 0;  // entries of this slot's row written so far in this tile
+    constexpr int R = 32 / RG;
+    const int lane = lane_id(), g = lane / RG;
+    const unsigned lt = lanemask_lt();
+#pragma unroll 1
+    for (int h = 0; h < R; ++h) {
+        const long long o0 = shfl64(out, h * RG), e0 = shfl64(out_end, h * RG);
+        const long long r = e0 - o0;
+        const int room = r < 0x7FFFFFFFLL ? (int)r : 0x7FFFFFFF;
+        int* ci = Ci + o0;
+        float* cx = Cx + o0;
+        float* acc = racc + h * (W + 8);
+        int o = 0;
 #pragma unroll 4
-    for (int base = 0; base < W; base += RG) {
-        const int c = base + gl;
-        const unsigned x = __float_as_uint(acc[c]);
-        const bool take = x != RG_EMPTY;
-        const unsigned bal = __ballot_sync(FULL, take);
-        if (take) {
-            const int pos = o + __popc(bal & below);
-            if (pos < room) {
-                ci[pos] = c0 + c;
-                cx[pos] = __uint_as_float(x);
+        for (int base = 0; base < W; base += 32) {
+            const int c = base + lane;
+            const unsigned x = __float_as_uint(acc[c]);
+            const bool take = x != RG_EMPTY;
+            const unsigned bal = __ballot_sync(FULL, take);
+            if (take) {
+                const int pos = o + __popc(bal & lt);
+                if (pos < room) {
+                    ci[pos] = c0 + c;
+                    cx[pos] = __uint_as_float(x);
+                }
+                acc[c] = __uint_as_float(RG_EMPTY);
             }
-            acc[c] = __uint_as_float(RG_EMPTY);
+            o += __popc(bal);
         }
-        o += __popc(bal & smask);
+        if (g == h) out += o;
     }
-    out += o;
 }
 
 // Column index and value of entry ei of A (k = -1 past the row's end).
@@ -515,7 +520,7 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
             const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
             if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
-            rg_emit<RG>(acc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
+            rg_emit<RG>(racc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
             __syncwarp();
         }
         if (active && gl == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
