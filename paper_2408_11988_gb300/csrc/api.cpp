@@ -112,11 +112,7 @@ static DevCsr dev(const ts_csr_desc* M) {
     return c;
 }
 
-static int cta_class_of(long long min_flops) {
-    int m = 0;
-    while ((1LL << m) < min_flops && m < 46) ++m;
-    return m + 1;
-}
+static int cta_class_of(long long min_flops) { return class_at_least(min_flops); }
 
 // ---------------------------------------------------------------------------
 // plans
@@ -203,7 +199,7 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
 }
 
 struct Layout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, bq = 0, total = 0;
     size_t split_rows = 0, split_done = 0, split_items = 0, stg_bits = 0, stg_vals = 0, stg_flags = 0;
     int dw = 0, dpad = 0;
     int W = 0, T = 1;
@@ -250,6 +246,8 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     if (Tmax > 1) L.tp = take(sizeof(long long) * (size_t)n * (Tmax + 1));
     // packed B, padded by four entries for the 16-byte loads of whole quads
     if (t.pack_b == 1 || cover_autotune) L.bpk = take(8 * ((size_t)nnzB + 4));
+    // row-aligned packed B for the row-group numeric kernels (one column tile)
+    if ((t.pack_b == 1 && L.T == 1 && t.row_lanes != 32) || cover_autotune) L.bq = take(padded_b_bytes(n, nnzB, d, 4));
     L.total = off;
     return L;
 }
@@ -441,14 +439,27 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
             tp = (long long*)((char*)ws + L.tp);
             TS_CUDA(launch_tile_split(dB, L.W, L.T, tp, st), fn);
         }
+        const int cg = copies_group(plan->cur.group, plan->n, plan->nnzB);
+        const bool copies = vals && plan->cur.accum == TS_ACC_COPIES &&
+                            numeric_copies_smem(L.W, cg, cfg.warps_per_cta) <= 227 * 1024;
+        const bool staged = !copies && plan->cur.stage == 1 &&
+                            numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024;
+        // the row-group kernels over one column tile read the row-aligned copy
+        const int qE = cfg.row_lanes == 4 ? 4 : 2;
+        const bool use_bq = !copies && !staged && vals && plan->cur.pack_b == 1 && L.T == 1 && L.bq &&
+                            B->nnz > 0 && cfg.row_lanes != 32 &&
+                            numeric_rgcta_smem(L.W, cfg.warps_per_cta, cfg.row_lanes) <= 220 * 1024 &&
+                            padded_b_fits(B->nrows, B->nnz, plan->d, qE);
         int2* bpk = nullptr;
-        if (vals && plan->cur.pack_b == 1 && B->nnz > 0) {
+        int4* bq = nullptr;
+        if (use_bq) {
+            bq = (int4*)((char*)ws + L.bq);
+            TS_CUDA(launch_pack_b_rows(dB, qE, plan->d, bq, &sc.hdr->err, st), fn);
+        } else if (vals && plan->cur.pack_b == 1 && B->nnz > 0) {
             bpk = (int2*)((char*)ws + L.bpk);
             TS_CUDA(launch_pack_b(dB, bpk, st), fn);
         }
-        const int cg = copies_group(plan->cur.group, plan->n, plan->nnzB);
-        if (vals && plan->cur.accum == TS_ACC_COPIES &&
-            numeric_copies_smem(L.W, cg, cfg.warps_per_cta) <= 227 * 1024) {
+        if (copies) {
             // light rows in row groups behind the copies kernel when they fit
             const bool rg = cfg.row_lanes != 32 && bpk &&
                             numeric_light_smem(L.W, cfg.warps_per_cta, cfg.row_lanes) <= 220 * 1024;
@@ -459,17 +470,16 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
                 TS_CUDA(launch_numeric_light_rows(dA, dB, plan->d, L.W, L.T, tp, bpk, sc, cfg,
                                                   (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                         fn);
-        } else if (plan->cur.stage == 1 && numeric_staged_smem(L.W, cfg.warps_per_cta, vals) <= 227 * 1024 &&
-                   (!vals || bpk || B->nnz == 0)) {
+        } else if (staged && (!vals || bpk || B->nnz == 0)) {
             TS_CUDA(launch_numeric_staged(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
                     fn);
         } else {
             LaunchCfg ncfg = cfg;
             if (ncfg.row_lanes != 32 &&
-                (!vals || !bpk || numeric_rgcta_smem(L.W, cfg.warps_per_cta, ncfg.row_lanes) > 220 * 1024))
-                ncfg.row_lanes = 32;  // row groups need the packed copy and room for their accumulators
+                (!vals || !(bpk || bq) || numeric_rgcta_smem(L.W, cfg.warps_per_cta, ncfg.row_lanes) > 220 * 1024))
+                ncfg.row_lanes = 32;  // row groups need a packed copy and room for their accumulators
             TS_CUDA(launch_numeric_dense(dA, dB, plan->d, L.W, L.T, tp, vals, bpk, plan->cur.group, sc, ncfg,
-                                         (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st),
+                                         (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st, bq),
                     fn);
         }
     } else {

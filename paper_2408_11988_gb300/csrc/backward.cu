@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256, 5) k_backward_light(BwdParams p) {
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
     const int g = lane / RG, gl = lane % RG;
     for (int i = tid; i < nw * R * p.dpad; i += blockDim.x) fsm[i] = 0.0f;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
@@ -476,12 +476,9 @@ __global__ void __launch_bounds__(256, 5) k_backward(BwdParams p) {
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     // layout: [nw][dpad] dense dC rows, then [nw][32] dA partials
     for (int i = tid; i < nw * (p.dpad + 32); i += blockDim.x) fsm[i] = 0.0f;
-    if (tid == 0) {
-        long long nh = 0, nr = 0;
-        for (int c = 1; c < NUM_CLASSES; ++c) {
-            nr += p.hdr->hist[c];
-            if (c >= p.cta_class) nh += p.hdr->hist[c];
-        }
+    if (tid < 32) {  // one warp; its lanes store the same values
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
         s_nrows = nr;
     }

@@ -29,9 +29,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Row class of f products (layout.h: eighths of an octave).
 __device__ __forceinline__ int flops_class(long long f) {
     if (f <= 0) return 0;
-    int c = 64 - __clzll(f);  // 1 + floor(log2 f)
+    const int lg = 63 - __clzll(f);
+    const int sub = lg >= CLASS_SUB_BITS ? (int)((f >> (lg - CLASS_SUB_BITS)) & ((1 << CLASS_SUB_BITS) - 1))
+                                         : (int)((f << (CLASS_SUB_BITS - lg)) & ((1 << CLASS_SUB_BITS) - 1));
+    const int c = 1 + (lg << CLASS_SUB_BITS) + sub;
     return c < NUM_CLASSES ? c : NUM_CLASSES - 1;
 }
 
@@ -339,16 +343,17 @@ __device__ __forceinline__ void pipelined_rows(const int* __restrict__ perm, lon
 }
 
 // Rows with products: all classes >= 1; heavy: classes >= cta_class.
+// Called by all 32 lanes of one warp (every lane gets the counts).
 __device__ __forceinline__ void sched_counts(const WsHeader* hdr, int cta_class, long long& nheavy,
                                              long long& nrows) {
     long long nh = 0, nr = 0;
-    for (int c = 1; c < NUM_CLASSES; ++c) {
+    for (int c = 1 + lane_id(); c < NUM_CLASSES; c += 32) {
         const long long h = hdr->hist[c];
         nr += h;
         if (c >= cta_class) nh += h;
     }
-    nheavy = nh;
-    nrows = nr;
+    nheavy = warp_sum(nh);
+    nrows = warp_sum(nr);
 }
 
 // Fetch the next split item for this block; false when none is left.  On

@@ -211,12 +211,9 @@ __global__ void __launch_bounds__(1024) k_numeric_hash(HashParams p) {
         vals[i] = 0.0f;
     }
     for (int i = tid; i < nw * p.dw; i += blockDim.x) bms[i] = 0u;
-    if (tid == 0) {
-        long long nh = 0, nr = 0;
-        for (int c = 1; c < NUM_CLASSES; ++c) {
-            nr += p.hdr->hist[c];
-            if (c >= p.cta_class) nh += p.hdr->hist[c];
-        }
+    if (tid < 32) {  // one warp; its lanes store the same values
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
         s_nrows = nr;
     }
@@ -276,8 +273,7 @@ cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, i
     p.hdr = s.hdr;
     // warp tables hold 3/4 * slots columns: rows with more products go to the block table
     int cc = cfg.cta_class;
-    int lim = 1;
-    while ((1LL << lim) <= (long long)slots * 3 / 4) ++lim;  // 2^(lim-1) <= 0.75 S
+    const int lim = flops_class_host((long long)slots * 3 / 4 + 1);  // warp rows: flops <= 0.75 S
     if (cc > lim) cc = lim;
     p.cta_class = cc;
     p.Cp = Cp;

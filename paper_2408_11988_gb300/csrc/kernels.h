@@ -77,10 +77,12 @@ cudaError_t launch_tile_split(const DevCsr& B, int W, int T, long long* tp, cuda
 // Numeric pass with a dense accumulator of width W over T column tiles.
 // Bpk: packed (column, value) copy of B or nullptr; G: lanes per A entry
 // (1 = flattened products).
+// Bq: row-aligned packed copy of B (launch_pack_b_rows, groups of 4 entries
+// for row_lanes 4, else 2) for the row-group kernels with T = 1, or nullptr.
 cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                  const long long* tp, bool values, const int2* Bpk, int G,
                                  const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,
-                                 float* Cx, long long nnzC, cudaStream_t st);
+                                 float* Cx, long long nnzC, cudaStream_t st, const int4* Bq = nullptr);
 // Numeric pass with the dense accumulator and cp.async staging of B.
 cudaError_t launch_numeric_staged(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                   const long long* tp, bool values, const int2* Bpk, const Sched& s,
@@ -97,6 +99,14 @@ cudaError_t launch_numeric_copies(const DevCsr& A, const DevCsr& B, long long d,
 size_t numeric_copies_smem(int W, int G, int warps);
 // Packed (column, value bits) copy of B's entries.
 cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st);
+// Row-aligned packed copy of B: row k starts at entry E*ceil((Bp[k] + (E-1)k)/E),
+// its last group padded with column -1; columns outside [0, d) are stored as
+// -1 and set ERR_B_COL in *err.  E = 2 or 4.
+cudaError_t launch_pack_b_rows(const DevCsr& B, int E, long long d, int4* Q, unsigned long long* err,
+                               cudaStream_t st);
+size_t padded_b_bytes(long long nB, long long nnzB, long long d, int E);
+// Whether the copy's groups can be numbered with 32 bits.
+bool padded_b_fits(long long nB, long long nnzB, long long d, int E);
 
 // Numeric pass with a per-warp hash accumulator of `slots` entries.
 cudaError_t launch_numeric_hash(const DevCsr& A, const DevCsr& B, long long d, int slots,

@@ -4,7 +4,29 @@
 
 namespace ts {
 
-constexpr int NUM_CLASSES = 48;  // class 0: no products; class c >= 1: flops in [2^(c-1), 2^c)
+// Row classes by products (flops): class 0 = no products; class
+// 1 + 8*lg + sub (lg = floor(log2 f), sub = the three bits of f below its
+// leading one) holds an eighth of an octave, so the rows of one class differ
+// in flops by less than 12.5 % and rows taken side by side in lockstep have
+// nearly equal lengths.
+constexpr int CLASS_SUB_BITS = 3;
+constexpr int NUM_CLASSES = 1 + 48 * (1 << CLASS_SUB_BITS);
+
+// Host copy of the device-side class function (common.cuh).
+inline int flops_class_host(long long f) {
+    if (f <= 0) return 0;
+    const int lg = 63 - __builtin_clzll((unsigned long long)f);
+    const int sub = lg >= CLASS_SUB_BITS ? (int)((f >> (lg - CLASS_SUB_BITS)) & ((1 << CLASS_SUB_BITS) - 1))
+                                         : (int)((f << (CLASS_SUB_BITS - lg)) & ((1 << CLASS_SUB_BITS) - 1));
+    const int c = 1 + (lg << CLASS_SUB_BITS) + sub;
+    return c < NUM_CLASSES ? c : NUM_CLASSES - 1;
+}
+
+// First class whose rows all have at least min_flops products (rounded up
+// to a class boundary).
+inline int class_at_least(long long min_flops) {
+    return min_flops <= 1 ? 1 : flops_class_host(min_flops - 1) + 1;
+}
 
 // error bits recorded in the workspace header by device-side checks
 constexpr unsigned long long ERR_A_COL = 1ull;     // column of A outside [0, n)

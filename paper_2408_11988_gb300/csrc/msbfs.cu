@@ -96,12 +96,9 @@ __global__ void __launch_bounds__(1024) k_msbfs_expand(BfsParams p) {
     __shared__ int s_red[32];
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
     for (int i = tid; i < nw * p.dw; i += blockDim.x) smem_u[i] = 0u;
-    if (tid == 0) {
-        long long nh = 0, nr = 0;
-        for (int c = 1; c < NUM_CLASSES; ++c) {
-            nr += p.hdr->hist[c];
-            if (c >= p.cta_class) nh += p.hdr->hist[c];
-        }
+    if (tid < 32) {  // one warp; its lanes store the same values
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
         s_nrows = nr;
     }
@@ -352,12 +349,9 @@ __global__ void __launch_bounds__(256) k_msbfs_pull(BfsParams p, const unsigned*
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ unsigned s_or[DWP];
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
-    if (tid == 0) {
-        long long nh = 0, nr = 0;
-        for (int c = 1; c < NUM_CLASSES; ++c) {
-            nr += p.hdr->hist[c];
-            if (c >= p.cta_class) nh += p.hdr->hist[c];
-        }
+    if (tid < 32) {  // one warp; its lanes store the same values
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
         s_nrows = nr;
     }

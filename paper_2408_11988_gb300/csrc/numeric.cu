@@ -486,6 +486,129 @@ __device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-aligned packed copy of B (one column tile, T = 1).  Row k's entries
+// start at entry S(k) = E * ceil((Bp[k] + (E-1) k) / E) of the copy, so every
+// row begins a group of E entries (one or two 16-byte loads) and
+// S(k) + len_k <= S(k+1) holds without a scan over the row lengths.  The
+// last group of a row is completed with pad entries (column -1, value 0),
+// and a column outside [0, d) (an input error, reported once by the packing
+// kernel) is stored as -1 too.  A slot maps a column c to accumulator index
+// min((unsigned)c, W): pads and bad columns land in the spare column W,
+// which is never read out, so the gather needs no per-entry segment or
+// range test.  Groups are numbered with 32 bits (the host checks the copy's
+// size).
+// ---------------------------------------------------------------------------
+// Row k of B as the copy holds it: its first entry s and length len in B
+// (clamped like SegWhole) and its first group g0 in the copy.
+template <int E>
+__device__ __forceinline__ void padded_row(const long long* __restrict__ Bp, long long nnzB, int d, int k,
+                                           long long& s, int& len, unsigned& g0) {
+    s = clampll(__ldg(Bp + k), 0, nnzB);
+    const long long e = clampll(__ldg(Bp + k + 1), s, nnzB);
+    len = (int)(e - s < d ? e - s : d);
+    g0 = (unsigned)((s + (long long)(E - 1) * k + (E - 1)) / E);
+}
+
+template <int E>
+__device__ __forceinline__ void padded_seg(const long long* __restrict__ Bp, long long nnzB, int d, int k,
+                                           unsigned& g0, int& ng) {
+    long long s;
+    int len;
+    padded_row<E>(Bp, nnzB, d, k, s, len, g0);
+    ng = (len + E - 1) / E;
+}
+
+// Segment (first group, groups) of B's row k for entry k of A (empty when
+// !ok; a bad k is an input error).
+template <int E>
+__device__ __forceinline__ void rgp_seg(const NumParams& p, int k, bool ok, unsigned& g0, int& ng,
+                                        unsigned long long* err) {
+    g0 = 0;
+    ng = 0;
+    if (!ok) return;
+    if ((unsigned)k < (unsigned)p.nB) padded_seg<E>(p.Bp, p.nnzB, p.d, k, g0, ng);
+    else atomicOr(err, ERR_A_COL);
+}
+
+// Group g of the copy (E = 2: one 16-byte load; E = 4: two).
+template <int E>
+__device__ __forceinline__ void rgp_load(const int4* __restrict__ Q, unsigned g, int4& v0, int4& v1) {
+    v0 = __ldg(Q + (size_t)g * (E / 2));
+    if constexpr (E == 4) v1 = __ldg(Q + (size_t)g * 2 + 1);
+}
+
+template <int E>
+__device__ __forceinline__ void rgp_apply(float* acc, const int4& v0, const int4& v1, float a, unsigned W) {
+    const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
+    const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        const unsigned c = (unsigned)cs[u] < W ? (unsigned)cs[u] : W;
+        rg_add(acc, (int)c, a * __int_as_float(bs[u]));
+    }
+}
+
+// rg_tile on the row-aligned copy: chunks of RG entries of every slot's row,
+// software-pipelined the same way (the next segment's description and first
+// group load while the current segment is accumulated).
+template <int RG, int E>
+__device__ __forceinline__ void rgp_tile(const NumParams& p, const int4* __restrict__ Q, float* acc, long long a0,
+                                         int len, int lmax, unsigned long long* err) {
+    const int lane = lane_id(), gl = lane % RG, src0 = (lane / RG) * RG;
+    const unsigned W = (unsigned)p.W;
+    int k0, k1;
+    float x0, x1;
+    rg_load_a(p, a0 + gl, gl < len, k0, x0);
+    rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
+    unsigned g0;
+    int n0;
+    rgp_seg<E>(p, k0, gl < len, g0, n0, err);
+    unsigned ng = __shfl_sync(FULL, g0, src0);
+    int nn = __shfl_sync(FULL, n0, src0);
+    float na = __shfl_sync(FULL, x0, src0);
+    int4 v0 = make_int4(0, 0, 0, 0), v1 = make_int4(0, 0, 0, 0);
+    if (gl < nn) rgp_load<E>(Q, ng + gl, v0, v1);
+    for (int e = 0; e < lmax; e += RG) {
+        int k2;
+        float x2;
+        unsigned g1;
+        int n1;
+        rg_load_a(p, a0 + e + 2 * RG + gl, e + 2 * RG + gl < len, k2, x2);
+        rgp_seg<E>(p, k1, e + RG + gl < len, g1, n1, err);
+        if (n1 > 0) prefetch_l2(Q + (size_t)g1 * (E / 2));  // the next chunk's rows of B into L2
+        const int nu = lmax - e < RG ? lmax - e : RG;
+        for (int u = 0; u < nu; ++u) {
+            const unsigned cg = ng;
+            const int cn = nn;
+            const float ca = na;
+            const int4 c0v = v0, c1v = v1;
+            // describe and start loading the segment after this one (the
+            // first of the next chunk after the last of this one)
+            const bool more = u + 1 < nu;
+            const int su = more ? src0 + u + 1 : src0;
+            ng = __shfl_sync(FULL, more ? g0 : g1, su);
+            nn = __shfl_sync(FULL, more ? n0 : n1, su);
+            na = __shfl_sync(FULL, more ? x0 : x1, su);
+            if (gl < nn) rgp_load<E>(Q, ng + gl, v0, v1);
+            if (gl < cn) {
+                rgp_apply<E>(acc, c0v, c1v, ca, W);
+                for (int q = gl + RG; q < cn; q += RG) {
+                    int4 w0, w1;
+                    rgp_load<E>(Q, cg + q, w0, w1);
+                    rgp_apply<E>(acc, w0, w1, ca, W);
+                }
+            }
+            __syncwarp();
+        }
+        g0 = g1;
+        n0 = n1;
+        x0 = x1;
+        k1 = k2;
+        x1 = x2;
+    }
+}
+
 // The warp's light rows: row groups idx0, idx0 + step, ... (step = R * warps).
 template <int RG>
 __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, long long idx0, long long end,
@@ -518,7 +641,8 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
         for (int t = 0; t < p.T; ++t) {
             const int c0 = t * p.W;
             const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
-            if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+            if (p.Bq) rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err);  // T = 1
+            else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             rg_emit<RG>(racc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
             __syncwarp();
@@ -541,7 +665,7 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     float* racc = reinterpret_cast<float*>(smem);
     for (int i = tid; i < nw * R * (p.W + 8); i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
@@ -577,7 +701,8 @@ __device__ __forceinline__ void rgcta_tile(const NumParams& p, const int4* P4, f
     const int c0 = t * p.W;
     const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
     unsigned long long* err = &p.hdr->err;
-    if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+    if (p.Bq) rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err);  // T = 1
+    else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
     else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
 }
 
@@ -650,7 +775,7 @@ __global__ void __launch_bounds__(256, 5) k_numeric_rgcta(NumParams p) {
     float* racc = reinterpret_cast<float*>(smem);
     float* sum = racc + (size_t)S * ld;
     for (int i = tid; i < S * ld + p.W; i += blockDim.x) reinterpret_cast<unsigned*>(racc)[i] = RG_EMPTY;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
@@ -718,7 +843,7 @@ __global__ void __launch_bounds__(256, 5) k_numeric(NumParams p) {
     const int slot = VALUES ? 5 * p.W : p.W;  // bytes per warp: W floats + W flags
     for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
 
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
@@ -774,6 +899,66 @@ __global__ void k_pack_b(long long nnz, const int* __restrict__ Bi, const float*
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
          j += (long long)gridDim.x * blockDim.x)
         P[j] = make_int2(__ldg(Bi + j), __float_as_int(__ldg(Bx + j)));
+}
+
+// The row-aligned copy (E entries per group): eight lanes per row of B, each
+// lane one entry per step (loads and stores of a row are contiguous), pads
+// included.
+template <int E>
+__global__ void __launch_bounds__(256) k_pack_b_rows(int nB, const long long* __restrict__ Bp, long long nnzB,
+                                                     const int* __restrict__ Bi, const float* __restrict__ Bx, int d,
+                                                     int2* __restrict__ Q, unsigned long long* err) {
+    const int gl = threadIdx.x & 7;
+    bool bad = false;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; k < nB; k += (gridDim.x * blockDim.x) >> 3) {
+        long long s;
+        int len;
+        unsigned g0;
+        padded_row<E>(Bp, nnzB, d, k, s, len, g0);
+        const int span = (len + E - 1) & ~(E - 1);
+        int2* q = Q + (size_t)g0 * E;
+        for (int j = gl; j < span; j += 8) {
+            int2 v = make_int2(-1, 0);
+            if (j < len) {
+                const int c = __ldg(Bi + s + j);
+                const bool ok = (unsigned)c < (unsigned)d;
+                bad |= !ok;
+                v = make_int2(ok ? c : -1, __float_as_int(__ldg(Bx + s + j)));
+            }
+            q[j] = v;
+        }
+    }
+    if (bad) atomicOr(err, ERR_B_COL);
+}
+
+// Entries of the row-aligned copy for B (n_B rows, nnzB entries, d columns)
+// with groups of E entries: room for S(k) + the row's groups of any row k
+// whose length is clamped to d.
+static long long padded_b_entries(long long nB, long long nnzB, long long d, int E) {
+    return (nnzB + (long long)(E - 1) * nB + d + 2LL * E + E - 1) / E * E;
+}
+
+size_t padded_b_bytes(long long nB, long long nnzB, long long d, int E) {
+    return 8 * (size_t)padded_b_entries(nB, nnzB, d, E);
+}
+
+bool padded_b_fits(long long nB, long long nnzB, long long d, int E) {
+    return padded_b_entries(nB, nnzB, d, E) / E < (1LL << 31) && nB < (1LL << 31);
+}
+
+cudaError_t launch_pack_b_rows(const DevCsr& B, int E, long long d, int4* Q, unsigned long long* err,
+                               cudaStream_t st) {
+    if (B.nrows == 0) return cudaSuccess;
+    if ((E != 2 && E != 4) || !padded_b_fits(B.nrows, B.nnz, d, E)) return cudaErrorInvalidValue;
+    long long blocks = (B.nrows + 31) / 32;  // 32 rows per block of 256 threads
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    int2* P = reinterpret_cast<int2*>(Q);
+    count_launch();
+    if (E == 2)
+        k_pack_b_rows<2><<<(unsigned)blocks, 256, 0, st>>>((int)B.nrows, B.rowptr, B.nnz, B.col, B.val, (int)d, P, err);
+    else
+        k_pack_b_rows<4><<<(unsigned)blocks, 256, 0, st>>>((int)B.nrows, B.rowptr, B.nnz, B.col, B.val, (int)d, P, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_b(const DevCsr& B, int2* P, cudaStream_t st) {
@@ -883,15 +1068,17 @@ cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long lon
 cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                  const long long* tp, bool values, const int2* Bpk, int G,
                                  const Sched& s, const LaunchCfg& cfg, const long long* Cp, int* Ci,
-                                 float* Cx, long long nnzC, cudaStream_t st) {
+                                 float* Cx, long long nnzC, cudaStream_t st, const int4* Bq) {
     cudaError_t e;
     if (A.nrows == 0) return cudaSuccess;
     if (W <= 0 || W % 32 || W > MAX_DENSE_W || (long long)W * T < d) return cudaErrorInvalidValue;
     if (cfg.warps_per_cta < 1 || cfg.warps_per_cta > 8) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(&s.hdr->heavy_ctr, 0, 2 * sizeof(unsigned long long), st))) return e;
-    const NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
+    NumParams p = numeric_params(A, B, d, W, T, tp, Bpk, s, cfg, Cp, Ci, Cx, nnzC);
     const int w = cfg.warps_per_cta;
-    if (values && Bpk && cfg.row_lanes != 32) {  // row groups need the padded packed copy
+    if (Bq && (T != 1 || !values || cfg.row_lanes == 32)) return cudaErrorInvalidValue;
+    p.Bq = Bq;
+    if (values && (Bpk || Bq) && cfg.row_lanes != 32) {  // row groups need a packed copy
         switch (cfg.row_lanes) {
             case 4:
                 if ((e = launch_rgcta<4>(p, w, cfg.sms, st))) return e;
@@ -1113,7 +1300,7 @@ __global__ void __launch_bounds__(256, 4) k_numeric_staged(NumParams p) {
     // layout: [nw][slot] accumulators, then [nw] staging areas
     for (int i = tid; i < nw * slot / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
     const StageArea<E> sa{smem + (size_t)nw * slot + (size_t)warp * StageArea<E>::BYTES};
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;

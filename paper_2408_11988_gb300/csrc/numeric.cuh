@@ -19,6 +19,7 @@ struct NumParams {
     const int* Bi;
     const float* Bx;
     const int2* Bpk;
+    const int4* Bq;  // row-aligned packed copy of B (T = 1, row-group kernels) or nullptr
     long long nnzB;
     int nB;
     int d;
@@ -49,6 +50,7 @@ inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, i
     p.Bi = B.col;
     p.Bx = B.val;
     p.Bpk = Bpk;
+    p.Bq = nullptr;
     p.nnzB = B.nnz;
     p.nB = (int)B.nrows;
     p.d = (int)d;

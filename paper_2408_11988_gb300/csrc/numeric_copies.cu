@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256, (G == 32 ? 3 : 4)) k_numeric_copies(NumPa
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     const size_t wbytes = pc_warp_bytes(p.W, NG);
     for (size_t i = tid; i < nw * wbytes / 4; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = PC_EMPTY;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;

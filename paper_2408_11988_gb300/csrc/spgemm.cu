@@ -167,13 +167,16 @@ __global__ void __launch_bounds__(256) k_scatter(long long n, const long long* _
     __shared__ long long s_base[NUM_CLASSES];
     const int tid = threadIdx.x;
     for (int c = tid; c < NUM_CLASSES; c += blockDim.x) s_cnt[c] = 0;
-    if (tid == 0) {
+    if (tid < 32) {  // start of class c = rows of the classes above it (warp scan, highest class first)
         long long run = 0;
-        for (int c = NUM_CLASSES - 1; c >= 1; --c) {
-            s_start[c] = run;
-            run += hdr->hist[c];
+        for (int top = NUM_CLASSES - 1; top >= 1; top -= 32) {
+            const int c = top - tid;
+            const long long h = c >= 1 ? hdr->hist[c] : 0;
+            const long long incl = warp_incl_scan(h);
+            if (c >= 1) s_start[c] = run + incl - h;
+            run += __shfl_sync(FULL, incl, 31);
         }
-        s_start[0] = run;
+        if (tid == 0) s_start[0] = run;
     }
     __syncthreads();
     const long long base = (long long)blockIdx.x * blockDim.x * SCATTER_ROWS;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     __shared__ int s_red[32];
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
     for (int i = tid; i < nw * p.slot; i += blockDim.x) smem_u[i] = 0;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(256, 6) k_symbolic_light(SymParams p) {
     const int g = lane / RG, gl = lane % RG;
     const int slotw = 8 * p.dw;  // words of one row's dpad bytes
     for (int i = tid; i < nw * R * slotw; i += blockDim.x) smem_u[i] = 0u;
-    if (tid == 0) {
+    if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
         s_nheavy = nh;
