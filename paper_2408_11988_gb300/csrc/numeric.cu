@@ -551,16 +551,15 @@ __device__ __forceinline__ void rgp_apply(float* acc, const int4& v0, const int4
 
 // rg_tile on the row-aligned copy: chunks of RG entries of every slot's row,
 // software-pipelined the same way (the next segment's description and first
-// group load while the current segment is accumulated).
+// group load while the current segment is accumulated).  The caller has
+// loaded the first two chunks of A (k0/x0: entry a0 + gl, k1/x1: entry
+// a0 + RG + gl, as rg_load_a gives them).
 template <int RG, int E>
 __device__ __forceinline__ void rgp_tile(const NumParams& p, const int4* __restrict__ Q, float* acc, long long a0,
-                                         int len, int lmax, unsigned long long* err) {
+                                         int len, int lmax, unsigned long long* err, int k0, float x0, int k1,
+                                         float x1) {
     const int lane = lane_id(), gl = lane % RG, src0 = (lane / RG) * RG;
     const unsigned W = (unsigned)p.W;
-    int k0, k1;
-    float x0, x1;
-    rg_load_a(p, a0 + gl, gl < len, k0, x0);
-    rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
     unsigned g0;
     int n0;
     rgp_seg<E>(p, k0, gl < len, g0, n0, err);
@@ -641,8 +640,7 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
         for (int t = 0; t < p.T; ++t) {
             const int c0 = t * p.W;
             const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
-            if (p.Bq) rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err);  // T = 1
-            else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+            if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
             rg_emit<RG>(racc, p.W, c0, out, out_end, p.Ci, p.Cx, err);
             __syncwarp();
@@ -652,12 +650,84 @@ __device__ __forceinline__ void rg_light_rows(const NumParams& p, float* racc, l
     if (bad) atomicOr(err, ERR_B_COL);
 }
 
+// Entries [a0, a0 + len) of A of a slot's row (len = 0 and inactive past the
+// schedule's end, or for a split row, whose entries are taken as split parts).
+__device__ __forceinline__ void rg_row_bounds(const NumParams& p, int row, const long long* mark, long long& a0,
+                                              int& len, bool& active) {
+    a0 = 0;
+    len = 0;
+    active = false;
+    if (row < 0) return;
+    a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+    const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+    if (mark && is_split_row(mark, row, a1 - a0)) return;
+    len = (int)(a1 - a0);
+    active = true;
+}
+
+// rg_light_rows on the row-aligned copy (T = 1), pipelined across row
+// groups: while group idx is gathered, the schedule entry of group idx + 2
+// steps and the row bounds of group idx + step are in flight; the next
+// group's first two chunks of A and output range load before this group's
+// read-out.  A group then starts with only B's row pointers and first groups
+// to wait for.
+template <int RG>
+__device__ __forceinline__ void rgp_light_rows(const NumParams& p, float* racc, long long idx0, long long end,
+                                               long long step, const long long* mark) {
+    constexpr int E = RG == 4 ? 4 : 2;
+    const int lane = lane_id(), g = lane / RG, gl = lane % RG;
+    float* acc = racc + g * (p.W + 8);  // W columns, a spare and padding
+    unsigned long long* err = &p.hdr->err;
+    auto row_at = [&](long long idx) { return idx + g < end ? __ldg(p.perm + idx + g) : -1; };
+    int row = row_at(idx0), nrow = row_at(idx0 + step);
+    long long a0;
+    int len;
+    bool active;
+    rg_row_bounds(p, row, mark, a0, len, active);
+    long long out = 0, out_end = 0;
+    if (active) {
+        out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+        out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+    }
+    int k0, k1;
+    float x0, x1;
+    rg_load_a(p, a0 + gl, gl < len, k0, x0);
+    rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
+    for (long long idx = idx0; idx < end; idx += step) {
+        long long na0;
+        int nlen;
+        bool nactive;
+        rg_row_bounds(p, nrow, mark, na0, nlen, nactive);
+        const int nnrow = row_at(idx + 2 * step);
+        const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        rgp_tile<RG, E>(p, p.Bq, acc, a0, len, lmax, err, k0, x0, k1, x1);
+        rg_load_a(p, na0 + gl, gl < nlen, k0, x0);
+        rg_load_a(p, na0 + RG + gl, RG + gl < nlen, k1, x1);
+        long long nout = 0, nout_end = 0;
+        if (nactive) {
+            nout = clampll(__ldg(p.Cp + nrow), 0, p.nnzC);
+            nout_end = clampll(__ldg(p.Cp + nrow + 1), nout, p.nnzC);
+        }
+        rg_emit<RG>(racc, p.W, 0, out, out_end, p.Ci, p.Cx, err);
+        __syncwarp();
+        if (active && gl == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
+        a0 = na0;
+        len = nlen;
+        active = nactive;
+        out = nout;
+        out_end = nout_end;
+        nrow = nnrow;
+    }
+}
+
 // Light rows only, in row groups; R = 32/RG accumulators of W + 8 floats per warp.
 // Launched behind k_numeric (which then skips light rows) with programmatic
 // dependent launch: its blocks may start while k_numeric's last blocks run.
 // Before exiting, each block waits for k_numeric to complete, so that work
-// queued after this kernel sees all of C.
-template <int RG>
+// queued after this kernel sees all of C.  PADDED: p.Bq is set (T = 1) and the
+// pipelined walk over the row-aligned copy runs (a separate instance keeps
+// each walk's registers to itself).
+template <int RG, bool PADDED>
 __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_nheavy, s_nrows;
@@ -673,8 +743,10 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     }
     __syncthreads();
     const long long* mark = p.s.stg_vals != nullptr ? p.s.flops : nullptr;
-    rg_light_rows<RG>(p, racc + (size_t)warp * R * (p.W + 8), s_nheavy + ((long long)blockIdx.x * nw + warp) * R, s_nrows,
-                      (long long)gridDim.x * nw * R, mark);
+    float* wacc = racc + (size_t)warp * R * (p.W + 8);
+    const long long idx0 = s_nheavy + ((long long)blockIdx.x * nw + warp) * R, step = (long long)gridDim.x * nw * R;
+    if constexpr (PADDED) rgp_light_rows<RG>(p, wacc, idx0, s_nrows, step, mark);
+    else rg_light_rows<RG>(p, wacc, idx0, s_nrows, step, mark);
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
@@ -701,8 +773,14 @@ __device__ __forceinline__ void rgcta_tile(const NumParams& p, const int4* P4, f
     const int c0 = t * p.W;
     const int Wd = p.d - c0 < p.W ? p.d - c0 : p.W;
     unsigned long long* err = &p.hdr->err;
-    if (p.Bq) rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err);  // T = 1
-    else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
+    if (p.Bq) {  // T = 1
+        const int gl = lane_id() % RG;
+        int k0, k1;
+        float x0, x1;
+        rg_load_a(p, a0 + gl, gl < len, k0, x0);
+        rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
+        rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err, k0, x0, k1, x1);
+    } else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
     else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
 }
 
@@ -1028,9 +1106,9 @@ static cudaError_t launch_g(const NumParams& p, int G, int warps, int sms, cudaS
     }
 }
 
-template <int RG>
-static cudaError_t launch_light(const NumParams& p, int warps, int sms, cudaStream_t st) {
-    const void* k = (const void*)k_numeric_light<RG>;
+template <int RG, bool PADDED>
+static cudaError_t launch_light_k(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    const void* k = (const void*)k_numeric_light<RG, PADDED>;
     const size_t smem = numeric_light_smem(p.W, warps, RG);
     cudaError_t e;
     if (smem == 0 || smem > 220 * 1024) return cudaErrorInvalidValue;
@@ -1048,7 +1126,12 @@ static cudaError_t launch_light(const NumParams& p, int warps, int sms, cudaStre
     lc.attrs = at;
     lc.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&lc, k_numeric_light<RG>, p);
+    return cudaLaunchKernelEx(&lc, k_numeric_light<RG, PADDED>, p);
+}
+
+template <int RG>
+static cudaError_t launch_light(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    return p.Bq ? launch_light_k<RG, true>(p, warps, sms, st) : launch_light_k<RG, false>(p, warps, sms, st);
 }
 
 cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
