@@ -173,7 +173,7 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     t.stage = force.stage ? force.stage : 2;
     t.pack_b = force.pack_b ? force.pack_b : 1;
     // row groups of 8 lanes (pairs) where four rows' accumulators fit well
-    // (W <= 256); one warp per light row for wider tiles
+    // (one tile, W <= 256); one warp per light row otherwise
     t.row_lanes = force.row_lanes ? force.row_lanes : 0;
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
@@ -189,7 +189,9 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
         return fail(TS_ERR_INVALID_ARG, "tuning: col_tile must be a multiple of 32 in [32, 4096]");
     if (t.col_tile > dpad) t.col_tile = (int)dpad;
-    if (t.row_lanes == 0) t.row_lanes = t.col_tile <= 256 ? 8 : 32;
+    // row groups only for a single tile of at most 256 columns: over several
+    // tiles B's segments are short and one warp per light row is faster
+    if (t.row_lanes == 0) t.row_lanes = (t.col_tile <= 256 && t.col_tile >= dpad) ? 8 : 32;
     if (t.cta_min_flops < 1) return fail(TS_ERR_INVALID_ARG, "tuning: cta_min_flops must be >= 1");
     if (t.warps_per_cta < 1 || t.warps_per_cta > 8)
         return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 8]");

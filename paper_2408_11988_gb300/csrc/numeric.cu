@@ -1162,6 +1162,21 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     if (Bq && (T != 1 || !values || cfg.row_lanes == 32)) return cudaErrorInvalidValue;
     p.Bq = Bq;
     if (values && (Bpk || Bq) && cfg.row_lanes != 32) {  // row groups need a packed copy
+        if (T > 1) {
+            // Over several column tiles a segment of B holds only d_tile/d of its
+            // row, so the block-wide sum of 32 slot accumulators per item and
+            // tile costs more than the item's products: split parts and heavy
+            // rows take the flag-and-atomic kernel, light rows the row groups.
+            NumParams ph = p;
+            ph.skip_light = 1;
+            if ((e = launch_g<true, true>(ph, G, w, cfg.sms, st))) return e;
+            switch (cfg.row_lanes) {
+                case 4: return launch_light<4>(p, w, cfg.sms, st);
+                case 8: return launch_light<8>(p, w, cfg.sms, st);
+                case 16: return launch_light<16>(p, w, cfg.sms, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
         switch (cfg.row_lanes) {
             case 4:
                 if ((e = launch_rgcta<4>(p, w, cfg.sms, st))) return e;
