@@ -72,6 +72,10 @@ __device__ __forceinline__ long long shfl64(long long v, int src) {
     return (long long)__shfl_sync(FULL, (unsigned long long)v, src);
 }
 
+__device__ __forceinline__ long long shfl64_down(long long v, int delta) {
+    return (long long)__shfl_down_sync(FULL, (unsigned long long)v, delta);
+}
+
 // owner_lane for 64-bit keys.
 __device__ __forceinline__ int owner_lane64(long long key, long long p) {
     int q = 0;

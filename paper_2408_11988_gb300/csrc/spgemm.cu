@@ -12,12 +12,13 @@ namespace ts {
 // ---------------------------------------------------------------------------
 // Row flops: flops_i = sum over stored (i,k) of nnz(B_k) (paper Sec. II-A:
 // flops = number of multiplications).  Rows of at most SHORT_ROW entries are
-// summed by one thread each.  Longer rows are cut into chunks of LONG_CHUNK
+// summed by the warp that holds them (32 rows per warp, their entries read
+// together).  Longer rows are cut into chunks of LONG_CHUNK
 // entries, queued as (row, chunk) items, and each chunk is summed by one
 // warp and added to its row with an atomic, so a row with very many entries
 // is spread over many warps.
 // ---------------------------------------------------------------------------
-constexpr int SHORT_ROW = 32;
+constexpr int SHORT_ROW = 256;
 constexpr int LONG_CHUNK = 256;
 
 // Row lengths of B clamped as SegWhole clamps them, as one int32 array: the
@@ -47,44 +48,66 @@ __global__ void __launch_bounds__(256) k_flops_rows(long long n, const long long
                                                     Seg segB, int nB, long long* __restrict__ flops,
                                                     long long* __restrict__ items, long long item_cap,
                                                     WsHeader* hdr) {
+    __shared__ long long s_f[256];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = lane_id();
     unsigned long long* err = &hdr->err;
     long long nchunks = 0;
-    long long a0 = 0, a1 = 0;
+    long long a0 = 0;
+    int len = 0;  // entries of this lane's row summed here (short rows)
     if (i < n) {
         a0 = clampll(__ldg(Ap + i), 0, nnzA);
-        a1 = clampll(__ldg(Ap + i + 1), a0, nnzA);
-        if (a1 - a0 <= SHORT_ROW) {
-            long long f = 0;
-#pragma unroll 4
-            for (long long e = a0; e < a1; ++e) {
-                const int k = __ldg(Ai + e);
-                if ((unsigned)k < (unsigned)nB) {
-                    long long s0;
-                    int len;
-                    segB(k, s0, len);
-                    f += len;
-                } else {
-                    atomicOr(err, ERR_A_COL);
-                }
-            }
-            flops[i] = f;
-        } else {
-            flops[i] = 0;
-            nchunks = (a1 - a0 + LONG_CHUNK - 1) / LONG_CHUNK;
-        }
+        const long long a1 = clampll(__ldg(Ap + i + 1), a0, nnzA);
+        if (a1 - a0 <= SHORT_ROW) len = (int)(a1 - a0);
+        else nchunks = (a1 - a0 + LONG_CHUNK - 1) / LONG_CHUNK;
     }
+    long long* wf = s_f + (threadIdx.x & ~31);
+    wf[lane] = 0;
+    __syncwarp();
+    // The short rows of the warp's 32 rows hold consecutive entries of A: they
+    // are numbered across the rows and read 32 at a time (coalesced); each
+    // entry's B row length goes to its row by a segmented sum over the lanes
+    // (the row of entry p is the last lane whose first number is <= p).
+    const int incl = warp_incl_scan(len), excl = incl - len;
+    const int total = __shfl_sync(FULL, incl, 31);
+    const long long shift = a0 - excl;  // entry of number p in row q: shift(q) + p
+    for (int p0 = 0; p0 < total; p0 += 32) {
+        const int p = p0 + lane;
+        const int q = owner_lane(excl, p);
+        const long long e = shfl64(shift, q) + p;
+        long long v = 0;
+        if (p < total) {
+            const int k = __ldg(Ai + e);
+            if ((unsigned)k < (unsigned)nB) {
+                long long s0;
+                int l;
+                segB(k, s0, l);
+                v = l;
+            } else {
+                atomicOr(err, ERR_A_COL);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {  // sum over this lane's run of equal q, from this lane on
+            const long long t = shfl64_down(v, o);
+            const int qo = __shfl_down_sync(FULL, q, o);
+            if (lane + o < 32 && qo == q) v += t;
+        }
+        const int qp = __shfl_up_sync(FULL, q, 1);
+        if (p < total && (lane == 0 || qp != q)) wf[q] += v;  // one lane per row and step
+        __syncwarp();
+    }
+    if (i < n) flops[i] = nchunks ? 0 : wf[lane];
     // reserve item slots: one atomic per warp
-    const int lane = lane_id();
-    long long incl = warp_incl_scan(nchunks);
-    const long long tot = __shfl_sync(FULL, incl, 31);
+    long long cincl = warp_incl_scan(nchunks);
+    const long long tot = __shfl_sync(FULL, cincl, 31);
     long long base = 0;
     if (tot > 0) {
         if (lane == 31) base = (long long)atomicAdd((unsigned long long*)&hdr->scratch[0], (unsigned long long)tot);
         base = __shfl_sync(FULL, base, 31);
     }
     for (long long c = 0; c < nchunks; ++c) {
-        const long long slot = base + incl - nchunks + c;
+        const long long slot = base + cincl - nchunks + c;
         if (slot < item_cap) items[slot] = (i << 24) | c;
         else atomicOr(err, ERR_CAPACITY);
     }
@@ -422,6 +445,35 @@ struct SymRowBody {
     }
 };
 
+// Marks set so far in the block's marks (all lanes of the calling warp get
+// the count; marks other warps are still setting may be missed, which only
+// delays the test below).
+template <bool FL>
+__device__ __forceinline__ int count_marks_warp(const unsigned* bm, int dw) {
+    const int words = FL ? 8 * dw : dw;
+    int c = 0;
+    for (int w = lane_id(); w < words; w += 32) c += __popc(((const volatile unsigned*)bm)[w]);
+    return warp_sum(c);
+}
+
+// A warp's chunks [first, a1) (stride 32 * warps) of a heavy row or split
+// part, marked into the block's marks.  Once all d columns are marked the
+// row's count is d whatever the remaining products, so the block stops: after
+// each of its chunks a warp counts the marks and raises *full when they
+// reach d, and every warp reads *full before its next chunk.  (Columns of B
+// in the skipped products are not range-checked here; the numeric pass checks
+// every entry of B.)
+template <int G, bool FL>
+__device__ __forceinline__ void sym_range(const SymParams& p, long long first, long long a1, long long stride,
+                                          SymVisit<FL>& vis, volatile int* full, unsigned long long* err) {
+    const bool test = p.dw <= 32;  // counting costs a pass over the marks: d <= 1024 only
+    for (long long e0 = first; e0 < a1; e0 += stride) {
+        if (*full) break;
+        sym_chunk<G, FL, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
+        if (test && count_marks_warp<FL>(vis.bm, p.dw) >= p.d && lane_id() == 0) *full = 1;
+    }
+}
+
 // Block total of per-thread counts (all threads get it).
 __device__ __forceinline__ int block_sum(int c, int* s_red) {
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
@@ -442,8 +494,10 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_red[32];
+    __shared__ int s_full;  // the current item's marks hold all d columns
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
     for (int i = tid; i < nw * p.slot; i += blockDim.x) smem_u[i] = 0;
+    if (tid == 0) s_full = 0;
     if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
@@ -463,9 +517,9 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         SplitItem it;
         while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
             SymVisit<FL> vis{p.Bi, smem_u, p.d, err, p.segB.nnzB};
-            for (long long e0 = it.e0 + 32LL * warp; e0 < it.e1; e0 += 32LL * nw)
-                sym_chunk<G, FL, SegWhole>(p, e0, (int)(it.e1 - e0 < 32 ? it.e1 - e0 : 32), vis, err);
+            sym_range<G, FL>(p, it.e0 + 32LL * warp, it.e1, 32LL * nw, vis, &s_full, err);
             __syncthreads();
+            if (tid == 0) s_full = 0;  // read again only after the next barrier
             unsigned* stg = p.s.stg_bits + (size_t)it.slot * p.dw;
             if (FL) {  // bytes -> bitmap words by ballot, one word per warp step
                 const unsigned char* fb = reinterpret_cast<const unsigned char*>(smem_u);
@@ -512,9 +566,9 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
         const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
         if (is_split_row(mark, row, a1 - a0)) continue;
         SymVisit<FL> vis{p.Bi, smem_u, p.d, err, p.segB.nnzB};
-        for (long long e0 = a0 + 32LL * warp; e0 < a1; e0 += 32LL * nw)
-            sym_chunk<G, FL, SegWhole>(p, e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), vis, err);
+        sym_range<G, FL>(p, a0 + 32LL * warp, a1, 32LL * nw, vis, &s_full, err);
         __syncthreads();
+        if (tid == 0) s_full = 0;  // read again only after the next barrier
         const int c = block_sum(count_and_clear<FL>(smem_u, p.dw, tid, blockDim.x), s_red);
         if (tid == 0) p.Cp_next[row] = c;
     }
