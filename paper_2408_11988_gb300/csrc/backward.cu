@@ -399,10 +399,25 @@ __global__ void __launch_bounds__(256, 5) k_backward_light(BwdParams p) {
         float x0, x1;
         brg_load_a(p, a0 + gl, gl < len, k0, x0);
         brg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
-        for (long long e = c0 + gl; e < c1; e += RG) {
-            const int c = __ldg(p.Ci + e);
-            if ((unsigned)c < (unsigned)p.d) gr[c] = __ldg(p.dC + e);
-            else atomicOr(err, ERR_C_ROW);
+        // the row of dC into the dense row, eight entries per lane in flight
+        // (the row is read once, from DRAM: a chain of single loads would
+        // wait out one memory latency per entry)
+        for (long long e = c0 + gl; e < c1; e += 8 * RG) {
+            int cc[8];
+            float vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long eu = e + u * RG;
+                cc[u] = eu < c1 ? __ldg(p.Ci + eu) : 0;
+                vv[u] = eu < c1 ? __ldg(p.dC + eu) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (e + u * RG < c1) {
+                    if ((unsigned)cc[u] < (unsigned)p.d) gr[cc[u]] = vv[u];
+                    else atomicOr(err, ERR_C_ROW);
+                }
+            }
         }
         long long sg;
         int L;

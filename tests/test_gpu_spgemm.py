@@ -172,6 +172,29 @@ def test_hub_row_and_dense_b():
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
+@pytest.mark.parametrize("d", [100, 1000, 1100])
+def test_heavy_rows_reaching_every_column(d):
+    # Heavy rows and split parts stop marking once all d columns are marked.
+    # Row 0 reaches every column only through its last entry's row of B;
+    # row 1 never reaches column d - 1; rows 2-3 saturate early (split rows).
+    n = 3000
+    rng = np.random.default_rng(80 + d)
+    B0 = synth.tall_skinny(n, d, 0.12, 81 + d)
+    Bp, Bc = B0.rowptr, B0.col
+    cols = [Bc[Bp[r]:Bp[r + 1]][Bc[Bp[r]:Bp[r + 1]] < d - 1] for r in range(n)]
+    cols[n - 1] = np.union1d(cols[n - 1], [d - 1])  # column d - 1 only in row n - 1 of B
+    B = _csr(n, d, cols, seed=83 + d)
+    rows = [np.arange(n), np.arange(n - 1), rng.choice(n - 1, 2500, replace=False), rng.choice(n - 1, 1500, replace=False)]
+    rows += [rng.choice(n, size=int(rng.integers(0, 40)), replace=False) for _ in range(n - 4)]
+    A = _csr(n, n, rows, seed=84 + d)
+    for t in (None, {"cta_min_flops": 1}, {"sym_group": 1}, {"sym_group": 16}, {"row_lanes": 32},
+              {"cta_min_flops": 64, "warps_per_cta": 2}):
+        Cp, _, _, _ = compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+        assert Cp[1] - Cp[0] == d and Cp[2] - Cp[1] == d - 1
+        compare_full(spgemm(dev(A).pattern(), dev(B).pattern(), semiring=OR_SELECT2ND, tuning=t), A, B,
+                     semiring=oracle.OR_SELECT2ND)
+
+
 @pytest.fixture(scope="module")
 def embed_full():
     return synth.rmat_embedding()
