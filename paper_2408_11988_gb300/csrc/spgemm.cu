@@ -620,7 +620,7 @@ __device__ __forceinline__ void symrg_mark(unsigned char* fl, const int c[4], in
 }
 
 template <int RG>
-__global__ void __launch_bounds__(256, 6) k_symbolic_light(SymParams p) {
+__global__ void __launch_bounds__(256, 5) k_symbolic_light(SymParams p) {
     extern __shared__ __align__(16) unsigned smem_u[];
     __shared__ long long s_nheavy, s_nrows;
     constexpr int R = 32 / RG;
@@ -656,14 +656,26 @@ __global__ void __launch_bounds__(256, 6) k_symbolic_light(SymParams p) {
         }
         const int len = (int)(a1 - a0);
         const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+        // chunks of RG entries, pipelined: while chunk e is marked, the
+        // segment of chunk e + RG (B's row pointers) and the column of
+        // chunk e + 2RG (A) are loaded
+        auto col_at = [&](int e) { return e + gl < len ? __ldg(p.Ai + a0 + e + gl) : -1; };
+        auto seg_of = [&](int k, long long& sg, int& L) {
+            sg = 0;
+            L = 0;
+            if (k == -1) return;
+            if ((unsigned)k < (unsigned)p.nB) p.segB(k, sg, L);
+            else atomicOr(err, ERR_A_COL);
+        };
+        int k1 = col_at(RG);
+        long long sg;
+        int L;
+        seg_of(col_at(0), sg, L);
         for (int e = 0; e < lmax; e += RG) {
-            long long sg = 0;
-            int L = 0;
-            if (e + gl < len) {
-                const int k = __ldg(p.Ai + a0 + e + gl);
-                if ((unsigned)k < (unsigned)p.nB) p.segB(k, sg, L);
-                else atomicOr(err, ERR_A_COL);
-            }
+            const int k2 = col_at(e + 2 * RG);
+            long long nsg;
+            int nL;
+            seg_of(k1, nsg, nL);
             const int nu = lmax - e < RG ? lmax - e : RG;
             for (int u = 0; u < nu; u += 2) {
                 const long long s0 = shfl64(sg, g * RG + u);
@@ -683,6 +695,9 @@ __global__ void __launch_bounds__(256, 6) k_symbolic_light(SymParams p) {
                     symrg_mark(fl, c1, p.d, err);
                 }
             }
+            sg = nsg;
+            L = nL;
+            k1 = k2;
         }
         __syncwarp();
         int c = 0;
