@@ -244,25 +244,30 @@ __global__ void __launch_bounds__(256) k_frontier_bits(long long n, int d, const
 template <int DWP>
 __device__ __forceinline__ void pull_or(const BfsParams& p, const unsigned* __restrict__ fb, long long e0,
                                         long long e1, int t0, int nt, unsigned acc[DWP], unsigned long long* err) {
+    // unrolled so that several neighbours' rows are in flight per thread; a
+    // bad column reads row 0 and contributes nothing (keep = 0)
+#pragma unroll 4
     for (long long e = e0 + t0; e < e1; e += nt) {
-        const int u = __ldg(p.Ai + e);
+        int u = __ldg(p.Ai + e);
+        unsigned keep = FULL;
         if ((unsigned)u >= (unsigned)p.nF) {
             atomicOr(err, ERR_A_COL);
-            continue;
+            u = 0;
+            keep = 0u;
         }
         const unsigned* r = fb + (long long)u * DWP;
         if constexpr (DWP >= 4) {
 #pragma unroll
             for (int m = 0; m < DWP; m += 4) {
                 const uint4 x = __ldg(reinterpret_cast<const uint4*>(r + m));
-                acc[m] |= x.x;
-                acc[m + 1] |= x.y;
-                acc[m + 2] |= x.z;
-                acc[m + 3] |= x.w;
+                acc[m] |= x.x & keep;
+                acc[m + 1] |= x.y & keep;
+                acc[m + 2] |= x.z & keep;
+                acc[m + 3] |= x.w & keep;
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < DWP; ++m) acc[m] |= __ldg(r + m);
+            for (int m = 0; m < DWP; ++m) acc[m] |= __ldg(r + m) & keep;
         }
     }
 }
@@ -345,7 +350,7 @@ __device__ __forceinline__ void pull_parents(const BfsParams& p, const unsigned*
 }
 
 template <int DWP>
-__global__ void __launch_bounds__(256) k_msbfs_pull(BfsParams p, const unsigned* __restrict__ fb) {
+__global__ void __launch_bounds__(256, 6) k_msbfs_pull(BfsParams p, const unsigned* __restrict__ fb) {
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ unsigned s_or[DWP];
     const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
