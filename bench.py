@@ -340,7 +340,7 @@ def main():
                        "nnz_A": nnzA, "nnz_B": B.nnz, "nnz_C": nnzC, "products": F,
                        "tuning": plan.tuning, "l2": "inputs larger than L2 (A+B+C > 129 MB)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "hbm", "kernel": "numeric pass (k_pack_b_rows + k_numeric_rgcta + k_numeric_light)",
+            "roofline": {"bound": "hbm", "kernel": "numeric pass (every kernel of ts_spgemm_numeric: packing of B, accumulating kernels)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "bytes_per_launch": num_bytes, "traffic": _traffic(args.workload),
