@@ -89,8 +89,9 @@ typedef struct ts_csr_desc {
  *                 multiple of 32).  Below d, B's columns are processed in
  *                 tiles of this width and each output row is the
  *                 concatenation of its tiles (B column tiling).
- *  cta_min_flops  rows with at least this many products (rounded up to a
- *                 power of two) run CTA-per-row; lighter rows warp-per-row.
+ *  cta_min_flops  rows with at least this many products (rounded up to the
+ *                 next boundary of the row classes, eighths of an octave of
+ *                 products) run CTA-per-row; lighter rows warp-per-row.
  *  warps_per_cta  warps per thread block (1..8).
  *  hash_slots     slots of a warp's hash table (power of two, >= 64).
  *  group          how a warp spreads the products of 32 entries of A over its
@@ -106,7 +107,9 @@ typedef struct ts_csr_desc {
  *                 TS_ACC_COPIES needs 8, 16 or 32 (32/group copies per warp);
  *                 with 1 or 4 it picks from B's mean row length.
  *  pack_b         1 = gather B from a packed (column, value) copy built in the
- *                 workspace at each call, 2 = from B's own arrays.
+ *                 workspace at each call (for the row-group numeric kernels
+ *                 over one column tile: a copy whose rows start on 16-byte
+ *                 groups), 2 = from B's own arrays.
  *  sym_group,     the same choice as `group` for the symbolic pass and for
  *  bwd_group      the backward pass (each pass may prefer its own).
  *  row_lanes      numeric pass (plus-times, pack_b = 1, dense accumulator):
@@ -114,9 +117,12 @@ typedef struct ts_csr_desc {
  *                 row groups, 32/row_lanes rows per warp in lockstep, each
  *                 with its own accumulator and no atomics (4: four entries
  *                 of B per lane, 8 and 16: two), in a kernel launched right
- *                 behind the one for the heavy rows.  Any value but 32 also
- *                 runs the symbolic pass's light rows in row groups of four
- *                 lanes (d <= 512, B.col 16-byte aligned).
+ *                 behind the one for the heavy rows; with one column tile the
+ *                 heavy rows and split parts run in row groups too (slot
+ *                 accumulators summed by the block).  Default: 8 for one
+ *                 tile of at most 256 columns, else 32.  Any value but 32
+ *                 also runs the symbolic pass's light rows in row groups of
+ *                 four lanes (d <= 512, B.col 16-byte aligned).
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.
