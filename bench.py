@@ -343,7 +343,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "numeric pass (every kernel of ts_spgemm_numeric: packing of B, accumulating kernels)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "bytes_per_launch": num_bytes, "traffic": _traffic(args.workload),
+                         "bytes_per_launch": num_bytes, "traffic": None if args.scale else _traffic(args.workload),
                          "column_tiles": tiles, "compulsory_bytes": comp_bytes,
                          "compulsory_frac": round(comp_bytes / (num_ms * 1e-3) / 1e9 / peak, 4)},
             "phases_ms": {"symbolic": round(statistics.mean(sym), 4), "numeric": round(num_ms, 4),
