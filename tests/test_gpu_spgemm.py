@@ -11,7 +11,7 @@ import torch
 import oracle
 import synth
 from synth import CSR
-from _cmp import compare_full, compare_rows, assert_pattern_equal, assert_values_close
+from _cmp import REL, compare_full, compare_rows, assert_pattern_equal, assert_values_close
 
 pytestmark = pytest.mark.gpu
 
@@ -95,6 +95,36 @@ def test_rmat_tiled_d1024():
     for t in (None, {"col_tile": 256}, {"col_tile": 256, "cta_min_flops": 32}, {"accum": ACC_HASH},
               {"accum": ACC_COPIES}, {"accum": ACC_COPIES, "col_tile": 256, "cta_min_flops": 32}):
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
+
+
+def test_tiled_full_size_sampled():
+    # the large tiled product at its full size and in the launch configuration
+    # the benchmark times (R-MAT scale 24, d = 1024, 1 %, tiles of 256):
+    # sampled rows of C, of dA and of dB against the oracle
+    A, B = synth.rmat_embedding(scale=24, edge_factor=16, d=1024, density=0.01, b_values="uniform",
+                                seed=synth.BASE_SEED + 5)
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd, tuning={"col_tile": 256})
+    C = plan.forward(Ad, Bd)
+    rp = C.rowptr.cpu().numpy()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= B.ncols)
+    rng = np.random.default_rng(24)
+    deg = np.diff(A.rowptr)
+    rows = np.concatenate([np.argsort(deg)[-8:], rng.choice(A.nrows, 1000, replace=False)])
+    compare_rows(C, A, B, rows)
+    dC = synth.grad_output(C.nnz, 25)
+    dA, dB = plan.backward(Ad, Bd, C, torch.as_tensor(dC, device="cuda"))
+    col = C.col.cpu().numpy()
+    dC = dC.astype(np.float64)
+    arows = np.concatenate([np.argsort(deg)[-4:], rng.choice(A.nrows, 500, replace=False)])
+    sA, bA = oracle.backward_dA_rows(A, B, rp, col, dC, arows)
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in arows])
+    assert np.all(np.abs(dA.cpu().numpy()[idx] - sA) <= REL * bA)
+    indeg = np.bincount(A.col, minlength=A.nrows)
+    krows = np.unique(np.concatenate([np.argsort(indeg)[-4:], rng.choice(B.nrows, 200, replace=False)]))
+    sB, bB = oracle.backward_dB_rows(A, B, rp, col, dC, krows)
+    idx = np.concatenate([np.arange(B.rowptr[k], B.rowptr[k + 1]) for k in krows])
+    assert np.all(np.abs(dB.cpu().numpy()[idx] - sB) <= REL * bB)
 
 
 def test_large_d_hash_and_tiles():
