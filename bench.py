@@ -70,9 +70,9 @@ def _kernel_sources_hash():
 
 def _traffic(workload):
     """DRAM bytes per launch of the numeric pass, from the JSON block of
-    profiles/dram_traffic.md, or None if that capture was taken on different
+    profiles/dram_traffic_embed_s22.md, or None if that capture was taken on different
     kernel sources."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    p = os.path.join(ROOT, "profiles", "dram_traffic_embed_s22.md")
     if not os.path.exists(p):
         return None
     with open(p) as f:
