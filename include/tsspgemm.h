@@ -410,17 +410,19 @@ TS_API ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tun
  * The caller passes A, B and C as for the other calls: C->rowptr (n+1 int64)
  * and C->col / C->val with room for C->nnz entries (the capacity).  On return
  * *nnzC_host holds nnz(C); if it exceeds the capacity the call returns
- * TS_ERR_CAPACITY after writing C->rowptr only.  Products whose workspace
- * (ts_workspace_size) exceeds the scratch are rejected with TS_ERR_UNSUPPORTED
- * before anything is enqueued.  The call synchronises `stream` once (to read
- * nnz(C)) and calls no allocating function.
+ * TS_ERR_CAPACITY after writing C->rowptr only.  Products whose forward
+ * workspace (the symbolic and numeric passes of the plan's current tuning;
+ * ts_workspace_size may be larger, since it also covers the autotuner's
+ * trials) exceeds the scratch are rejected with TS_ERR_UNSUPPORTED before
+ * anything is enqueued.  The call synchronises `stream` once (to read
+ * nnz(C)) and calls no allocating function.  Because of that synchronisation
+ * it cannot be called while `stream` is being captured into a CUDA graph.
  *
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one scratch
- * array and each call re-initialises what it needs, so calls whose work
- * overlaps on the GPU (different streams, different threads) race: serialise
- * them.
+ * (cudaGetSymbolAddress), which needs that device to be current.  All calls
+ * on a device share the one scratch array and each call re-initialises what
+ * it needs, so calls whose work overlaps on the GPU (different streams,
+ * different threads) race: serialise them.
  */
 TS_API size_t ts_noalloc_scratch_bytes(void);
 TS_API ts_status ts_spgemm_forward_noalloc(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,

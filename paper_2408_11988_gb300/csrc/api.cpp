@@ -345,6 +345,14 @@ extern "C" ts_status ts_workspace_size(const ts_plan* plan, size_t* bytes) {
     return ok();
 }
 
+namespace ts {
+// Workspace of the symbolic and numeric passes under the plan's current
+// tuning (no autotuner regions); used by ts_spgemm_forward_noalloc.
+size_t forward_workspace_bytes(const ts_plan* plan) {
+    return plan_layout(plan->n, plan->d, plan->cur, plan->nnzA, plan->nnzB).total;
+}
+}  // namespace ts
+
 static ts_status check_operands(const ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                 void* ws, size_t ws_bytes, const Layout& L, const char* fn) {
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
@@ -587,6 +595,14 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     // coordinate descent from the heuristic default: each field in turn takes
     // the value that times fastest with the others fixed; fields fixed by the
     // plan's `force` are not varied
+    // errors the symbolic pass found in the operands end the search at once;
+    // after that the error word is cleared before every trial and read after
+    // it, so that a candidate whose kernels flagged a failure (a hash table
+    // too small for a row, which skips the row and so also times faster) is
+    // dropped instead of chosen, and does not fail the final check
+    s = read_errors(ws, L0, st, fn);
+    if (s != TS_OK) return s;
+    unsigned long long* err_word = &((WsHeader*)((char*)ws + L0.hdr))->err;
     cudaEvent_t e0, e1;
     TS_CUDA(cudaEventCreate(&e0), fn);
     TS_CUDA(cudaEventCreate(&e1), fn);
@@ -599,6 +615,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         const Layout L = plan_layout(plan->n, plan->d, cand, A->nnz, B->nnz);
         if (L.total > ws_bytes) return TS_OK;  // does not fit the caller's workspace
         plan->cur = cand;
+        TS_CUDA(cudaMemsetAsync(err_word, 0, sizeof *err_word, st), fn);
         float tot = 0.0f;
         for (int r = 0; r <= reps; ++r) {  // the first run warms up
             TS_CUDA(cudaEventRecord(e0, st), fn);
@@ -614,6 +631,10 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
             TS_CUDA(cudaEventElapsedTime(&ms, e0, e1), fn);
             if (r > 0) tot += ms;
         }
+        unsigned long long err = 0;
+        TS_CUDA(cudaMemcpyAsync(&err, err_word, sizeof err, cudaMemcpyDeviceToHost, st), fn);
+        TS_CUDA(cudaStreamSynchronize(st), fn);
+        if (err) return TS_OK;  // this candidate cannot run the product: skip it
         const float avg = tot / reps;
         if (avg < best_ms) {
             best_ms = avg;
@@ -688,6 +709,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     if (chosen) *chosen = best;
     // leave C holding the product of the chosen tuning
     const Layout Lb = plan_layout(plan->n, plan->d, best, A->nnz, B->nnz);
+    TS_CUDA(cudaMemsetAsync(err_word, 0, sizeof *err_word, st), fn);
     s = run_numeric(plan, A, B, C, ws, Lb, st, fn);
     if (s != TS_OK) return s;
     s = read_errors(ws, Lb, st, fn);

@@ -9,7 +9,11 @@
 // table and its slot is cleared.  Heavy rows (the CTA schedule) use one table
 // of (warps * S) slots and one bitmap for the whole block.  Rows whose
 // distinct columns do not fit raise ERR_HASH_FULL instead of being dropped
-// silently.
+// silently.  A block row with more distinct columns than the block table
+// holds at 75% load (known beforehand from C's row pointers) runs in column
+// windows: one walk over its products marks the bitmap only, then for each
+// run of bitmap words whose columns fit the table, a walk inserts only the
+// columns of that window and the window is read out before the next one.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -51,13 +55,19 @@ struct HashVisit {
     unsigned mask;
     int d;
     unsigned long long* err;
+    // 0: bitmap and table; 1: bitmap only; 2: table only, columns [lo, hi)
+    int mode = 0, lo = 0, hi = 0;
     __device__ __forceinline__ void insert(int c, float v) {
         if ((unsigned)c >= (unsigned)d) {
-            atomicOr(err, ERR_B_COL);
+            if (mode != 2) atomicOr(err, ERR_B_COL);
             return;
         }
-        atomicOr(bm + (c >> 5), 1u << (c & 31));
-        if (!VALUES) return;
+        if (mode == 2) {
+            if (c < lo || c >= hi) return;
+        } else {
+            atomicOr(bm + (c >> 5), 1u << (c & 31));
+        }
+        if (!VALUES || mode == 1) return;
         unsigned h = hash_slot(c, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
             const int k = atomicCAS(keys + h, -1, c);
@@ -108,14 +118,14 @@ __device__ __forceinline__ float find_slot(const int* keys, const float* vals, u
 // block cooperate word-range by word-range (each warp takes a contiguous
 // range of bitmap words; ranges are ordered by a block scan).
 template <bool VALUES, bool CTA>
-__device__ __forceinline__ void hash_emit(int* keys, float* vals, unsigned* bm, unsigned mask, int dw,
+__device__ __forceinline__ void hash_emit(int* keys, float* vals, unsigned* bm, unsigned mask, int w0, int w1,
                                           long long out, long long out_end, int* Ci, float* Cx,
                                           int* s_warp_tot, unsigned long long* err) {
     const int lane = lane_id();
     const int nw = CTA ? (blockDim.x >> 5) : 1;
     const int w = CTA ? warp_id() : 0;
-    const int per = (dw + nw - 1) / nw;
-    const int wb = w * per, we = wb + per < dw ? wb + per : dw;
+    const int per = (w1 - w0 + nw - 1) / nw;
+    const int wb = w0 + w * per < w1 ? w0 + w * per : w1, we = wb + per < w1 ? wb + per : w1;
     // count of this warp's range
     long long base = out;
     if (CTA) {
@@ -169,30 +179,94 @@ __device__ __forceinline__ void hash_emit(int* keys, float* vals, unsigned* bm, 
     }
 }
 
+// The products of entries [a0, a1) of A through visitor vis (the block's
+// warps take 32-entry chunks in turn).
+template <bool VALUES, bool CTA>
+__device__ __forceinline__ void hash_walk(const HashParams& p, long long a0, long long a1, HashVisit<VALUES>& vis,
+                                          unsigned long long* err) {
+    const int nw = blockDim.x >> 5;
+    const long long first = CTA ? a0 + 32LL * warp_id() : a0;
+    const long long stride = CTA ? 32LL * nw : 32LL;
+    const SegWhole seg{p.Bp, p.nnzB, p.d};
+    for (long long e0 = first; e0 < a1; e0 += stride)
+        expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, VALUES ? p.Ax : nullptr, p.nB, seg,
+                     vis, err);
+}
+
+// A block row wider than the table (see the top of the file): bitmap walk,
+// then per window of bitmap words holding at most `cap` columns a table walk
+// restricted to the window and its read-out.  s_win[0..1]: window end and
+// its column count, chosen by warp 0.
+template <bool VALUES>
+__device__ __noinline__ void hash_row_windows(const HashParams& p, long long a0, long long a1, long long out,
+                                              long long out_end, int* keys, float* vals, unsigned* bm,
+                                              unsigned mask, int* s_warp_tot, int* s_win) {
+    unsigned long long* err = &p.hdr->err;
+    const unsigned cap = (mask + 1) - (mask + 1) / 4;  // >= 48 columns, more than one word
+    HashVisit<VALUES> vis{p.Bi, p.Bx, keys, vals, bm, mask, p.d, err};
+    vis.mode = 1;
+    hash_walk<VALUES, true>(p, a0, a1, vis, err);
+    __syncthreads();
+    const int lane = lane_id();
+    long long pos = out;
+    for (int wlo = 0; wlo < p.dw;) {
+        if (warp_id() == 0) {
+            int whi = wlo;
+            unsigned tot = 0;
+            for (;;) {  // extend the window 32 words at a time while its columns fit
+                const int x = whi + lane;
+                const unsigned c = x < p.dw ? (unsigned)__popc(bm[x]) : 0u;
+                const unsigned inc = (unsigned)warp_incl_scan((int)c);
+                // inc grows with the lane, so the lanes that fit form a prefix
+                const unsigned fit = __ballot_sync(FULL, x < p.dw && tot + inc <= cap);
+                const int nfit = __popc(fit);
+                if (nfit > 0) tot += __shfl_sync(FULL, inc, nfit - 1);
+                whi += nfit;
+                if (nfit < 32 || whi >= p.dw) break;
+            }
+            if (lane == 0) {
+                s_win[0] = whi;
+                s_win[1] = (int)tot;
+            }
+        }
+        __syncthreads();
+        const int whi = s_win[0], cnt = s_win[1];
+        vis.mode = 2;
+        vis.lo = 32 * wlo;
+        vis.hi = 32 * whi;
+        hash_walk<VALUES, true>(p, a0, a1, vis, err);
+        __syncthreads();  // (also: every thread has read s_win before warp 0 rewrites it)
+        hash_emit<VALUES, true>(keys, vals, bm, mask, wlo, whi, pos, out_end, p.Ci, p.Cx, s_warp_tot, err);
+        pos += cnt;
+        wlo = whi;
+    }
+    if (threadIdx.x == 0 && pos != out_end) atomicOr(err, ERR_C_ROW);
+}
+
 template <bool VALUES, bool CTA>
 __device__ __forceinline__ void hash_row(const HashParams& p, int row, int* keys, float* vals, unsigned* bm,
-                                         unsigned mask, int* s_warp_tot) {
+                                         unsigned mask, int* s_warp_tot, int* s_win) {
     unsigned long long* err = &p.hdr->err;
     const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
     const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
     const long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
     const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
     if (VALUES && out_end - out > (long long)(mask + 1) - (long long)(mask + 1) / 4) {
-        // more distinct columns than the table holds at 75% load
-        if (CTA ? threadIdx.x == 0 : lane_id() == 0) atomicOr(err, ERR_HASH_FULL);
+        // more distinct columns than the table holds at 75% load: a block
+        // row runs in column windows; a warp row never gets here (warps take
+        // only rows with fewer products than 3/4 of their table)
+        if (CTA) {
+            hash_row_windows<VALUES>(p, a0, a1, out, out_end, keys, vals, bm, mask, s_warp_tot, s_win);
+        } else if (lane_id() == 0) {
+            atomicOr(err, ERR_HASH_FULL);
+        }
         return;
     }
-    const int nw = blockDim.x >> 5;
-    const long long first = CTA ? a0 + 32LL * warp_id() : a0;
-    const long long stride = CTA ? 32LL * nw : 32LL;
     HashVisit<VALUES> vis{p.Bi, p.Bx, keys, vals, bm, mask, p.d, err};
-    const SegWhole seg{p.Bp, p.nnzB, p.d};
-    for (long long e0 = first; e0 < a1; e0 += stride)
-        expand_chunk(e0, (int)(a1 - e0 < 32 ? a1 - e0 : 32), p.Ai, VALUES ? p.Ax : nullptr, p.nB, seg,
-                     vis, err);
+    hash_walk<VALUES, CTA>(p, a0, a1, vis, err);
     if (CTA) __syncthreads();
     else __syncwarp();
-    hash_emit<VALUES, CTA>(keys, vals, bm, mask, p.dw, out, out_end, p.Ci, p.Cx, s_warp_tot, err);
+    hash_emit<VALUES, CTA>(keys, vals, bm, mask, 0, p.dw, out, out_end, p.Ci, p.Cx, s_warp_tot, err);
 }
 
 template <bool VALUES>
@@ -200,6 +274,7 @@ __global__ void __launch_bounds__(1024) k_numeric_hash(HashParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item, s_nheavy, s_nrows;
     __shared__ int s_warp_tot[33];
+    __shared__ int s_win[2];
     const int nw = blockDim.x >> 5, warp = warp_id(), tid = threadIdx.x;
     // layout: keys [nw*S] int, vals [nw*S] float, bitmaps [nw*dw] unsigned
     const int totS = nw * p.S;
@@ -225,14 +300,14 @@ __global__ void __launch_bounds__(1024) k_numeric_hash(HashParams p) {
         const long long h = s_item;
         __syncthreads();
         if (h >= nheavy) break;
-        hash_row<VALUES, true>(p, p.perm[h], keys, vals, bms, (unsigned)(totS - 1), s_warp_tot);
+        hash_row<VALUES, true>(p, p.perm[h], keys, vals, bms, (unsigned)(totS - 1), s_warp_tot, s_win);
     }
     int* wk = keys + warp * p.S;
     float* wv = vals + warp * p.S;
     unsigned* wb = bms + warp * p.dw;
     for (long long idx = nheavy + (long long)blockIdx.x * nw + warp; idx < nrows;
          idx += (long long)gridDim.x * nw)
-        hash_row<VALUES, false>(p, p.perm[idx], wk, wv, wb, (unsigned)(p.S - 1), nullptr);
+        hash_row<VALUES, false>(p, p.perm[idx], wk, wv, wb, (unsigned)(p.S - 1), nullptr, nullptr);
 }
 
 size_t numeric_hash_smem(int slots, int warps, bool values) {

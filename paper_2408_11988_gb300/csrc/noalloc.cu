@@ -17,6 +17,7 @@
 
 namespace ts {
 ts_status set_last_error(ts_status s, const char* msg);
+size_t forward_workspace_bytes(const ts_plan* plan);
 }
 
 namespace {
@@ -62,9 +63,10 @@ extern "C" ts_status ts_spgemm_forward_noalloc(ts_plan* plan, const ts_csr_desc*
                                                const ts_csr_desc* C, int64_t* nnzC_host, void* stream) {
     if (!plan || !A || !B || !C || !C->rowptr || !nnzC_host)
         return ts::set_last_error(TS_ERR_INVALID_ARG, "ts_spgemm_forward_noalloc: NULL argument");
-    size_t need = 0;
-    ts_status s = ts_workspace_size(plan, &need);
-    if (s != TS_OK) return s;
+    // the layout of the symbolic and numeric passes alone (without the
+    // autotuner's trial regions that ts_workspace_size also covers)
+    const size_t need = ts::forward_workspace_bytes(plan);
+    ts_status s = TS_OK;
     if (need > kScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,

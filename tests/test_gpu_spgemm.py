@@ -367,3 +367,43 @@ def test_unaligned_b_columns_and_b_tail(tuning):
     assert Bu.col.data_ptr() % 16 != 0
     for Bx in (Bd, Bu):
         compare_full(spgemm(dev(A), Bx, tuning=tuning), A, B)
+
+
+def _wide_hub_product(seed=93, n=4096, d=8192, hub=7, hub_len=3000):
+    """d = 8192 (hash accumulator) with one hub row of A whose row of C holds
+    about 7,700 distinct columns, more than a block's hash table holds at
+    75% load with the default 8 warps x 1024 slots (6,144)."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        k = hub_len if i == hub else 8
+        rows.append(np.sort(rng.choice(n, k, replace=False)))
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    A = CSR(n, n, rp, np.concatenate(rows).astype(np.int32), rng.random(int(rp[-1]), dtype=np.float32))
+    B = synth.tall_skinny(n, d, 8.0 / d, seed + 1)
+    B.val = synth.uniform(B.nnz, seed + 2)
+    return A, B
+
+
+@pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 2}, {"hash_slots": 64, "warps_per_cta": 1},
+                                    {"hash_slots": 256, "warps_per_cta": 4}])
+def test_hash_block_row_wider_than_table(tuning):
+    A, B = _wide_hub_product()
+    t = dict(tuning or {}, accum=ACC_HASH)
+    C = spgemm(dev(A), dev(B), tuning=t)
+    Cp, _, _, _ = compare_full(C, A, B)
+    assert Cp[8] - Cp[7] > 6144  # the hub row really is wider than the default table
+
+
+def test_autotune_wide_hub_row():
+    # the autotuner tries hash tables of several sizes on a product with a row
+    # wider than some of them; it must finish and leave the right product
+    A, B = _wide_hub_product(seed=94)
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    C = plan.forward(Ad, Bd)
+    plan.autotune(Ad, Bd, C, reps=1)
+    plan.check()
+    compare_full(C, A, B)
+    compare_full(plan.forward(Ad, Bd), A, B)

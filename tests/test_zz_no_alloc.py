@@ -80,3 +80,25 @@ def test_noalloc_reports_capacity_and_size_limits():
     assert st == N.TS_ERR_UNSUPPORTED and "scratch" in N.last_error()
     N.lib().ts_plan_destroy(h)
     assert int(N.lib().ts_noalloc_scratch_bytes()) == 32 << 20
+
+
+def test_noalloc_size_check_counts_only_the_forward_layout():
+    """A product whose autotuner-covering workspace (ts_workspace_size) is
+    larger than the built-in scratch while the forward passes' own layout fits
+    must still run: the size check counts the forward layout only."""
+    A, B = synth.er_product(n=86016, k=8, d=256, density=0.05, seed=92)
+    Ad, Bd = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+    plan = Plan(Ad, Bd)
+    cover = ctypes.c_size_t(0)
+    assert N.lib().ts_workspace_size(plan.handle, ctypes.byref(cover)) == N.TS_OK
+    assert cover.value > int(N.lib().ts_noalloc_scratch_bytes())
+    ref = plan.forward(Ad, Bd)
+    rp_ref, col_ref, val_ref = ref.to_host()
+    st, nnz, C = _noalloc(plan, Ad, Bd, capacity=ref.nnz)
+    assert st == N.TS_OK, N.last_error()
+    assert nnz == ref.nnz
+    rp, col, val = C.to_host()
+    np.testing.assert_array_equal(rp, rp_ref)
+    np.testing.assert_array_equal(col, col_ref)
+    Cp, Ci, Cx, Cb = oracle.spgemm(A, B)
+    assert np.all(np.abs(val.astype(np.float64) - Cx) <= REL * Cb)
