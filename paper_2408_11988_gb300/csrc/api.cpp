@@ -180,8 +180,9 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
         return fail(TS_ERR_INVALID_ARG, "tuning: group, sym_group and bwd_group must be 1, 2, 4, 8, 16 or 32");
     if (t.pack_b != 1 && t.pack_b != 2) return fail(TS_ERR_INVALID_ARG, "tuning: pack_b must be 1 or 2");
-    if (t.row_lanes != 0 && t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 && t.row_lanes != 32)
-        return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes must be 4, 8, 16 or 32");
+    if (t.row_lanes != 0 && t.row_lanes != 1 && t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 &&
+        t.row_lanes != 32)
+        return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes must be 1, 4, 8, 16 or 32");
     if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES)
         return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH or TS_ACC_COPIES");
     if (t.accum == TS_ACC_COPIES && dpad > 4096)
@@ -191,7 +192,17 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     if (t.col_tile > dpad) t.col_tile = (int)dpad;
     // row groups only for a single tile of at most 256 columns: over several
     // tiles B's segments are short and one warp per light row is faster
-    if (t.row_lanes == 0) t.row_lanes = (t.col_tile <= 256 && t.col_tile >= dpad) ? 8 : 32;
+    // wide rows (one tile of 256 < W <= 1024 columns): one shared accumulator
+    // per warp with occupancy bits, so that A is walked once and only the
+    // occupied columns are read out
+    const bool one_tile = t.col_tile >= dpad;
+    if (t.row_lanes == 0) {
+        if (one_tile && t.col_tile <= 256) t.row_lanes = 8;
+        else if (one_tile && t.col_tile <= 1024) t.row_lanes = 1;
+        else t.row_lanes = 32;
+    }
+    if (t.row_lanes == 1 && !(one_tile && t.col_tile <= 1024))
+        return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes = 1 needs one column tile of at most 1024 columns");
     if (t.cta_min_flops < 1) return fail(TS_ERR_INVALID_ARG, "tuning: cta_min_flops must be >= 1");
     if (t.warps_per_cta < 1 || t.warps_per_cta > 8)
         return fail(TS_ERR_INVALID_ARG, "tuning: warps_per_cta must be in [1, 8]");
@@ -471,7 +482,7 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
         }
         if (copies) {
             // light rows in row groups behind the copies kernel when they fit
-            const bool rg = cfg.row_lanes != 32 && bpk &&
+            const bool rg = cfg.row_lanes != 32 && cfg.row_lanes != 1 && bpk &&
                             numeric_light_smem(L.W, cfg.warps_per_cta, cfg.row_lanes) <= 220 * 1024;
             TS_CUDA(launch_numeric_copies(dA, dB, plan->d, L.W, L.T, tp, bpk, cg, sc, cfg,
                                           (const long long*)C->rowptr, C->col, (float*)C->val, C->nnz, st, rg),
@@ -687,7 +698,11 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                 break;
             case 8:
                 if (plan->force.row_lanes || !vals) break;
-                for (int rl : {32, 4, 8, 16}) { c.row_lanes = rl; cands.push_back(c); }
+                for (int rl : {32, 4, 8, 16, 1}) {
+                    if (rl == 1 && !(best.col_tile >= dpad && best.col_tile <= 1024)) continue;
+                    c.row_lanes = rl;
+                    cands.push_back(c);
+                }
                 break;
             case 6:
                 if (plan->force.stage) break;

@@ -48,7 +48,8 @@ struct LaunchCfg {
     int cta_class = 14;      // rows of flops class >= this run CTA-per-row
     int sms = 152;
     int group = 1;           // lanes per A entry (1 = flattened products)
-    int row_lanes = 32;      // numeric light rows: 32 = a warp per row, 4/8/16 = row groups
+    int row_lanes = 32;      // numeric light rows: 32 = a warp per row, 4/8/16 = row groups,
+                             // 1 = a warp per row on one shared accumulator (wide kernel)
 };
 
 // Bytes of the scan partials for n values.
@@ -123,6 +124,9 @@ cudaError_t launch_numeric_light_rows(const DevCsr& A, const DevCsr& B, long lon
 // Dynamic shared memory of the row-group light-row kernel (0: bad row_lanes).
 size_t numeric_light_smem(int W, int warps, int row_lanes);
 size_t numeric_rgcta_smem(int W, int warps, int row_lanes);
+// Dynamic shared memory of the wide kernel (row_lanes = 1: one accumulator
+// of W <= 1024 floats and its occupancy bitmap per warp).
+size_t numeric_wide_smem(int W, int warps);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).

@@ -538,15 +538,35 @@ __device__ __forceinline__ void rgp_load(const int4* __restrict__ Q, unsigned g,
     if constexpr (E == 4) v1 = __ldg(Q + (size_t)g * 2 + 1);
 }
 
-template <int E>
-__device__ __forceinline__ void rgp_apply(float* acc, const int4& v0, const int4& v1, float a, unsigned W) {
+// How a slot adds a product into its accumulator.  AddPlain: the slot's own
+// accumulator (row groups): a column outside [0, W) (a pad) goes to the
+// spare column W.  AddShared: one accumulator shared by several slots (see
+// the wide kernel below): pads are skipped, the value is added with a
+// shared-memory float reduction and the column's occupancy bit is set.
+struct AddPlain {
+    float* acc;
+    __device__ __forceinline__ void operator()(int c, unsigned W, float v) const {
+        rg_add(acc, (unsigned)c < W ? c : (int)W, v);
+    }
+};
+
+struct AddShared {
+    float* acc;
+    unsigned* bm;
+    __device__ __forceinline__ void operator()(int c, unsigned W, float v) const {
+        if ((unsigned)c < W) {
+            atomicAdd(acc + c, v);
+            atomicOr(bm + (c >> 5), 1u << (c & 31));
+        }
+    }
+};
+
+template <int E, class Add>
+__device__ __forceinline__ void rgp_apply(const Add& add, const int4& v0, const int4& v1, float a, unsigned W) {
     const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
     const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
 #pragma unroll
-    for (int u = 0; u < E; ++u) {
-        const unsigned c = (unsigned)cs[u] < W ? (unsigned)cs[u] : W;
-        rg_add(acc, (int)c, a * __int_as_float(bs[u]));
-    }
+    for (int u = 0; u < E; ++u) add(cs[u], W, a * __int_as_float(bs[u]));
 }
 
 // rg_tile on the row-aligned copy: chunks of RG entries of every slot's row,
@@ -554,8 +574,8 @@ __device__ __forceinline__ void rgp_apply(float* acc, const int4& v0, const int4
 // group load while the current segment is accumulated).  The caller has
 // loaded the first two chunks of A (k0/x0: entry a0 + gl, k1/x1: entry
 // a0 + RG + gl, as rg_load_a gives them).
-template <int RG, int E>
-__device__ __forceinline__ void rgp_tile(const NumParams& p, const int4* __restrict__ Q, float* acc, long long a0,
+template <int RG, int E, class Add>
+__device__ __forceinline__ void rgp_tile(const NumParams& p, const int4* __restrict__ Q, const Add& acc, long long a0,
                                          int len, int lmax, unsigned long long* err, int k0, float x0, int k1,
                                          float x1) {
     const int lane = lane_id(), gl = lane % RG, src0 = (lane / RG) * RG;
@@ -700,7 +720,7 @@ __device__ __forceinline__ void rgp_light_rows(const NumParams& p, float* racc, 
         rg_row_bounds(p, nrow, mark, na0, nlen, nactive);
         const int nnrow = row_at(idx + 2 * step);
         const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
-        rgp_tile<RG, E>(p, p.Bq, acc, a0, len, lmax, err, k0, x0, k1, x1);
+        rgp_tile<RG, E>(p, p.Bq, AddPlain{acc}, a0, len, lmax, err, k0, x0, k1, x1);
         rg_load_a(p, na0 + gl, gl < nlen, k0, x0);
         rg_load_a(p, na0 + RG + gl, RG + gl < nlen, k1, x1);
         long long nout = 0, nout_end = 0;
@@ -779,7 +799,7 @@ __device__ __forceinline__ void rgcta_tile(const NumParams& p, const int4* P4, f
         float x0, x1;
         rg_load_a(p, a0 + gl, gl < len, k0, x0);
         rg_load_a(p, a0 + RG + gl, RG + gl < len, k1, x1);
-        rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, acc, a0, len, lmax, err, k0, x0, k1, x1);
+        rgp_tile<RG, RG == 4 ? 4 : 2>(p, p.Bq, AddPlain{acc}, a0, len, lmax, err, k0, x0, k1, x1);
     } else if (p.T == 1) rg_tile<RG>(p, SegWhole{p.Bp, p.nnzB, p.d}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
     else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
 }
@@ -907,6 +927,393 @@ __global__ void __launch_bounds__(256, 5) k_numeric_rgcta(NumParams p) {
         if (out != out_end && tid == 0) atomicOr(err, ERR_C_ROW);
     }
     if (bad) atomicOr(err, ERR_B_COL);
+}
+
+// ---------------------------------------------------------------------------
+// Wide rows (plus-times, one column tile of 256 < W <= 1024 columns: for
+// d = 1024 the four 256-column tiles of B side by side, so that A is walked
+// once instead of once per tile).  Private accumulators of W floats per row
+// group would leave too few rows in flight per SM, and reading a W-wide
+// accumulator out costs W/32 steps per row although a row of C holds only
+// a few dozen of its W columns.  Here a team -- one warp for a light row,
+// the whole block for a heavy row or a part of a split row -- owns ONE
+// accumulator of W floats and a bitmap of W/32 occupancy words.  The team's
+// slots of 8 lanes take contiguous shares of the item's entries of A and
+// walk their segments of B on the row-aligned copy as the row-group kernels
+// do (pairs of entries per lane, next segment in flight), but all add into
+// the shared accumulator: a shared-memory float reduction for the value and
+// an OR of the column's bit.  The read-out visits the occupied columns only:
+// output positions are dealt to the lanes 32 at a time, so every store
+// writes 32 consecutive entries of C, and lane l finds the column of rank j
+// by a search over the words' running counts and a select inside the word.
+// ---------------------------------------------------------------------------
+
+// Position of the k-th (0-based) set bit of x (k < popc(x)): binary search
+// over halves, quarters, ... of the word by population counts.
+__device__ __forceinline__ int select_bit(unsigned x, int k) {
+    int pos = 0;
+    int c = __popc(x & 0xFFFFu);
+    if (k >= c) { k -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xFFu);
+    if (k >= c) { k -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xFu);
+    if (k >= c) { k -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (k >= c) { k -= c; x >>= 2; pos += 2; }
+    if (k >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
+// Read-out of a shared accumulator acc[0..32*nw) with bitmap bm[0..nw)
+// (nw <= 32) into C[out, out_end): positions 32*r + lane for rounds
+// r = r0, r0 + rstep, ... (a block team splits the rounds over its warps);
+// every emitted column of acc is reset to 0.  Returns the row's count.
+// Called with all 32 lanes converged; the caller clears the bitmap after
+// every warp of the team has passed.
+__device__ __forceinline__ int wide_emit(float* acc, const unsigned* bm, int nw, long long out, long long out_end,
+                                         int* Ci, float* Cx, int r0, int rstep, unsigned long long* err) {
+    const int lane = lane_id();
+    const unsigned word = lane < nw ? bm[lane] : 0u;
+    const int cnt = __popc(word);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(FULL, incl, 31);
+    const long long r = out_end - out;
+    const int room = r < (long long)total ? (int)r : total;
+    bool over = false;
+    for (int base = 32 * r0; base < total; base += 32 * rstep) {
+        const int j = base + lane;
+        // word of rank j: the number of words whose running count is <= j
+        int w = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1)
+            if (__shfl_sync(FULL, incl, w + st - 1) <= j) w += st;
+        const unsigned x = __shfl_sync(FULL, word, w);
+        const int before = __shfl_sync(FULL, incl - cnt, w);
+        if (j < total) {
+            const int c = 32 * w + select_bit(x, j - before);
+            const float v = acc[c];
+            acc[c] = 0.0f;
+            if (j < room) {
+                Ci[out + j] = c;
+                Cx[out + j] = v;
+            } else {
+                over = true;
+            }
+        }
+    }
+    if (over) atomicOr(err, ERR_C_ROW);
+    return total;
+}
+
+// Segments of one chunk of up to 32 entries of A (lane l: entry l, its
+// segment of B in the row-aligned copy as first pair g0 and pairs np, and
+// A's value a; np = 0 past the chunk) added into the shared accumulator.
+// Groups of four lanes take one segment each, lane gl its pairs gl, gl + 4,
+// ...; two steps of eight segments are in flight at once (up to four
+// 16-byte loads per lane before any is used).
+__device__ __forceinline__ void wide_chunk_walk(const int4* __restrict__ Q, const AddShared& add, unsigned W,
+                                                unsigned g0, int np, float a, int nvalid) {
+    const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
+    for (int s0 = 0; s0 < nvalid; s0 += 16) {
+        const int ea = s0 + grp, eb = s0 + 8 + grp;
+        const unsigned ga = __shfl_sync(FULL, g0, ea & 31), gb = __shfl_sync(FULL, g0, eb & 31);
+        int na = __shfl_sync(FULL, np, ea & 31), nb = __shfl_sync(FULL, np, eb & 31);
+        const float xa = __shfl_sync(FULL, a, ea & 31), xb = __shfl_sync(FULL, a, eb & 31);
+        if (ea >= nvalid) na = 0;
+        if (eb >= nvalid) nb = 0;
+        int4 u0 = make_int4(-1, 0, -1, 0), u1 = u0, v0 = u0, v1 = u0;
+        if (gl < na) u0 = __ldg(Q + ga + gl);
+        if (gl < nb) v0 = __ldg(Q + gb + gl);
+        if (gl + 4 < na) u1 = __ldg(Q + ga + gl + 4);
+        if (gl + 4 < nb) v1 = __ldg(Q + gb + gl + 4);
+        add(u0.x, W, xa * __int_as_float(u0.y));
+        add(u0.z, W, xa * __int_as_float(u0.w));
+        add(v0.x, W, xb * __int_as_float(v0.y));
+        add(v0.z, W, xb * __int_as_float(v0.w));
+        add(u1.x, W, xa * __int_as_float(u1.y));
+        add(u1.z, W, xa * __int_as_float(u1.w));
+        add(v1.x, W, xb * __int_as_float(v1.y));
+        add(v1.z, W, xb * __int_as_float(v1.w));
+        // rows of B longer than 16 entries
+        for (int q = gl + 8; q < na; q += 4) {
+            const int4 w = __ldg(Q + ga + q);
+            add(w.x, W, xa * __int_as_float(w.y));
+            add(w.z, W, xa * __int_as_float(w.w));
+        }
+        for (int q = gl + 8; q < nb; q += 4) {
+            const int4 w = __ldg(Q + gb + q);
+            add(w.x, W, xb * __int_as_float(w.y));
+            add(w.z, W, xb * __int_as_float(w.w));
+        }
+    }
+}
+
+// Entry e of A for this lane (ok: inside the chunk): its column k (-1 if
+// none) and value a.
+__device__ __forceinline__ void wide_load_a(const NumParams& p, long long e, bool ok, int& k, float& a) {
+    k = -1;
+    a = 0.0f;
+    if (ok) {
+        k = __ldg(p.Ai + e);
+        a = __ldg(p.Ax + e);
+    }
+}
+
+// Segment (first pair, pairs) of B's row k in the row-aligned copy (none
+// for k = -1; a column of A outside [0, n) is an input error).
+__device__ __forceinline__ void wide_seg(const NumParams& p, int k, unsigned& g0, int& np, unsigned long long* err) {
+    g0 = 0;
+    np = 0;
+    if (k < 0) return;
+    if (k < p.nB) padded_seg<2>(p.Bp, p.nnzB, p.d, k, g0, np);
+    else atomicOr(err, ERR_A_COL);
+}
+
+// Chunks first, first + stride, ... (< e1) of 32 entries of A walked by
+// one warp into the shared accumulator, in three stages: while chunk c is
+// walked, the row pointers of B for chunk c + 1 and the entries of A of
+// chunk c + 2 are in flight.
+__device__ __forceinline__ void wide_range(const NumParams& p, const AddShared& add, long long first, long long e1,
+                                           long long stride, unsigned long long* err) {
+    const int lane = lane_id();
+    const unsigned W = (unsigned)p.W;
+    int k;
+    float a;
+    wide_load_a(p, first + lane, first + lane < e1, k, a);
+    unsigned g0;
+    int np;
+    wide_seg(p, k, g0, np, err);
+    float ca = a;
+    wide_load_a(p, first + stride + lane, first + stride + lane < e1, k, a);
+    for (long long e = first; e < e1; e += stride) {
+        const int nv = e1 - e < 32 ? (int)(e1 - e) : 32;
+        unsigned g1;
+        int np1;
+        wide_seg(p, k, g1, np1, err);  // chunk c + 1
+        const float ca1 = a;
+        const long long e2 = e + 2 * stride;
+        wide_load_a(p, e2 + lane, e2 + lane < e1, k, a);  // chunk c + 2
+        wide_chunk_walk(p.Bq, add, W, g0, np, ca, nv);
+        g0 = g1;
+        np = np1;
+        ca = ca1;
+    }
+}
+
+// A light row as the pipeline holds it: its row id (-1: none), first entry
+// of A and length.
+struct WideRow {
+    int row;
+    int len;
+    long long a0;
+};
+
+__device__ __forceinline__ WideRow wide_row(const NumParams& p, int row) {
+    WideRow r{row, 0, 0};
+    if (row < 0) return r;
+    r.a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+    r.len = (int)(clampll(__ldg(p.Ap + row + 1), r.a0, p.nnzA) - r.a0);
+    return r;
+}
+
+// The light rows of one warp in natural row order: chunks c, c + step, ...
+// of 32 consecutive rows, and in each chunk the rows with products below
+// the heavy threshold (split rows carry a negative mark in the flops array
+// and heavy rows belong to the blocks).  Rows of C that follow each other
+// are then written one after another by the same warp, so that C's lines
+// fill while they are in L2, and A is read in order.  The flops of the
+// chunk after the current one are loaded ahead.
+struct LightRows {
+    long long chunk, step, nchunks;
+    long long base;
+    unsigned mask;
+    long long f_next;  // this lane's row of chunk `chunk + step`
+    __device__ __forceinline__ static bool light(long long f, int cc) { return f > 0 && flops_class(f) < cc; }
+    __device__ __forceinline__ static long long flops_of(const NumParams& p, long long c, long long nchunks) {
+        const long long row = c * 32 + lane_id();
+        return (c < nchunks && row < p.nB) ? __ldg(p.s.flops + row) : 0;
+    }
+    __device__ __forceinline__ void start(const NumParams& p, long long c0, long long st, int cc) {
+        step = st;
+        nchunks = ((long long)p.nB + 31) / 32;
+        chunk = c0;
+        base = c0 * 32;
+        mask = __ballot_sync(FULL, light(flops_of(p, c0, nchunks), cc));
+        f_next = flops_of(p, c0 + st, nchunks);
+    }
+    // next light row of this warp, -1 when none is left (warp-uniform)
+    __device__ __forceinline__ int next(const NumParams& p, int cc) {
+        while (mask == 0) {
+            if (chunk >= nchunks) return -1;
+            chunk += step;
+            base = chunk * 32;
+            mask = __ballot_sync(FULL, light(f_next, cc));
+            f_next = flops_of(p, chunk + step, nchunks);
+        }
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        return (int)(base + b);
+    }
+};
+
+// Persistent kernel: split parts, then heavy rows (team = block: warp w
+// walks the item's chunks w, w + warps, ... into its own accumulator and the
+// block sums the warps' accumulators into warp 0's),
+// then light rows (team = warp, in natural row order, pipelined: while row
+// r is walked and read out, the row pointers of B for row r + 1's first
+// chunk, the entries of A of row r + 2 and the bounds of row r + 3 are in
+// flight).  Shared memory per warp: W + 8 floats of accumulator and
+// W/32 + 1 bitmap words (zero between items: every read-out resets what it
+// emitted).
+__global__ void __launch_bounds__(256, 4) k_numeric_wide(NumParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item, s_nheavy, s_nrows;
+    __shared__ int s_last;
+    __shared__ int s_wcnt[MAX_DENSE_W / 32 + 1];
+    const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    const int ld = p.W + 8, nw = p.W >> 5, bmw = nw + 1;
+    const int per_warp = ld + bmw;  // 4-byte words
+    for (int i = tid; i < nwarps * per_warp; i += blockDim.x) reinterpret_cast<unsigned*>(smem)[i] = 0u;
+    if (tid < 32) {  // one warp; its lanes store the same values
+        long long nh, nr;
+        sched_counts(p.hdr, p.cta_class, nh, nr);
+        s_nheavy = nh;
+        s_nrows = nr;
+    }
+    __syncthreads();
+    const long long nheavy = s_nheavy, nrows = s_nrows;
+    unsigned long long* err = &p.hdr->err;
+    const bool split_ok = p.s.stg_vals != nullptr;
+    const long long* mark = split_ok ? p.s.flops : nullptr;
+    // block teams: every warp walks its chunks into its own accumulator (no
+    // contention between warps on the float additions), then the block sums
+    // the warps' accumulators column by column
+    float* wacc = reinterpret_cast<float*>(smem) + (size_t)warp * per_warp;
+    unsigned* wbm = reinterpret_cast<unsigned*>(wacc) + ld;
+    const AddShared wadd{wacc, wbm};
+    float* acc0 = reinterpret_cast<float*>(smem);  // warp 0's accumulator takes the sum
+    unsigned* bm0 = reinterpret_cast<unsigned*>(smem) + ld;
+    // column c summed over the warps (and reset in every warp but 0, whose
+    // accumulator gets the sum); returns whether any warp reached it
+    auto merge_col = [&](int c, float& v) -> bool {
+        bool any = false;
+        v = 0.0f;
+        for (int w = 0; w < nwarps; ++w) {
+            float* aw = reinterpret_cast<float*>(smem) + (size_t)w * per_warp;
+            const unsigned* bw = reinterpret_cast<const unsigned*>(aw) + ld;
+            if ((bw[c >> 5] >> (c & 31)) & 1u) {
+                v += aw[c];
+                any = true;
+                if (w) aw[c] = 0.0f;
+            }
+        }
+        return any;
+    };
+    auto clear_bitmaps = [&]() {
+        for (int i = tid; i < nwarps * nw; i += blockDim.x)
+            reinterpret_cast<unsigned*>(smem)[(size_t)(i / nw) * per_warp + ld + (i % nw)] = 0u;
+    };
+    // parts of split rows: accumulate, then add the occupied columns into the
+    // row's staging slot; the block completing a row's last part reads it out
+    const long long nitems = split_ok ? min(*(volatile long long*)&p.hdr->scratch[2], p.item_cap) : 0;
+    SplitItem it;
+    while (next_split_item(p.s, p.Ap, p.nnzA, nitems, &s_item, it)) {
+        wide_range(p, wadd, it.e0 + 32LL * warp, it.e1, 32LL * nwarps, err);
+        __syncthreads();
+        float* sv = p.s.stg_vals + (size_t)it.slot * p.s.dpad;
+        unsigned char* sf = p.s.stg_flags + (size_t)it.slot * p.s.dpad;
+        for (int c = tid; c < p.W; c += blockDim.x) {
+            float v;
+            if (merge_col(c, v)) {
+                atomicAdd(sv + c, v);
+                sf[c] = 1;
+                acc0[c] = 0.0f;
+            }
+        }
+        __syncthreads();
+        clear_bitmaps();
+        __syncthreads();
+        if (!split_part_done(p.s, it.slot, it.nsub, &s_last)) continue;
+        split_row_readout<true>(p, it, s_wcnt);
+    }
+    // heavy rows, one per block
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&p.hdr->heavy_ctr, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const int row = p.perm[h];
+        const long long a0 = clampll(__ldg(p.Ap + row), 0, p.nnzA);
+        const long long a1 = clampll(__ldg(p.Ap + row + 1), a0, p.nnzA);
+        if (mark && is_split_row(mark, row, a1 - a0)) continue;
+        const long long out = clampll(__ldg(p.Cp + row), 0, p.nnzC);
+        const long long out_end = clampll(__ldg(p.Cp + row + 1), out, p.nnzC);
+        wide_range(p, wadd, a0 + 32LL * warp, a1, 32LL * nwarps, err);
+        __syncthreads();
+        for (int c = tid; c < p.W; c += blockDim.x) {
+            float v;
+            if (merge_col(c, v)) acc0[c] = v;
+        }
+        __syncthreads();
+        // warp 0's bitmap becomes the union
+        for (int i = tid; i < nw; i += blockDim.x) {
+            unsigned u = 0;
+            for (int w = 0; w < nwarps; ++w) u |= reinterpret_cast<const unsigned*>(smem)[(size_t)w * per_warp + ld + i];
+            bm0[i] = u;
+        }
+        __syncthreads();
+        const int tot = wide_emit(acc0, bm0, nw, out, out_end, p.Ci, p.Cx, warp, nwarps, err);
+        __syncthreads();
+        clear_bitmaps();
+        if (tid == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+        __syncthreads();
+    }
+    // light rows, one per warp, in natural row order
+    const unsigned W = (unsigned)p.W;
+    const int cc = p.cta_class;
+    LightRows q;
+    q.start(p, (long long)blockIdx.x * nwarps + warp, (long long)gridDim.x * nwarps, cc);
+    // pipeline fill: r0 with its segments, r1 with its entries of A, r2
+    WideRow r0 = wide_row(p, q.next(p, cc));
+    int k;
+    float a;
+    wide_load_a(p, r0.a0 + lane, lane < r0.len, k, a);
+    unsigned g0;
+    int np;
+    wide_seg(p, k, g0, np, err);
+    float ca = a;
+    WideRow r1 = wide_row(p, q.next(p, cc));
+    wide_load_a(p, r1.a0 + lane, lane < r1.len, k, a);
+    WideRow r2 = wide_row(p, q.next(p, cc));
+    while (r0.row >= 0) {
+        const WideRow r3 = wide_row(p, q.next(p, cc));
+        const long long out = clampll(__ldg(p.Cp + r0.row), 0, p.nnzC);
+        const long long out_end = clampll(__ldg(p.Cp + r0.row + 1), out, p.nnzC);
+        unsigned g1;
+        int np1;
+        wide_seg(p, k, g1, np1, err);  // row r + 1: segments of its first chunk
+        const float ca1 = a;
+        wide_load_a(p, r2.a0 + lane, lane < r2.len, k, a);  // row r + 2: its first chunk of A
+        wide_chunk_walk(p.Bq, wadd, W, g0, np, ca, r0.len < 32 ? r0.len : 32);
+        if (r0.len > 32) wide_range(p, wadd, r0.a0 + 32, r0.a0 + r0.len, 32, err);  // a long light row
+        __syncwarp();
+        const int tot = wide_emit(wacc, wbm, nw, out, out_end, p.Ci, p.Cx, 0, 1, err);
+        if (lane == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+        __syncwarp();
+        if (lane < nw) wbm[lane] = 0u;
+        __syncwarp();
+        r0 = r1;
+        r1 = r2;
+        r2 = r3;
+        g0 = g1;
+        np = np1;
+        ca = ca1;
+    }
+}
+
+size_t numeric_wide_smem(int W, int warps) {
+    return (size_t)warps * 4 * (size_t)((W + 8) + (W / 32 + 1));
 }
 
 template <bool VALUES, int G, bool PACKED>
@@ -1077,6 +1484,20 @@ static cudaError_t launch_rgcta(const NumParams& p, int warps, int sms, cudaStre
     return cudaGetLastError();
 }
 
+static cudaError_t launch_wide(const NumParams& p, int warps, int sms, cudaStream_t st) {
+    const void* k = (const void*)k_numeric_wide;
+    const size_t smem = numeric_wide_smem(p.W, warps);
+    cudaError_t e;
+    if (p.W > 1024 || p.T != 1 || !p.Bq || smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid(k, 32 * warps, smem, sms);
+    count_launch();
+    k_numeric_wide<<<grid, 32 * warps, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <bool VALUES, int G, bool PACKED>
 static cudaError_t launch_one(const NumParams& p, int warps, int sms, cudaStream_t st) {
     const void* k = (const void*)k_numeric<VALUES, G, PACKED>;
@@ -1161,6 +1582,10 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
     const int w = cfg.warps_per_cta;
     if (Bq && (T != 1 || !values || cfg.row_lanes == 32)) return cudaErrorInvalidValue;
     p.Bq = Bq;
+    if (cfg.row_lanes == 1) {  // one shared accumulator per team, on the row-aligned copy
+        if (!values || !Bq || T != 1 || W > 1024) return cudaErrorInvalidValue;
+        return launch_wide(p, w, cfg.sms, st);
+    }
     if (values && (Bpk || Bq) && cfg.row_lanes != 32) {  // row groups need a packed copy
         if (T > 1) {
             // Over several column tiles a segment of B holds only d_tile/d of its

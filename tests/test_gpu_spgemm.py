@@ -48,6 +48,7 @@ TUNINGS = [
     {"row_lanes": 4, "pack_b": 2}, {"row_lanes": 8, "cta_min_flops": 1 << 20, "warps_per_cta": 2},
     {"row_lanes": 32}, {"row_lanes": 32, "sym_group": 16},   # one warp per light row in every pass
     {"accum": ACC_COPIES, "row_lanes": 32}, {"accum": ACC_COPIES, "row_lanes": 4, "group": 32},
+    {"row_lanes": 1}, {"row_lanes": 1, "cta_min_flops": 1}, {"row_lanes": 1, "warps_per_cta": 3},  # shared accumulators
 ]
 
 
@@ -369,7 +370,7 @@ def test_unaligned_b_columns_and_b_tail(tuning):
         compare_full(spgemm(dev(A), Bx, tuning=tuning), A, B)
 
 
-def _wide_hub_product(seed=93, n=4096, d=8192, hub=7, hub_len=3000):
+def _wide_hub_product(seed=93, n=4096, d=8192, hub=7, hub_len=3000, density=None):
     """d = 8192 (hash accumulator) with one hub row of A whose row of C holds
     about 7,700 distinct columns, more than a block's hash table holds at
     75% load with the default 8 warps x 1024 slots (6,144)."""
@@ -381,7 +382,7 @@ def _wide_hub_product(seed=93, n=4096, d=8192, hub=7, hub_len=3000):
     rp = np.zeros(n + 1, dtype=np.int64)
     rp[1:] = np.cumsum([len(r) for r in rows])
     A = CSR(n, n, rp, np.concatenate(rows).astype(np.int32), rng.random(int(rp[-1]), dtype=np.float32))
-    B = synth.tall_skinny(n, d, 8.0 / d, seed + 1)
+    B = synth.tall_skinny(n, d, density or 8.0 / d, seed + 1)
     B.val = synth.uniform(B.nnz, seed + 2)
     return A, B
 
@@ -407,3 +408,44 @@ def test_autotune_wide_hub_row():
     plan.check()
     compare_full(C, A, B)
     compare_full(plan.forward(Ad, Bd), A, B)
+
+
+WIDE_TUNINGS = [None, {"cta_min_flops": 1}, {"cta_min_flops": 1 << 20}, {"warps_per_cta": 1},
+                {"warps_per_cta": 4, "cta_min_flops": 64}, {"warps_per_cta": 8, "cta_min_flops": 300}]
+
+
+@pytest.mark.parametrize("d", [1024, 700, 288])
+@pytest.mark.parametrize("tuning", WIDE_TUNINGS)
+def test_wide_rows_shared_accumulator(d, tuning):
+    # one column tile of 256 < W <= 1024 columns: light rows one warp each,
+    # heavy rows and split parts one block each, on one shared accumulator
+    # per team with occupancy bits (row_lanes = 1, the default there)
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=d, density=0.01, seed=60 + d % 7, b_values="uniform")
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd, tuning=tuning)
+    assert plan.tuning["row_lanes"] == 1
+    compare_full(plan.forward(Ad, Bd), A, B)
+
+
+@pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1}, {"warps_per_cta": 2}, {"cta_min_flops": 1 << 20}])
+def test_wide_rows_split_hub(tuning):
+    # a hub row of 3000 entries of A (three split parts) reaching all 1024
+    # columns, and dense-ish rows of B (5 %)
+    A, B = _wide_hub_product(seed=95, d=1024, density=0.05)
+    C = spgemm(dev(A), dev(B), tuning=tuning)
+    Cp, _, _, _ = compare_full(C, A, B)
+    assert Cp[8] - Cp[7] == 1024
+
+
+def test_wide_rows_nan_and_empty():
+    # NaN products keep their columns; empty rows of A and of B
+    A, B = synth.rmat_embedding(scale=11, edge_factor=8, d=1024, density=0.01, seed=96, b_values="uniform")
+    B.val = B.val.copy()
+    B.val[::97] = np.nan
+    C = spgemm(dev(A), dev(B))
+    rp, col, val = C.to_host()
+    Cp, Ci, Cx, Cb = oracle.spgemm(A, B)
+    assert_pattern_equal(rp, col, Cp, Ci)
+    both = np.isnan(Cx)
+    np.testing.assert_array_equal(np.isnan(val[: Cx.size]), both)
+    assert_values_close(val[: Cx.size][~both], Cx[~both], Cb[~both])
