@@ -9,11 +9,25 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tsspgemm.h"
 #include "kernels.h"
 #include "layout.h"
 
 using namespace ts;
+
+// NVTX range around an entry point or one of its phases, so that a profiler
+// timeline (nsys, ncu --nvtx) shows the passes by name.  Without a tool
+// attached the push and pop cost a few nanoseconds.
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // errors
@@ -405,6 +419,7 @@ static ts_status read_errors(void* ws, const Layout& L, cudaStream_t st, const c
 extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                         int64_t* C_rowptr, int64_t* nnzC_host, void* ws,
                                         size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("ts_spgemm_symbolic");
     const char* fn = "ts_spgemm_symbolic";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     const Layout L = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
@@ -415,10 +430,16 @@ extern "C" ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, con
     const Sched sc = carve(ws, L);
     const DevCsr dA = dev(A), dB = dev(B);
     plan->sym_valid = false;
-    TS_CUDA(launch_row_schedule(dA, dB, sc, (long long*)C_rowptr, st), fn);
+    {
+        NvtxRange r("row flops and classes");
+        TS_CUDA(launch_row_schedule(dA, dB, sc, (long long*)C_rowptr, st), fn);
+    }
     LaunchCfg scfg = cfg_of(plan->cur);
     scfg.group = plan->cur.sym_group;
-    TS_CUDA(launch_symbolic(dA, dB, plan->d, sc, scfg, (long long*)C_rowptr, st), fn);
+    {
+        NvtxRange r("row counts and scan");
+        TS_CUDA(launch_symbolic(dA, dB, plan->d, sc, scfg, (long long*)C_rowptr, st), fn);
+    }
     plan->sym_valid = true;
     plan->sym_ws = ws;
     plan->sym_ptrs[0] = A->rowptr;
@@ -513,6 +534,7 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
 
 extern "C" ts_status ts_spgemm_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                        const ts_csr_desc* C, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("ts_spgemm_numeric");
     const char* fn = "ts_spgemm_numeric";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     const Layout L = plan_layout(plan->n, plan->d, plan->cur, A ? A->nnz : plan->nnzA, B ? B->nnz : plan->nnzB);
@@ -531,6 +553,7 @@ extern "C" ts_status ts_spgemm_numeric(ts_plan* plan, const ts_csr_desc* A, cons
 static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                               const ts_csr_desc* C, const float* dC, float* dA, float* dB, void* ws,
                               size_t ws_bytes, void* stream, const char* fn) {
+    NvtxRange nvtx_range("ts_spgemm_backward");
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (plan->semiring != TS_SR_PLUS_TIMES_F32)
         return fail(TS_ERR_UNSUPPORTED, "%s: the boolean semiring has no gradient", fn);
@@ -589,6 +612,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                                       const ts_csr_desc* C, const float* dC_val, float* dA_scratch,
                                       float* dB_scratch, int32_t reps, ts_tuning* chosen, void* ws,
                                       size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("ts_plan_autotune");
     const char* fn = "ts_plan_autotune";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (reps < 1) return fail(TS_ERR_INVALID_ARG, "%s: reps must be >= 1", fn);
@@ -790,6 +814,7 @@ extern "C" ts_status f2v_workspace_size(int64_t n, int64_t d, int64_t nnz_A, int
 extern "C" ts_status f2v_step(const ts_csr_desc* A, const ts_csr_desc* Z, int64_t r0, int64_t b,
                               const int32_t* neg, int32_t s, float lr, int32_t k, float* U_out, void* ws,
                               size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("f2v_step");
     const char* fn = "f2v_step";
     ts_status st_;
     if ((st_ = check_desc(A, "A", false)) != TS_OK) return st_;
@@ -868,6 +893,7 @@ extern "C" size_t ts_validate_workspace_size(void) { return 256; }
 
 extern "C" ts_status ts_csr_validate(const ts_csr_desc* M, int64_t* bad_row, void* ws, size_t ws_bytes,
                                      void* stream) {
+    NvtxRange nvtx_range("ts_csr_validate");
     const char* fn = "ts_csr_validate";
     ts_status s = check_desc(M, "M", false);
     if (s != TS_OK) return s;
@@ -995,6 +1021,7 @@ extern "C" ts_status msbfs_step(const ts_csr_desc* A, const ts_csr_desc* F, uint
                                 int32_t* levels, int32_t level, const ts_csr_desc* F_next,
                                 int64_t F_next_capacity, int64_t* nnz_next_host, void* ws,
                                 size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("msbfs_step");
     return bfs_step(A, F, visited, levels, nullptr, level, F_next, F_next_capacity, nnz_next_host, ws, ws_bytes,
                     stream, "msbfs_step");
 }
@@ -1003,6 +1030,7 @@ extern "C" ts_status msbfs_step_parents(const ts_csr_desc* A, const ts_csr_desc*
                                         int32_t* levels, int32_t* parents, int32_t level,
                                         const ts_csr_desc* F_next, int64_t F_next_capacity,
                                         int64_t* nnz_next_host, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("msbfs_step_parents");
     if (!parents) return fail(TS_ERR_INVALID_ARG, "msbfs_step_parents: parents is NULL");
     return bfs_step(A, F, visited, levels, parents, level, F_next, F_next_capacity, nnz_next_host, ws, ws_bytes,
                     stream, "msbfs_step_parents");
@@ -1319,6 +1347,7 @@ static bool same_descs(const std::vector<ts_csr_desc>& v, const ts_csr_desc* x, 
 extern "C" ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, const ts_csr_desc* A,
                                        const ts_csr_desc* B, const ts_csr_desc* C, void* ws, size_t ws_bytes,
                                        void* stream) {
+    NvtxRange nvtx_range("ts_spgemm_batched");
     const char* fn = "ts_spgemm_batched";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (!plan->bound) return fail(TS_ERR_STATE, "%s: call ts_batched_bind first", fn);
@@ -1351,6 +1380,7 @@ extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t c
                                                 const float* const* dC_val, float* const* dA_val,
                                                 float* const* dB_val, void* ws, size_t ws_bytes,
                                                 void* stream) {
+    NvtxRange nvtx_range("ts_spgemm_batched_backward");
     const char* fn = "ts_spgemm_batched_backward";
     if (!plan) return fail(TS_ERR_INVALID_ARG, "%s: plan is NULL", fn);
     if (!plan->grads) return fail(TS_ERR_STATE, "%s: call ts_batched_bind_grads first", fn);
