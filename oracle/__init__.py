@@ -9,6 +9,7 @@ code with the CUDA path.  Inputs come from ``synth`` (seeded generators).
 What each function follows:
   spgemm      -- paper Sec. II-A (semiring product, flops = multiplications)
                  and Sec. III-A, Eq. 1 (row-wise Gustavson).
+  spgemm_count -- the row counts of that product's pattern (its first half).
   msbfs       -- paper Alg. 3 (multi-source BFS over the boolean semiring).
   bfs_levels  -- textbook FIFO-queue BFS (hop distance), one source.
   backward*   -- gradients of <dC, A*B> w.r.t. the stored values of A and B
@@ -124,6 +125,21 @@ def spgemm(A, B, semiring: int = PLUS_TIMES, rows: Optional[np.ndarray] = None):
     if semiring == PLUS_TIMES:
         return Cp, Ci[:tot], Cx[:tot], Cb[:tot]
     return Cp, Ci[:tot], None, None
+
+
+def spgemm_count(A, B) -> np.ndarray:
+    """Row pointers of C = A*B (int64[n+1]): nnz(C_i) is the number of distinct
+    columns over the rows of B that row i of A selects (Eq. 1's pattern)."""
+    Ap, Ai = _i64(A.rowptr), _i32(A.col)
+    Bp, Bi = _i64(B.rowptr), _i32(B.col)
+    n = A.nrows
+    cnt = np.zeros(max(n, 1), dtype=np.int64)
+    tot = _L().oracle_spgemm_count(B.ncols, _p(Ap), _p(Ai), _p(Bp), _p(Bi), None, n, _p(cnt))
+    if tot < 0:
+        raise MemoryError("oracle_spgemm_count")
+    Cp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt[:n], out=Cp[1:])
+    return Cp
 
 
 def msbfs(A, sources: np.ndarray, maxlev: int = 4096):

@@ -97,6 +97,10 @@ def test_batched_full_size_sampled():
     g.replay()
     torch.cuda.synchronize()
     bp.check()
+    # C's row pointers of every instance against the oracle's count pass
+    for b, (A, B) in enumerate(inst):
+        np.testing.assert_array_equal(bp.Cs[b].rowptr.cpu().numpy(), oracle.spgemm_count(A, B),
+                                      err_msg=f"instance {b}")
     rng = np.random.default_rng(2)
     for b in rng.choice(len(inst), 6, replace=False):
         A, B = inst[b]

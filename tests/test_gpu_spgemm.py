@@ -98,17 +98,26 @@ def test_rmat_tiled_d1024():
         compare_full(spgemm(dev(A), dev(B), tuning=t), A, B)
 
 
-def test_tiled_full_size_sampled():
-    # the large tiled product at its full size and in the launch configuration
-    # the benchmark times (R-MAT scale 24, d = 1024, 1 %, tiles of 256):
-    # sampled rows of C, of dA and of dB against the oracle
+@pytest.fixture(scope="module")
+def tiled_full():
     A, B = synth.rmat_embedding(scale=24, edge_factor=16, d=1024, density=0.01, b_values="uniform",
                                 seed=synth.BASE_SEED + 5)
+    return A, B, oracle.spgemm_count(A, B)
+
+
+@pytest.mark.parametrize("tuning", [None, {"col_tile": 256}])
+def test_tiled_full_size_sampled(tiled_full, tuning):
+    # the large product at its full size (R-MAT scale 24, d = 1024, 1 %) in
+    # the launch configuration the benchmark times (default: one 1024-wide
+    # accumulator made of the four 256-column tiles) and with B walked in
+    # column tiles of 256: C's row pointers for all rows, and sampled rows of
+    # C, of dA and of dB against the oracle
+    A, B, Cp_all = tiled_full
     Ad, Bd = dev(A), dev(B)
-    plan = Plan(Ad, Bd, tuning={"col_tile": 256})
+    plan = Plan(Ad, Bd, tuning=tuning)
     C = plan.forward(Ad, Bd)
     rp = C.rowptr.cpu().numpy()
-    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= B.ncols)
+    np.testing.assert_array_equal(rp, Cp_all)
     rng = np.random.default_rng(24)
     deg = np.diff(A.rowptr)
     rows = np.concatenate([np.argsort(deg)[-8:], rng.choice(A.nrows, 1000, replace=False)])
@@ -231,15 +240,23 @@ def embed_full():
     return synth.rmat_embedding()
 
 
+@pytest.fixture(scope="module")
+def embed_full_rowptr(embed_full):
+    # C's row pointers for every row, from the oracle's count pass
+    A, B = embed_full
+    return oracle.spgemm_count(A, B)
+
+
 @pytest.mark.parametrize("tuning", [None, {"accum": ACC_COPIES}, {"group": 2, "sym_group": 2}, {"row_lanes": 4},
                                     {"row_lanes": 32}])
-def test_embedding_full_size_sampled(embed_full, tuning):
-    # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %
+def test_embedding_full_size_sampled(embed_full, embed_full_rowptr, tuning):
+    # sparse-embedding workload at full size: R-MAT scale 22, d = 256, 5 %:
+    # C's row pointers for all rows, columns and values on sampled rows
     A, B = embed_full
     Ad, Bd = dev(A), dev(B)
     C = spgemm(Ad, Bd, tuning=tuning)
     rp = C.rowptr.cpu().numpy()
-    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= B.ncols)
+    np.testing.assert_array_equal(rp, embed_full_rowptr)
     deg = np.diff(A.rowptr)
     rng = np.random.default_rng(0)
     rows = np.concatenate([np.argsort(deg)[-8:], rng.choice(A.nrows, 3000, replace=False)])

@@ -97,6 +97,20 @@ def test_spgemm_matches_scipy():
     assert np.all(Cb >= np.abs(Cx) * (1 - 1e-15))
 
 
+def test_spgemm_count_matches_scipy_pattern():
+    # row counts of the pattern alone: the distinct columns per row of the
+    # structural product (scipy's product of 0/1 matrices counts products,
+    # its nonzeros are the distinct columns since all terms are positive)
+    A, B = synth.er_product(n=700, k=5, d=96, density=0.08, seed=17)
+    Cp = oracle.spgemm_count(A, B)
+    Sa = sp.csr_matrix((np.ones(A.nnz), A.col, A.rowptr), shape=(A.nrows, A.ncols))
+    Sb = sp.csr_matrix((np.ones(B.nnz), B.col, B.rowptr), shape=(B.nrows, B.ncols))
+    S = (Sa @ Sb).tocsr()
+    S.sort_indices()
+    np.testing.assert_array_equal(Cp, S.indptr)
+    np.testing.assert_array_equal(Cp, oracle.spgemm(A, B)[0])
+
+
 def test_spgemm_golden_eq1():
     g = json.load(open(os.path.join(GOLDEN, "eq1_small.json")))
     n, d = g["n"], g["d"]
