@@ -72,6 +72,15 @@ typedef int32_t ts_status;
 #define TS_ACC_COPIES 3  /* dense accumulator, one private copy per lane group
                           * and no atomics (plus-times; the boolean semiring
                           * uses TS_ACC_DENSE)                                  */
+#define TS_ACC_DENSE_B 4 /* B expanded dense in the workspace and each row of C
+                          * summed in registers: the dense-B SpMM form of the
+                          * product (plus-times, d <= 256; Sec. V's comparison
+                          * with SpMM).  TS_ACC_AUTO picks it for plus-times
+                          * when B holds at least 600/1000 (64 < d <= 128) or
+                          * 450/1000 (128 < d <= 256) of its n*d entries: the
+                          * crossovers measured on R-MAT scale-20 products; at
+                          * d <= 64 the sparse path stays as fast up to a full
+                          * B and is kept                                      */
 
 typedef struct ts_csr_desc {
     int64_t nrows;

@@ -5,9 +5,9 @@ multi-source BFS of its Alg. 3, a differentiable plus-times product and a
 batched, graph-capturable launch.  The kernels live in libtsspgemm.so (C ABI:
 include/tsspgemm.h); this package only marshals torch tensors to it.
 """
-from ._native import (ACC_AUTO, ACC_COPIES, ACC_DENSE, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, TSError)
+from ._native import (ACC_AUTO, ACC_COPIES, ACC_DENSE, ACC_DENSE_B, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, TSError)
 
 from .ops import DeviceCSR, Plan, spgemm, validate
 
-__all__ = ["ACC_AUTO", "ACC_COPIES", "ACC_DENSE", "ACC_HASH", "OR_SELECT2ND", "PLUS_TIMES", "TSError",
+__all__ = ["ACC_AUTO", "ACC_COPIES", "ACC_DENSE", "ACC_DENSE_B", "ACC_HASH", "OR_SELECT2ND", "PLUS_TIMES", "TSError",
            "DeviceCSR", "Plan", "spgemm", "validate"]

@@ -30,6 +30,7 @@ ACC_AUTO = 0
 ACC_DENSE = 1
 ACC_HASH = 2
 ACC_COPIES = 3
+ACC_DENSE_B = 4
 
 
 class CsrDesc(ctypes.Structure):

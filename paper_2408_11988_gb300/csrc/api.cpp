@@ -172,11 +172,23 @@ static int copies_group(int group, long long nB, long long nnzB) {
     return avg <= 8.0 ? 8 : (avg <= 16.0 ? 16 : 32);
 }
 
+// Whether B is dense enough for the dense-B form (plus-times, 64 < d <= 256):
+// the density above which it beat the sparse numeric pass on R-MAT scale-20
+// products (edge factor 16) on GB300, per width of the accumulator.
+static bool dense_b_auto(bool vals, long long d, long long nB, long long nnzB) {
+    const long long dpad = round_up(d, 32);
+    if (!vals || dpad <= 64 || dpad > 256 || nB <= 0) return false;
+    const double permille = dpad <= 128 ? 600.0 : 450.0;
+    return (double)nnzB * 1000.0 >= permille * (double)nB * (double)d;
+}
+
 static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& t,
-                                long long nB = 0, long long nnzB = 0) {
+                                long long nB = 0, long long nnzB = 0, bool vals = false) {
     const long long dpad = round_up(d, 32);
     t = ts_tuning{};
-    t.accum = force.accum ? force.accum : (dpad <= 4096 ? TS_ACC_DENSE : TS_ACC_HASH);
+    t.accum = force.accum ? force.accum
+                          : (dense_b_auto(vals, d, nB, nnzB) ? TS_ACC_DENSE_B
+                                                              : (dpad <= 4096 ? TS_ACC_DENSE : TS_ACC_HASH));
     t.col_tile = force.col_tile ? force.col_tile : (int)std::min<long long>(dpad, 1024);
     t.cta_min_flops = force.cta_min_flops ? force.cta_min_flops : 4096;
     t.warps_per_cta = force.warps_per_cta ? force.warps_per_cta : 8;
@@ -197,8 +209,11 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     if (t.row_lanes != 0 && t.row_lanes != 1 && t.row_lanes != 4 && t.row_lanes != 8 && t.row_lanes != 16 &&
         t.row_lanes != 32)
         return fail(TS_ERR_INVALID_ARG, "tuning: row_lanes must be 1, 4, 8, 16 or 32");
-    if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES)
-        return fail(TS_ERR_INVALID_ARG, "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH or TS_ACC_COPIES");
+    if (t.accum != TS_ACC_DENSE && t.accum != TS_ACC_HASH && t.accum != TS_ACC_COPIES && t.accum != TS_ACC_DENSE_B)
+        return fail(TS_ERR_INVALID_ARG,
+                    "tuning: accum must be TS_ACC_DENSE, TS_ACC_HASH, TS_ACC_COPIES or TS_ACC_DENSE_B");
+    if (t.accum == TS_ACC_DENSE_B && dpad > 256)
+        return fail(TS_ERR_INVALID_ARG, "tuning: TS_ACC_DENSE_B needs d <= 256");
     if (t.accum == TS_ACC_COPIES && dpad > 4096)
         return fail(TS_ERR_INVALID_ARG, "tuning: TS_ACC_COPIES needs d <= 4096");
     if (t.col_tile < 32 || t.col_tile % 32 || t.col_tile > 4096)
@@ -226,7 +241,8 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
 }
 
 struct Layout {
-    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, bq = 0, total = 0;
+    size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, bq = 0, denseb = 0,
+           total = 0;
     size_t split_rows = 0, split_done = 0, split_items = 0, stg_bits = 0, stg_vals = 0, stg_flags = 0;
     int dw = 0, dpad = 0;
     int W = 0, T = 1;
@@ -275,6 +291,8 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     if (t.pack_b == 1 || cover_autotune) L.bpk = take(8 * ((size_t)nnzB + 4));
     // row-aligned packed B for the row-group numeric kernels (one column tile)
     if ((t.pack_b == 1 && L.T == 1 && t.row_lanes != 32) || cover_autotune) L.bq = take(padded_b_bytes(n, nnzB, d, 4));
+    // dense copy of B and its pattern bitmap (dense-B form only)
+    if (t.accum == TS_ACC_DENSE_B) L.denseb = take(dense_b_bytes(n, d));
     L.total = off;
     return L;
 }
@@ -334,7 +352,7 @@ extern "C" ts_status ts_plan_create(const ts_csr_desc* A, const ts_csr_desc* B, 
     p->nnzB = B->nnz;
     p->semiring = semiring;
     if (force) p->force = *force;
-    ts_status s = resolve_tuning(p->d, p->force, p->cur, p->n, p->nnzB);
+    ts_status s = resolve_tuning(p->d, p->force, p->cur, p->n, p->nnzB, semiring == TS_SR_PLUS_TIMES_F32);
     if (s != TS_OK) {
         delete p;
         return s;
@@ -357,7 +375,7 @@ extern "C" ts_status ts_plan_get_tuning(const ts_plan* plan, ts_tuning* out) {
 extern "C" ts_status ts_plan_set_tuning(ts_plan* plan, const ts_tuning* tuning) {
     if (!plan || !tuning) return fail(TS_ERR_INVALID_ARG, "ts_plan_set_tuning: NULL argument");
     ts_tuning merged = *tuning, t;
-    ts_status s = resolve_tuning(plan->d, merged, t, plan->n, plan->nnzB);
+    ts_status s = resolve_tuning(plan->d, merged, t, plan->n, plan->nnzB, plan->semiring == TS_SR_PLUS_TIMES_F32);
     if (s != TS_OK) return s;
     plan->cur = t;
     return ok();
@@ -475,7 +493,12 @@ static ts_status run_numeric(ts_plan* plan, const ts_csr_desc* A, const ts_csr_d
     const Sched sc = carve(ws, L);
     const DevCsr dA = dev(A), dB = dev(B);
     const LaunchCfg cfg = cfg_of(plan->cur);
-    if (plan->cur.accum == TS_ACC_DENSE || plan->cur.accum == TS_ACC_COPIES) {
+    if (plan->cur.accum == TS_ACC_DENSE_B && vals) {
+        TS_CUDA(launch_numeric_denseb(dA, dB, plan->d, sc, cfg, (const long long*)C->rowptr, C->col, (float*)C->val,
+                                      C->nnz, (char*)ws + L.denseb, st),
+                fn);
+    } else if (plan->cur.accum == TS_ACC_DENSE || plan->cur.accum == TS_ACC_COPIES ||
+               plan->cur.accum == TS_ACC_DENSE_B) {
         long long* tp = nullptr;
         if (L.T > 1) {
             tp = (long long*)((char*)ws + L.tp);
@@ -646,7 +669,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
     float best_ms = 1e30f;
     auto try_one = [&](const ts_tuning& cand_in) -> ts_status {
         ts_tuning cand;
-        if (resolve_tuning(plan->d, cand_in, cand, plan->n, B->nnz) != TS_OK) return TS_OK;  // skip
+        if (resolve_tuning(plan->d, cand_in, cand, plan->n, B->nnz, vals) != TS_OK) return TS_OK;  // skip
         const Layout L = plan_layout(plan->n, plan->d, cand, A->nnz, B->nnz);
         if (L.total > ws_bytes) return TS_OK;  // does not fit the caller's workspace
         plan->cur = cand;
@@ -697,9 +720,10 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
                 break;
             case 2:
                 if (plan->force.accum) break;
-                for (int acc : {TS_ACC_DENSE, TS_ACC_COPIES, TS_ACC_HASH}) {
+                for (int acc : {TS_ACC_DENSE, TS_ACC_COPIES, TS_ACC_HASH, TS_ACC_DENSE_B}) {
                     if (acc == TS_ACC_HASH && plan->d <= 256) continue;
                     if (acc == TS_ACC_COPIES && (!vals || dpad > 4096)) continue;
+                    if (acc == TS_ACC_DENSE_B && (!vals || dpad > 256)) continue;
                     c.accum = acc;
                     cands.push_back(c);
                 }

@@ -129,6 +129,13 @@ size_t numeric_rgcta_smem(int W, int warps, int row_lanes);
 size_t numeric_wide_smem(int W, int warps);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
+// Numeric pass with B expanded dense (plus-times, d <= 256): dense_ws holds
+// dense_b_bytes(B.nrows, d) bytes for the copy and its pattern bitmap.
+size_t dense_b_bytes(long long nB, long long d);
+cudaError_t launch_numeric_denseb(const DevCsr& A, const DevCsr& B, long long d, const Sched& s,
+                                  const LaunchCfg& cfg, const long long* Cp, int* Ci, float* Cx, long long nnzC,
+                                  void* dense_ws, cudaStream_t st);
+
 // Backward: dA (SDDMM on A's pattern) and dB (A^T dC on B's pattern).
 cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const long long* Cp,
                             const int* Ci, long long nnzC, const float* dC, float* dA, float* dB,

@@ -43,7 +43,7 @@ def test_host_side_errors(lib):
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(Bbig), 0, None, ctypes.byref(h)) == N.TS_ERR_UNSUPPORTED
     bad_t = N.Tuning(0, 48, 0, 0, 0, 0, 0, 0, 0, 0, 0)
     assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bad_t), ctypes.byref(h)) == N.TS_ERR_INVALID_ARG
-    for bad in ({"bwd_group": 3}, {"group": 64}, {"row_lanes": 2}, {"accum": 4}, {"accum": N.ACC_COPIES, "col_tile": 4096 + 32}):
+    for bad in ({"bwd_group": 3}, {"group": 64}, {"row_lanes": 2}, {"accum": 5}, {"accum": N.ACC_COPIES, "col_tile": 4096 + 32}):
         bt = N.Tuning.from_dict(bad)
         assert lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), 0, ctypes.byref(bt), ctypes.byref(h)) \
             == N.TS_ERR_INVALID_ARG, bad
@@ -90,3 +90,42 @@ def test_host_side_errors(lib):
                         None, ctypes.c_void_p(256), sz2.value, None) == N.TS_ERR_INVALID_ARG
     assert N.status_string(N.TS_ERR_CAPACITY) == "TS_ERR_CAPACITY"
     assert lib.ts_version() >= 100
+
+
+def test_automatic_accumulator_choice(lib):
+    # plan creation only (no launch): the dense-B form above the measured
+    # density crossovers (60 % for 64 < d <= 128, 45 % for d <= 256, never for
+    # d <= 64), the wide shared accumulator for one tile of 256 < W <= 1024,
+    # row groups up to 256 columns, hash above 4096; boolean products never
+    # take the dense-B form
+    from paper_2408_11988_gb300 import _native as N
+
+    def tuning(n, d, nnzB, semiring=0, force=None):
+        A = N.CsrDesc(n, n, 8 * n, 8, 8, 8)
+        B = N.CsrDesc(n, d, nnzB, 8, 8, 8)
+        h = ctypes.c_void_p()
+        f = N.Tuning.from_dict(force) if force else None
+        st = lib.ts_plan_create(ctypes.byref(A), ctypes.byref(B), semiring, ctypes.byref(f) if f else None,
+                                ctypes.byref(h))
+        if st != N.TS_OK:
+            return st
+        t = N.Tuning()
+        assert lib.ts_plan_get_tuning(h, ctypes.byref(t)) == N.TS_OK
+        assert lib.ts_plan_destroy(h) == N.TS_OK
+        return t.as_dict()
+
+    n = 1000
+    assert tuning(n, 128, int(0.59 * n * 128))["accum"] == N.ACC_DENSE
+    assert tuning(n, 128, int(0.60 * n * 128))["accum"] == N.ACC_DENSE_B
+    assert tuning(n, 128, n * 128, semiring=1)["accum"] == N.ACC_DENSE
+    assert tuning(n, 256, int(0.44 * n * 256))["accum"] == N.ACC_DENSE
+    assert tuning(n, 256, int(0.45 * n * 256))["accum"] == N.ACC_DENSE_B
+    assert tuning(n, 64, n * 64)["accum"] == N.ACC_DENSE
+    assert tuning(n, 300, n * 300)["accum"] == N.ACC_DENSE
+    assert tuning(n, 300, 10, force={"accum": N.ACC_DENSE_B}) == N.TS_ERR_INVALID_ARG
+    t = tuning(n, 1024, 10 * n)
+    assert t["accum"] == N.ACC_DENSE and t["col_tile"] == 1024 and t["row_lanes"] == 1
+    t = tuning(n, 256, 13 * n)
+    assert t["accum"] == N.ACC_DENSE and t["row_lanes"] == 8
+    assert tuning(n, 5000, 10 * n)["accum"] == N.ACC_HASH
+    assert tuning(n, 1024, 10 * n, force={"row_lanes": 1, "col_tile": 256}) == N.TS_ERR_INVALID_ARG

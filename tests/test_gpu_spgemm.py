@@ -15,7 +15,7 @@ from _cmp import REL, compare_full, compare_rows, assert_pattern_equal, assert_v
 
 pytestmark = pytest.mark.gpu
 
-from paper_2408_11988_gb300 import (ACC_COPIES, ACC_DENSE, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, DeviceCSR, Plan,
+from paper_2408_11988_gb300 import (ACC_COPIES, ACC_DENSE, ACC_DENSE_B, ACC_HASH, OR_SELECT2ND, PLUS_TIMES, DeviceCSR, Plan,
                                     TSError, spgemm, validate)
 
 
@@ -466,3 +466,50 @@ def test_wide_rows_nan_and_empty():
     both = np.isnan(Cx)
     np.testing.assert_array_equal(np.isnan(val[: Cx.size]), both)
     assert_values_close(val[: Cx.size][~both], Cx[~both], Cb[~both])
+
+
+def _full_b(n, d, seed):
+    """B with every one of its n*d entries stored (the dense-B SpMM case)."""
+    rp = np.arange(0, n * d + 1, d, dtype=np.int64)
+    col = np.tile(np.arange(d, dtype=np.int32), n)
+    return CSR(n, d, rp, col, synth.normal(n * d, seed))
+
+
+@pytest.mark.parametrize("tuning", [{"accum": ACC_DENSE_B}, {"accum": ACC_DENSE_B, "cta_min_flops": 1},
+                                    {"accum": ACC_DENSE_B, "cta_min_flops": 1 << 20},
+                                    {"accum": ACC_DENSE_B, "warps_per_cta": 2}])
+@pytest.mark.parametrize("d", [32, 64, 100, 128, 256])
+def test_dense_b_all_entries(tuning, d):
+    # B given all of its entries: a row-wise SpMM over a dense B; C's rows are
+    # full wherever A's row is non-empty
+    A = synth.rmat(11, 16, 80 + d)
+    A.val = synth.uniform(A.nnz, 81)
+    B = _full_b(A.nrows, d, 82)
+    C = spgemm(dev(A), dev(B), tuning=tuning)
+    compare_full(C, A, B)
+
+
+@pytest.mark.parametrize("d,density,auto_dense_b", [(128, 0.02, False), (128, 0.3, False), (128, 0.7, True),
+                                                     (128, 0.95, True), (256, 0.35, False), (256, 0.55, True),
+                                                     (64, 0.95, False)])
+def test_dense_b_partial_density_and_auto_switch(d, density, auto_dense_b):
+    # B partly dense: the dense-B form keeps the structural pattern of Eq. 1;
+    # without a forced accumulator the plan takes it above the measured
+    # crossover (60 % for d <= 128, 45 % for d <= 256, never for d <= 64)
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=d, density=density, seed=83, b_values="uniform")
+    Ad, Bd = dev(A), dev(B)
+    auto = Plan(Ad, Bd)
+    assert auto.tuning["accum"] == (ACC_DENSE_B if auto_dense_b else ACC_DENSE)
+    compare_full(auto.forward(Ad, Bd), A, B)
+    compare_full(spgemm(Ad, Bd, tuning={"accum": ACC_DENSE_B}), A, B)
+
+
+def test_dense_b_split_hub_and_boolean():
+    # a split hub row (three parts) over a 60 % dense B, and the boolean
+    # semiring with the dense-B accumulator requested (it runs the sparse
+    # dense-accumulator path: the dense-B form is plus-times only)
+    A, B = _wide_hub_product(seed=84, d=256, density=0.6)
+    Ad, Bd = dev(A), dev(B)
+    compare_full(spgemm(Ad, Bd, tuning={"accum": ACC_DENSE_B}), A, B)
+    C = spgemm(Ad.pattern(), Bd.pattern(), semiring=OR_SELECT2ND, tuning={"accum": ACC_DENSE_B})
+    compare_full(C, A, B, semiring=oracle.OR_SELECT2ND)
