@@ -636,7 +636,11 @@ def batched_record(args, ws, rank, local, dist, steps=None, warmup=None):
     plain_ms = _max_over_ranks(dist, e0.elapsed_time(e1) / steps)
     del plans
     bp = BatchedProduct(As, Bs, tuning=tuning)
-    chosen = bp.autotune() if args.autotune else None
+    # per-instance tuning (accumulator kind, heavy-row threshold) by the
+    # batched autotuner, each instance timed on its own
+    t_at = time.perf_counter()
+    bp.autotune(reps=1)
+    autotune_s = time.perf_counter() - t_at
     Cs = bp.forward()
     torch.cuda.synchronize()
     dC_hosts = [synth.grad_output(int(C.rowptr[-1].item()), 1 + i) for i, C in enumerate(Cs)]
@@ -693,8 +697,11 @@ def batched_record(args, ws, rank, local, dist, steps=None, warmup=None):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched-64", "description": desc, "instances": len(inst), "rows": n,
                    "nnz_A": nnzA, "nnz_C": nnzC, "products": F, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2", "tuning": bp.tuning_summary() if hasattr(bp, "tuning_summary")
-                   else chosen},
+                   "l2": "inputs larger than L2"},
+        "tuning": dict({k: v for k, v in bp.tuning_summary().items() if k != "per_instance"},
+                       autotune_s=round(autotune_s, 2),
+                       per_instance=[[x["accum"], x["width"], x["heavy_min_flops"]]
+                                     for x in bp.tuning_summary()["per_instance"]]),
         "plain_forward": {"ms": round(plain_ms, 4), "gflops": round(2.0 * F / (plain_ms * 1e-3) / 1e9, 3),
                           "what": "64 separate symbolic+numeric calls (host sync each)"},
         "batched_forward": {"ms": round(fwd_ms, 4), "gflops": round(2.0 * F / (fwd_ms * 1e-3) / 1e9, 3),

@@ -353,21 +353,31 @@ TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, 
                      size_t ws_bytes, void* stream);
 
 /*
- * Batched products: `count` independent C_b = A_b * B_b of uneven shapes,
- * each phase one launch over all instances, graph capturable.  The batch is
- * computed as the one product of the block-diagonal matrix diag(A_1..A_m)
- * with the stacked [B_1; ...; B_m] (row block b of it is C_b): the instances
- * are gathered into the workspace, the single-product passes run once, and
- * the rows are scattered back into each instance's C.
+ * Batched products: `count` independent C_b = A_b * B_b of uneven shapes
+ * (the serving pattern of many graphs at once; the paper has no batched
+ * mode), each phase one launch over all instances, graph capturable.  The
+ * kernels read and write every instance's own arrays through a device table
+ * of instance descriptors; the rows of all instances are numbered one after
+ * another and scheduled together (rows with products at or above their
+ * instance's heavy threshold one block each from a list, the others one warp
+ * each).  Forward: four launches (row flops with the packed and dense copies
+ * of B, row counts, per-instance scan, numeric); backward: two (clear dA/dB,
+ * gradients).  Every instance has its own tuning in its descriptor: the
+ * accumulator (the shared accumulator with occupancy bits over one column
+ * tile of d_b padded to 32, or the dense-B form for d_b <= 256) and the
+ * heavy-row threshold.  d_b is at most 1024.
  *
  * Protocol (descriptor arrays are host arrays of `count` descriptors with
  * device pointers):
- *  1. ts_batched_plan_create reads shapes and nnz only (host).  `force` fixes
- *     tuning fields of the concatenated product (NULL: automatic).
+ *  1. ts_batched_plan_create reads shapes and nnz only (host).  `force`
+ *     fixes, for every instance, accum (TS_ACC_DENSE_B: the dense-B form
+ *     where d_b <= 256 and the product is plus-times; any other non-zero
+ *     value: the shared accumulator) and cta_min_flops (the heavy
+ *     threshold); 0 chooses per instance (dense-B above the density
+ *     crossover of TS_ACC_DENSE_B, threshold 4096).  Other fields are unused.
  *  2. ts_batched_workspace_size, then ts_batched_bounds: computes, on the
  *     device, C_capacity[b] = sum over the rows of A_b of min(d_b, flops_i),
- *     an upper bound on nnz(C_b) (synchronises).  The bounds enlarge the
- *     workspace: query ts_batched_workspace_size again afterwards.
+ *     an upper bound on nnz(C_b) (synchronises).
  *  3. ts_batched_bind: the caller allocates C_b (rowptr n_b+1, col/val with
  *     C_b.nnz >= C_capacity[b]) and binds A, B, C (uploads the descriptors,
  *     synchronises).  ts_batched_bind_grads binds per-instance dC (nnz(C_b)
@@ -378,11 +388,17 @@ TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, 
  *     graph and replayed.  The descriptor / gradient arrays passed must equal
  *     those bound (checked on the host).  After the forward, C_b.rowptr holds
  *     the exact structure and nnz(C_b) = C_b.rowptr[n_b]; an instance whose C
- *     exceeds its capacity keeps only its rowptr and the error is reported by
- *     ts_batched_check.  The backward uses the C pattern of the preceding
- *     forward.
- *  ts_batched_check synchronises and reports device-side errors;
- *  ts_batched_autotune tunes the concatenated product on the bound data.
+ *     exceeds its capacity gets its entries up to the capacity only, and the
+ *     error (TS_ERR_CAPACITY) is reported by ts_batched_check.  The backward
+ *     uses the row flops and the C pattern of the preceding forward.
+ *  ts_batched_check synchronises and reports device-side errors.
+ *  ts_batched_autotune times, instance by instance, every accumulator kind
+ *  it may use and heavy thresholds of 1024, 4096, 16384 products and none
+ *  on that instance alone, keeps the fastest in its descriptor, and leaves
+ *  every C_b computed with the chosen tunings; `chosen` (may be NULL)
+ *  receives instance 0's.  ts_batched_get_tuning reports instance b's
+ *  tuning (accum TS_ACC_DENSE or TS_ACC_DENSE_B, col_tile = its accumulator
+ *  width, cta_min_flops = its heavy threshold).
  */
 TS_API ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A, const ts_csr_desc* B,
                                         int32_t semiring, const ts_tuning* force, ts_batched_plan** out);
@@ -404,6 +420,7 @@ TS_API ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count
 TS_API ts_status ts_batched_check(ts_batched_plan* plan, void* ws, size_t ws_bytes, void* stream);
 TS_API ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tuning* chosen, void* ws,
                                      size_t ws_bytes, void* stream);
+TS_API ts_status ts_batched_get_tuning(const ts_batched_plan* plan, int32_t b, ts_tuning* out);
 
 /*
  * Forward product that allocates nothing (the paper has no counterpart; this

@@ -114,6 +114,7 @@ _SIGS = {
                                         c_size_t, c_void_p]),
     "ts_batched_check": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),
     "ts_batched_autotune": (c_int32, [c_void_p, c_int32, P(Tuning), c_void_p, c_size_t, c_void_p]),
+    "ts_batched_get_tuning": (c_int32, [c_void_p, c_int32, P(Tuning)]),
     "ts_noalloc_scratch_bytes": (c_size_t, []),
     "ts_spgemm_forward_noalloc": (c_int32, [c_void_p, P(CsrDesc), P(CsrDesc), P(CsrDesc), P(c_int64),
                                             c_void_p]),

@@ -1,8 +1,9 @@
 """Batched TS-SpGEMM through the ts_batched_* / ts_spgemm_batched* C ABI.
 
-All instances run as one product (block-diagonal A times stacked B), one
-launch per phase; `forward` and `backward` never synchronise with the host,
-so they can be captured once in a CUDA graph (`capture`) and replayed.
+All instances run together, one launch per phase, each read and written in
+place; every instance keeps its own tuning (accumulator, heavy threshold).
+`forward` and `backward` never synchronise with the host, so they can be
+captured once in a CUDA graph (`capture`) and replayed.
 """
 from __future__ import annotations
 
@@ -101,6 +102,21 @@ class BatchedProduct:
         N.call("ts_batched_autotune", self._h, reps, ctypes.byref(t), _ptr(self._ws), self._ws.numel(),
                _stream(stream))
         return t.as_dict()
+
+    def tuning_summary(self) -> dict:
+        """Per-instance tuning: counts of each accumulator kind and heavy
+        threshold, and the list per instance."""
+        per = []
+        for b in range(self.count):
+            t = N.Tuning()
+            N.call("ts_batched_get_tuning", self._h, b, ctypes.byref(t))
+            per.append({"accum": "dense_b" if t.accum == N.ACC_DENSE_B else "shared",
+                        "width": int(t.col_tile), "heavy_min_flops": int(t.cta_min_flops)})
+        kinds, mins = {}, {}
+        for x in per:
+            kinds[x["accum"]] = kinds.get(x["accum"], 0) + 1
+            mins[str(x["heavy_min_flops"])] = mins.get(str(x["heavy_min_flops"]), 0) + 1
+        return {"accumulators": kinds, "heavy_thresholds": mins, "per_instance": per}
 
     def capture(self, backward: bool = False) -> torch.cuda.CUDAGraph:
         """Capture forward (and backward) once; replay() recomputes them."""

@@ -1094,28 +1094,35 @@ extern "C" ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capaci
 }
 
 // ---------------------------------------------------------------------------
-// batched products: the block-diagonal concatenation as one product
+// batched products: one launch per phase over all instances, each instance
+// read and written in place through a device table of descriptors
 // ---------------------------------------------------------------------------
+static const long long BAT_MAX_D = 1024;
+
 struct ts_batched_plan {
     int count = 0;
     int semiring = 0;
-    std::vector<long long> n, d, annz, bnnz, row_off, annz_off, bnnz_off, cap;
-    long long N = 0, D = 0, NNZA = 0, NNZB = 0, CAP = 0;
-    long long max_rows = 0, max_annz = 0, max_bnnz = 0, max_cap = 0;
-    ts_plan* inner = nullptr;
+    std::vector<long long> n, d, annz, bnnz, row_off, chunk_off, cap;
+    // per-instance tuning: accumulator width, kind, dense copy width, heavy threshold
+    std::vector<int> W, accum, Wd;
+    std::vector<long long> heavy_min;
+    long long N = 0, NC = 0, max_work = 0;  // rows, 32-row chunks (a chunk lies in one instance)
+    int Wmax = 32;
     bool have_bounds = false;
     bool bound = false;
     std::vector<ts_csr_desc> bA, bB, bC;
     std::vector<const float*> gdC;
     std::vector<float*> gdA, gdB;
     bool grads = false;
-    ~ts_batched_plan() { delete inner; }
+    std::vector<InstDesc> host;  // the table last uploaded
 };
 
 struct BLayout {
-    size_t inst = 0, bound = 0, Ap = 0, Ai = 0, Ax = 0, Bp = 0, Bi = 0, Bx = 0, Cp = 0, Ci = 0, Cx = 0;
-    size_t dC = 0, dA = 0, dB = 0, inner = 0, inner_bytes = 0, total = 0;
+    size_t inst = 0, bound = 0, ctl = 0, flops = 0, heavy = 0, total = 0;
+    std::vector<size_t> q, dense;  // per instance: packed copy, dense copy (0: none)
 };
+
+static bool bat_vals(const ts_batched_plan* p) { return p->semiring == TS_SR_PLUS_TIMES_F32; }
 
 static BLayout batched_layout(const ts_batched_plan* p) {
     BLayout L;
@@ -1125,45 +1132,21 @@ static BLayout batched_layout(const ts_batched_plan* p) {
         off += align256(bytes);
         return o;
     };
-    const bool vals = p->semiring == TS_SR_PLUS_TIMES_F32;
     L.inst = take(sizeof(InstDesc) * (size_t)p->count);
     L.bound = take(sizeof(long long) * (size_t)p->count);
-    L.Ap = take(sizeof(long long) * (size_t)(p->N + 1));
-    L.Ai = take(sizeof(int) * (size_t)p->NNZA);
-    L.Ax = vals ? take(sizeof(float) * (size_t)p->NNZA) : 0;
-    L.Bp = take(sizeof(long long) * (size_t)(p->N + 1));
-    L.Bi = take(sizeof(int) * (size_t)p->NNZB);
-    L.Bx = vals ? take(sizeof(float) * (size_t)p->NNZB) : 0;
-    L.Cp = take(sizeof(long long) * (size_t)(p->N + 1));
-    L.Ci = take(sizeof(int) * (size_t)p->CAP);
-    L.Cx = vals ? take(sizeof(float) * (size_t)p->CAP) : 0;
-    if (vals) {
-        L.dC = take(sizeof(float) * (size_t)p->CAP);
-        L.dA = take(sizeof(float) * (size_t)p->NNZA);
-        L.dB = take(sizeof(float) * (size_t)p->NNZB);
+    L.ctl = take(sizeof(BatchCtl));
+    L.flops = take(sizeof(long long) * (size_t)std::max<long long>(p->N, 1));
+    L.heavy = take(sizeof(int) * (size_t)std::max<long long>(p->N, 1));
+    L.q.assign((size_t)p->count, 0);
+    L.dense.assign((size_t)p->count, 0);
+    for (int b = 0; b < p->count; ++b) {
+        L.q[b] = take(padded_b_bytes(p->n[b], p->bnnz[b], p->d[b], 2));
+        // every plus-times instance narrow enough for the dense-B form keeps
+        // room for its dense copy, so that the autotuner may choose it
+        if (bat_vals(p) && p->Wd[b] <= 256) L.dense[b] = take(dense_b_bytes(p->n[b], p->d[b]));
     }
-    size_t inner = 0;
-    ts_workspace_size(p->inner, &inner);
-    L.inner = take(inner);
-    L.inner_bytes = inner;
     L.total = off;
     return L;
-}
-
-static ts_csr_desc cat_desc(char* ws, const ts_batched_plan* p, const BLayout& L, char which) {
-    const bool vals = p->semiring == TS_SR_PLUS_TIMES_F32;
-    ts_csr_desc c{};
-    if (which == 'A') {
-        c = ts_csr_desc{p->N, p->N, p->NNZA, (int64_t*)(ws + L.Ap), (int32_t*)(ws + L.Ai),
-                        vals ? (void*)(ws + L.Ax) : nullptr};
-    } else if (which == 'B') {
-        c = ts_csr_desc{p->N, p->D, p->NNZB, (int64_t*)(ws + L.Bp), (int32_t*)(ws + L.Bi),
-                        vals ? (void*)(ws + L.Bx) : nullptr};
-    } else {
-        c = ts_csr_desc{p->N, p->D, p->CAP, (int64_t*)(ws + L.Cp), (int32_t*)(ws + L.Ci),
-                        vals ? (void*)(ws + L.Cx) : nullptr};
-    }
-    return c;
 }
 
 static ts_status batched_ws_check(const ts_batched_plan* p, void* ws, size_t ws_bytes, const BLayout& L,
@@ -1176,19 +1159,18 @@ static ts_status batched_ws_check(const ts_batched_plan* p, void* ws, size_t ws_
     return TS_OK;
 }
 
-static ts_status upload_insts(ts_batched_plan* p, const ts_csr_desc* A, const ts_csr_desc* B,
-                              const ts_csr_desc* C, char* ws, const BLayout& L, cudaStream_t st, const char* fn) {
-    std::vector<InstDesc> h((size_t)p->count);
+static void fill_insts(ts_batched_plan* p, const ts_csr_desc* A, const ts_csr_desc* B, const ts_csr_desc* C,
+                       char* ws, const BLayout& L) {
+    p->host.assign((size_t)p->count, InstDesc{});
     for (int b = 0; b < p->count; ++b) {
-        InstDesc& I = h[b];
+        InstDesc& I = p->host[b];
         I.n = p->n[b];
         I.d = p->d[b];
         I.annz = p->annz[b];
         I.bnnz = p->bnnz[b];
         I.cap = C ? C[b].nnz : 0;
         I.row_off = p->row_off[b];
-        I.annz_off = p->annz_off[b];
-        I.bnnz_off = p->bnnz_off[b];
+        I.chunk_off = p->chunk_off[b];
         I.A_rowptr = (const long long*)A[b].rowptr;
         I.A_col = A[b].col;
         I.A_val = (const float*)A[b].val;
@@ -1201,9 +1183,37 @@ static ts_status upload_insts(ts_batched_plan* p, const ts_csr_desc* A, const ts
         I.dC = p->grads ? p->gdC[b] : nullptr;
         I.dA = p->grads ? p->gdA[b] : nullptr;
         I.dB = p->grads ? p->gdB[b] : nullptr;
+        I.heavy_min = p->heavy_min[b];
+        I.W = p->W[b];
+        I.accum = p->accum[b];
+        I.Wd = p->Wd[b];
+        I.Bq = (int4*)(ws + L.q[b]);
+        I.Bd = L.dense[b] ? (float*)(ws + L.dense[b]) : nullptr;
+        I.Bbits = L.dense[b] ? (unsigned*)(ws + L.dense[b] + (size_t)p->n[b] * p->Wd[b] * 4) : nullptr;
+        if (!I.Bd) I.accum = BAT_SPARSE;
     }
-    TS_CUDA(cudaMemcpyAsync(ws + L.inst, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice, st), fn);
+}
+
+static ts_status upload_insts(ts_batched_plan* p, const ts_csr_desc* A, const ts_csr_desc* B,
+                              const ts_csr_desc* C, char* ws, const BLayout& L, cudaStream_t st, const char* fn) {
+    fill_insts(p, A, B, C, ws, L);
+    TS_CUDA(cudaMemcpyAsync(ws + L.inst, p->host.data(), sizeof(InstDesc) * p->host.size(), cudaMemcpyHostToDevice,
+                            st),
+            fn);
     TS_CUDA(cudaStreamSynchronize(st), fn);
+    return TS_OK;
+}
+
+static ts_status batched_errors(char* ws, const BLayout& L, cudaStream_t st, const char* fn) {
+    unsigned long long err = 0;
+    TS_CUDA(cudaMemcpyAsync(&err, &((BatchCtl*)(ws + L.ctl))->err, sizeof err, cudaMemcpyDeviceToHost, st), fn);
+    TS_CUDA(cudaStreamSynchronize(st), fn);
+    if (err & ERR_CAPACITY) return fail(TS_ERR_CAPACITY, "%s: an instance's C exceeds its capacity", fn);
+    if (err)
+        return fail(TS_ERR_BAD_CSR, "%s: device checks failed (flags 0x%llx: %s%s%s)", fn, err,
+                    (err & ERR_A_COL) ? "column of A out of range; " : "",
+                    (err & ERR_B_COL) ? "column of B out of range; " : "",
+                    (err & ERR_C_ROW) ? "C row does not match its rowptr; " : "");
     return TS_OK;
 }
 
@@ -1216,42 +1226,51 @@ extern "C" ts_status ts_batched_plan_create(int32_t count, const ts_csr_desc* A,
     if (count < 1 || !A || !B) return fail(TS_ERR_INVALID_ARG, "%s: need count >= 1 and descriptor arrays", fn);
     if (semiring != TS_SR_PLUS_TIMES_F32 && semiring != TS_SR_OR_SELECT2ND_BOOL)
         return fail(TS_ERR_INVALID_ARG, "%s: unknown semiring %d", fn, semiring);
+    const ts_tuning f = force ? *force : ts_tuning{};
+    if (f.cta_min_flops < 0) return fail(TS_ERR_INVALID_ARG, "%s: cta_min_flops must be >= 0", fn);
+    if (f.accum < 0 || f.accum > TS_ACC_DENSE_B) return fail(TS_ERR_INVALID_ARG, "%s: unknown accum", fn);
     ts_batched_plan* p = new ts_batched_plan;
     p->count = count;
     p->semiring = semiring;
+    const bool vals = semiring == TS_SR_PLUS_TIMES_F32;
     for (int b = 0; b < count; ++b) {
         if (A[b].nrows < 0 || A[b].ncols != A[b].nrows || B[b].nrows != A[b].nrows || B[b].ncols < 1 ||
             A[b].nnz < 0 || B[b].nnz < 0) {
             delete p;
             return fail(TS_ERR_INVALID_ARG, "%s: instance %d: A must be n x n and B n x d (d >= 1)", fn, b);
         }
+        if (B[b].ncols > BAT_MAX_D) {
+            delete p;
+            return fail(TS_ERR_UNSUPPORTED, "%s: instance %d: d = %lld above the batched limit %lld", fn, b,
+                        (long long)B[b].ncols, BAT_MAX_D);
+        }
         p->n.push_back(A[b].nrows);
         p->d.push_back(B[b].ncols);
         p->annz.push_back(A[b].nnz);
         p->bnnz.push_back(B[b].nnz);
         p->row_off.push_back(p->N);
-        p->annz_off.push_back(p->NNZA);
-        p->bnnz_off.push_back(p->NNZB);
+        p->chunk_off.push_back(p->NC);
         p->N += A[b].nrows;
-        p->NNZA += A[b].nnz;
-        p->NNZB += B[b].nnz;
-        p->D = std::max<long long>(p->D, B[b].ncols);
-        p->max_rows = std::max<long long>(p->max_rows, A[b].nrows + 1);
-        p->max_annz = std::max<long long>(p->max_annz, A[b].nnz);
-        p->max_bnnz = std::max<long long>(p->max_bnnz, B[b].nnz);
+        p->NC += (A[b].nrows + 31) / 32;
+        const int w = (int)round_up(B[b].ncols, 32);
+        int wd = 32;
+        while (wd < w) wd *= 2;
+        p->W.push_back(w);
+        p->Wd.push_back(wd);
+        p->Wmax = std::max(p->Wmax, w);
+        // default tuning of the instance; `force` fixes a field for all
+        const bool dense = f.accum == TS_ACC_DENSE_B ? (vals && wd <= 256)
+                         : f.accum == 0 ? (dense_b_auto(vals, B[b].ncols, A[b].nrows, B[b].nnz) && wd <= 256)
+                                         : false;
+        p->accum.push_back(dense ? BAT_DENSE_B : BAT_SPARSE);
+        p->heavy_min.push_back(f.cta_min_flops ? f.cta_min_flops : 4096);
+        p->max_work = std::max<long long>(p->max_work, std::max<long long>(A[b].nnz, B[b].nnz));
     }
     if (p->N > INT32_MAX) {
         delete p;
         return fail(TS_ERR_UNSUPPORTED, "%s: more than 2^31-1 rows in total", fn);
     }
     p->cap.assign((size_t)count, 0);
-    const ts_csr_desc iA{p->N, p->N, p->NNZA, nullptr, nullptr, nullptr};
-    const ts_csr_desc iB{p->N, p->D, p->NNZB, nullptr, nullptr, nullptr};
-    ts_status s = ts_plan_create(&iA, &iB, semiring, force, &p->inner);
-    if (s != TS_OK) {
-        delete p;
-        return s;
-    }
     *out = p;
     return ok();
 }
@@ -1267,6 +1286,42 @@ extern "C" ts_status ts_batched_workspace_size(const ts_batched_plan* plan, size
     return ok();
 }
 
+extern "C" ts_status ts_batched_get_tuning(const ts_batched_plan* plan, int32_t b, ts_tuning* out) {
+    if (!plan || !out || b < 0 || b >= plan->count)
+        return fail(TS_ERR_INVALID_ARG, "ts_batched_get_tuning: bad arguments");
+    ts_tuning t{};
+    t.accum = plan->accum[b] == BAT_DENSE_B ? TS_ACC_DENSE_B : TS_ACC_DENSE;
+    t.col_tile = plan->W[b];
+    t.cta_min_flops = plan->heavy_min[b];
+    t.warps_per_cta = 8;
+    t.row_lanes = 1;
+    t.pack_b = 1;
+    *out = t;
+    return ok();
+}
+
+// The forward passes over instances [b0, b0 + nb) (rows g0 .. g1 - 1).
+static ts_status bat_forward(ts_batched_plan* plan, char* w, const BLayout& L, int b0, int nb, cudaStream_t st,
+                             const char* fn, bool numeric = true) {
+    const InstDesc* inst = (const InstDesc*)(w + L.inst) + b0;
+    BatchCtl* ctl = (BatchCtl*)(w + L.ctl);
+    long long* flops = (long long*)(w + L.flops);
+    int* heavy = (int*)(w + L.heavy);
+    const long long g0 = plan->row_off[b0];
+    const long long g1 = plan->row_off[b0 + nb - 1] + plan->n[b0 + nb - 1];
+    const long long c0 = plan->chunk_off[b0];
+    const long long c1 = plan->chunk_off[b0 + nb - 1] + (plan->n[b0 + nb - 1] + 31) / 32;
+    const int sms = sm_count();
+    TS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(BatchCtl), st), fn);
+    TS_CUDA(launch_bat_prepare(inst, nb, g0, g1, flops, heavy, ctl, sms, st), fn);
+    if (!numeric) return TS_OK;
+    TS_CUDA(launch_bat_symbolic(inst, nb, c0, c1, 0, flops, heavy, ctl, plan->Wmax, sms, st), fn);
+    TS_CUDA(launch_bat_scan(inst, nb, ctl, st), fn);
+    TS_CUDA(launch_bat_numeric(inst, nb, c0, c1, bat_vals(plan) ? 1 : 0, flops, heavy, ctl, plan->Wmax, sms, st),
+            fn);
+    return TS_OK;
+}
+
 extern "C" ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc* A, const ts_csr_desc* B,
                                        int64_t* C_capacity, void* ws, size_t ws_bytes, void* stream) {
     const char* fn = "ts_batched_bounds";
@@ -1274,7 +1329,7 @@ extern "C" ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc*
     const BLayout L = batched_layout(plan);
     ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
-    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    const bool vals = bat_vals(plan);
     for (int b = 0; b < plan->count; ++b) {
         if (A[b].nrows != plan->n[b] || A[b].nnz != plan->annz[b] || B[b].ncols != plan->d[b] ||
             B[b].nnz != plan->bnnz[b])
@@ -1284,26 +1339,16 @@ extern "C" ts_status ts_batched_bounds(ts_batched_plan* plan, const ts_csr_desc*
     cudaStream_t st = (cudaStream_t)stream;
     char* w = (char*)ws;
     if ((s = upload_insts(plan, A, B, nullptr, w, L, st, fn)) != TS_OK) return s;
-    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B');
+    if ((s = bat_forward(plan, w, L, 0, plan->count, st, fn, false)) != TS_OK) return s;
     const InstDesc* inst = (const InstDesc*)(w + L.inst);
-    TS_CUDA(launch_batch_gather(inst, plan->count, std::max(plan->max_rows, std::max(plan->max_annz, plan->max_bnnz)),
-                                (long long*)cA.rowptr, cA.col, (float*)cA.val, (long long*)cB.rowptr, cB.col,
-                                (float*)cB.val, st),
+    TS_CUDA(launch_batch_bounds(inst, plan->count, (const long long*)(w + L.flops), (long long*)(w + L.bound), st),
             fn);
-    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
-    const Sched sc = carve(w + L.inner, IL);
-    TS_CUDA(launch_row_flops(dev(&cA), dev(&cB), sc, st), fn);
-    TS_CUDA(launch_batch_bounds(inst, plan->count, sc.flops, (long long*)(w + L.bound), st), fn);
     std::vector<long long> bnd((size_t)plan->count);
     TS_CUDA(cudaMemcpyAsync(bnd.data(), w + L.bound, sizeof(long long) * bnd.size(), cudaMemcpyDeviceToHost, st), fn);
-    if ((s = read_errors(w + L.inner, IL, st, fn)) != TS_OK) return s;
-    plan->CAP = 0;
-    plan->max_cap = 0;
+    if ((s = batched_errors(w, L, st, fn)) != TS_OK) return s;
     for (int b = 0; b < plan->count; ++b) {
         plan->cap[b] = bnd[b];
         C_capacity[b] = bnd[b];
-        plan->CAP += bnd[b];
-        plan->max_cap = std::max(plan->max_cap, bnd[b]);
     }
     plan->have_bounds = true;
     plan->bound = false;
@@ -1318,7 +1363,7 @@ extern "C" ts_status ts_batched_bind(ts_batched_plan* plan, const ts_csr_desc* A
     const BLayout L = batched_layout(plan);
     ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
-    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
+    const bool vals = bat_vals(plan);
     for (int b = 0; b < plan->count; ++b) {
         if (A[b].nrows != plan->n[b] || A[b].nnz != plan->annz[b] || B[b].ncols != plan->d[b] ||
             B[b].nnz != plan->bnnz[b])
@@ -1381,23 +1426,8 @@ extern "C" ts_status ts_spgemm_batched(ts_batched_plan* plan, int32_t count, con
     const BLayout L = batched_layout(plan);
     ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    char* w = (char*)ws;
-    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
-    const InstDesc* inst = (const InstDesc*)(w + L.inst);
-    TS_CUDA(launch_batch_gather(inst, plan->count, std::max(plan->max_rows, std::max(plan->max_annz, plan->max_bnnz)),
-                                (long long*)cA.rowptr, cA.col, (float*)cA.val, (long long*)cB.rowptr, cB.col,
-                                (float*)cB.val, st),
-            fn);
-    if ((s = ts_spgemm_symbolic(plan->inner, &cA, &cB, cC.rowptr, nullptr, w + L.inner, L.inner_bytes, stream)) != TS_OK)
-        return s;
-    if ((s = ts_spgemm_numeric(plan->inner, &cA, &cB, &cC, w + L.inner, L.inner_bytes, stream)) != TS_OK) return s;
-    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
-    TS_CUDA(launch_batch_scatter(inst, plan->count, std::max(plan->max_rows, plan->max_cap), (const long long*)cC.rowptr,
-                                 cC.col,
-                                 (const float*)cC.val, &carve(w + L.inner, IL).hdr->err, st),
-            fn);
-    return ok();
+    s = bat_forward(plan, (char*)ws, L, 0, plan->count, (cudaStream_t)stream, fn);
+    return s == TS_OK ? ok() : s;
 }
 
 extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t count,
@@ -1418,15 +1448,13 @@ extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t c
     if (s != TS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     char* w = (char*)ws;
-    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
-    const InstDesc* inst = (const InstDesc*)(w + L.inst);
-    float* dC = (float*)(w + L.dC);
-    float* dA = (float*)(w + L.dA);
-    float* dB = (float*)(w + L.dB);
-    TS_CUDA(launch_batch_gather_dc(inst, plan->count, plan->max_cap, (const long long*)cC.rowptr, dC, st), fn);
-    if ((s = ts_spgemm_backward(plan->inner, &cA, &cB, &cC, dC, dA, dB, w + L.inner, L.inner_bytes, stream)) != TS_OK)
-        return s;
-    TS_CUDA(launch_batch_scatter_grads(inst, plan->count, std::max(plan->max_annz, plan->max_bnnz), dA, dB, st), fn);
+    BatchCtl* ctl = (BatchCtl*)(w + L.ctl);
+    // the backward reuses the forward's row flops, heavy list and C pattern
+    TS_CUDA(cudaMemsetAsync(&ctl->q_bwd, 0, sizeof ctl->q_bwd, st), fn);
+    TS_CUDA(launch_bat_backward((const InstDesc*)(w + L.inst), plan->count, 0, plan->N, plan->max_work,
+                                (const long long*)(w + L.flops), (const int*)(w + L.heavy), ctl, plan->Wmax,
+                                sm_count(), st),
+            fn);
     return ok();
 }
 
@@ -1436,27 +1464,70 @@ extern "C" ts_status ts_batched_check(ts_batched_plan* plan, void* ws, size_t ws
     const BLayout L = batched_layout(plan);
     ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
-    const Layout IL = plan_layout(plan->inner->n, plan->inner->d, plan->inner->cur, plan->NNZA, plan->NNZB);
-    s = read_errors((char*)ws + L.inner, IL, (cudaStream_t)stream, fn);
+    s = batched_errors((char*)ws, L, (cudaStream_t)stream, fn);
     return s == TS_OK ? ok() : s;
 }
 
+// Per instance, every candidate (accumulator kind x heavy-row threshold) is
+// timed on that instance alone (its four forward launches over its rows
+// only) and the fastest kept in its descriptor.
 extern "C" ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tuning* chosen, void* ws,
                                          size_t ws_bytes, void* stream) {
     const char* fn = "ts_batched_autotune";
     if (!plan || !plan->bound) return fail(TS_ERR_STATE, "%s: bind the plan first", fn);
+    if (reps < 1) return fail(TS_ERR_INVALID_ARG, "%s: reps must be >= 1", fn);
     const BLayout L = batched_layout(plan);
     ts_status s = batched_ws_check(plan, ws, ws_bytes, L, fn);
     if (s != TS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
     char* w = (char*)ws;
-    const ts_csr_desc cA = cat_desc(w, plan, L, 'A'), cB = cat_desc(w, plan, L, 'B'), cC = cat_desc(w, plan, L, 'C');
-    // one forward leaves the concatenated operands and the schedule in ws
-    if ((s = ts_spgemm_batched(plan, plan->count, plan->bA.data(), plan->bB.data(), plan->bC.data(), ws, ws_bytes,
-                               stream)) != TS_OK)
-        return s;
-    const bool vals = plan->semiring == TS_SR_PLUS_TIMES_F32;
-    s = ts_plan_autotune(plan->inner, &cA, &cB, &cC, vals ? (const float*)(w + L.dC) : nullptr,
-                         vals ? (float*)(w + L.dA) : nullptr, vals ? (float*)(w + L.dB) : nullptr, reps, chosen,
-                         w + L.inner, L.inner_bytes, stream);
-    return s;
+    cudaEvent_t e0, e1;
+    TS_CUDA(cudaEventCreate(&e0), fn);
+    TS_CUDA(cudaEventCreate(&e1), fn);
+    const long long mins[] = {1024, 4096, 16384, 1LL << 50};
+    for (int b = 0; b < plan->count && s == TS_OK; ++b) {
+        if (plan->n[b] == 0) continue;
+        int best_acc = plan->accum[b];
+        long long best_min = plan->heavy_min[b];
+        float best_ms = 1e30f;
+        for (int acc = BAT_SPARSE; acc <= BAT_DENSE_B && s == TS_OK; ++acc) {
+            if (acc == BAT_DENSE_B && !L.dense[b]) continue;
+            for (long long hm : mins) {
+                plan->accum[b] = acc;
+                plan->heavy_min[b] = hm;
+                fill_insts(plan, plan->bA.data(), plan->bB.data(), plan->bC.data(), w, L);
+                if (cudaMemcpyAsync(w + L.inst + b * sizeof(InstDesc), &plan->host[b], sizeof(InstDesc),
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                    s = cuda_fail(cudaGetLastError(), fn);
+                    break;
+                }
+                float tot = 0.0f;
+                for (int r = 0; r <= reps && s == TS_OK; ++r) {
+                    if (cudaEventRecord(e0, st) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+                    if (s == TS_OK) s = bat_forward(plan, w, L, b, 1, st, fn);
+                    if (s == TS_OK && cudaEventRecord(e1, st) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+                    if (s == TS_OK && cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+                    float ms = 0.0f;
+                    if (s == TS_OK) cudaEventElapsedTime(&ms, e0, e1);
+                    if (r > 0) tot += ms;
+                }
+                if (s == TS_OK && tot / reps < best_ms) {
+                    best_ms = tot / reps;
+                    best_acc = acc;
+                    best_min = hm;
+                }
+            }
+        }
+        plan->accum[b] = best_acc;
+        plan->heavy_min[b] = best_min;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TS_OK) return s;
+    if ((s = upload_insts(plan, plan->bA.data(), plan->bB.data(), plan->bC.data(), w, L, st, fn)) != TS_OK) return s;
+    // leave every C_b holding the product of the chosen tunings
+    if ((s = bat_forward(plan, w, L, 0, plan->count, st, fn)) != TS_OK) return s;
+    if ((s = batched_errors(w, L, st, fn)) != TS_OK) return s;
+    if (chosen) ts_batched_get_tuning(plan, 0, chosen);
+    return ok();
 }

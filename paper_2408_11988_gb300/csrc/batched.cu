@@ -1,67 +1,682 @@
 // Batched TS-SpGEMM: many independent products C_b = A_b * B_b of uneven
-// shapes.  The batch is the single product of the block-diagonal matrix
-// diag(A_1, ..., A_m) with the stacked matrix [B_1; ...; B_m] (every B_b has
-// columns < d_b <= d_max), whose row block b is exactly C_b.  One kernel
-// gathers the instances into that product's arrays, the single-product passes
-// run once over all rows (one launch per phase), and one kernel scatters the
-// rows back into the instances' own C (and gradient) arrays.  Nothing here
-// synchronises with the host, so the whole sequence can be captured in a
-// CUDA graph and replayed.
+// shapes, each phase one launch over all instances, graph capturable.
+//
+// The kernels read every instance's own arrays through a device table of
+// instance descriptors (InstDesc): there is no copy of the instances into a
+// common product and no copy of the results back.  The rows of all
+// instances are numbered one after another (instance b owns rows
+// row_off_b .. row_off_b + n_b - 1); a kernel finds a row's instance by a
+// binary search over the table.  Each descriptor carries that instance's
+// own tuning: its accumulator width W_b (one column tile of the instance's
+// 32-column-padded d_b), its accumulator kind (the shared accumulator with
+// occupancy bits, or the dense-B form for a dense enough B_b) and its
+// heavy-row threshold.
+//
+// Forward (four launches): prepare (row flops, the row-aligned packed copy
+// of each B_b and, for dense-B instances, the dense copy; rows at or above
+// their instance's threshold go on the heavy list), symbolic (row counts
+// into each C_b's row pointers: heavy rows one block each from the list,
+// light rows one warp each in row order), scan (one block per instance),
+// numeric (as the symbolic pass, writing each C_b).  Backward (two
+// launches): the gradients are cleared, then dA by rows and dB by float
+// atomics.  Nothing waits on another block: the only coordination is
+// atomic counters over the heavy list.
 #include "common.cuh"
+#include "denseb.cuh"
 #include "kernels.h"
+#include "numeric.cuh"
+#include "rowgroup.cuh"
+#include "wide.cuh"
 
 namespace ts {
 
-// Gather the instances into the concatenated CSR arrays.  Row r of instance
-// b becomes row row_off + r; column k of A_b becomes row_off + k (block
-// diagonal); B's columns are unchanged.  blockIdx.y = instance.
-__global__ void __launch_bounds__(256) k_batch_gather(const InstDesc* __restrict__ inst, long long* Ap, int* Ai,
-                                                      float* Ax, long long* Bp, int* Bi, float* Bx) {
-    const InstDesc I = inst[blockIdx.y];
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = t0; i <= I.n; i += stride) {
-        Ap[I.row_off + i] = clampll(I.A_rowptr[i], 0, I.annz) + I.annz_off;
-        Bp[I.row_off + i] = clampll(I.B_rowptr[i], 0, I.bnnz) + I.bnnz_off;
+// Instance of global row g (the last instance whose first row is <= g; an
+// instance without rows shares its first row with the next one).
+__device__ __forceinline__ int inst_of(const InstDesc* __restrict__ inst, int count, long long g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&inst[mid].row_off) <= g) lo = mid;
+        else hi = mid - 1;
     }
-    for (long long e = t0; e < I.annz; e += stride) {
-        const int k = I.A_col[e];
-        Ai[I.annz_off + e] = ((unsigned)k < (unsigned)I.n) ? (int)(I.row_off + k) : -1;  // -1: caught as bad column
-        if (Ax) Ax[I.annz_off + e] = I.A_val[e];
+    return lo;
+}
+
+// The single-product parameters the shared walks read, for instance I.
+__device__ __forceinline__ NumParams inst_params(const InstDesc& I) {
+    NumParams p{};
+    p.Ap = I.A_rowptr;
+    p.Ai = I.A_col;
+    p.Ax = I.A_val;
+    p.nnzA = I.annz;
+    p.Bp = I.B_rowptr;
+    p.Bi = I.B_col;
+    p.Bx = I.B_val;
+    p.Bq = I.Bq;
+    p.nnzB = I.bnnz;
+    p.nB = (int)I.n;
+    p.d = (int)I.d;
+    p.W = I.W;
+    p.T = 1;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// prepare: four rows per warp, eight lanes per row (coalesced reads of the
+// row's entries)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bat_prepare(const InstDesc* __restrict__ inst, int count, long long g0,
+                                                     long long g1, long long* __restrict__ flops,
+                                                     int* __restrict__ heavy, BatchCtl* ctl) {
+    const int lane = lane_id(), gl = lane & 7, slot = lane >> 3;
+    bool bad_a = false, bad_b = false;
+    const long long step = ((long long)gridDim.x * blockDim.x >> 5) * 4;
+    for (long long base = g0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; base < g1;
+         base += step) {
+        const long long g = base + slot;
+        const bool act = g < g1;
+        const InstDesc& I = inst[act ? inst_of(inst, count, g) : 0];
+        const long long i = act ? g - I.row_off : 0;
+        // products of row i of A_b: eight lanes over its entries, summed
+        long long f = 0;
+        if (act) {
+            const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+            for (long long e = a0 + gl; e < a1; e += 8) {
+                const int k = __ldg(I.A_col + e);
+                if ((unsigned)k < (unsigned)I.n) {
+                    const long long s = clampll(__ldg(I.B_rowptr + k), 0, I.bnnz);
+                    const long long t = clampll(__ldg(I.B_rowptr + k + 1), s, I.bnnz);
+                    f += t - s < I.d ? t - s : I.d;
+                } else {
+                    bad_a = true;
+                }
+            }
+        }
+        f += __shfl_xor_sync(FULL, f, 1);
+        f += __shfl_xor_sync(FULL, f, 2);
+        f += __shfl_xor_sync(FULL, f, 4);
+        if (act && gl == 0) {
+            flops[g] = f;
+            if (f > 0 && f >= I.heavy_min) heavy[atomicAdd(&ctl->nheavy, 1ull)] = (int)g;
+        }
+        // row i of B_b: its packed pairs (pads and bad columns as -1), and
+        // for a dense-B instance its dense row and pattern words
+        long long s = 0;
+        int len = 0;
+        unsigned q0 = 0;
+        if (act) padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, (int)i, s, len, q0);
+        const bool dense = act && I.accum == BAT_DENSE_B && I.Bd;
+        float* r = dense ? I.Bd + (size_t)i * I.Wd : nullptr;
+        unsigned* bw = dense ? I.Bbits + (size_t)i * (I.Wd >> 5) : nullptr;
+        if (dense) {  // cleared before the entries land
+            for (int c = 4 * gl; c < I.Wd; c += 32) *reinterpret_cast<float4*>(r + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int x = gl; x < (I.Wd >> 5); x += 8) bw[x] = 0u;
+        }
+        __syncwarp();
+        if (act) {
+            int2* Q = reinterpret_cast<int2*>(I.Bq) + 2 * (size_t)q0;
+            const int span = (len + 1) & ~1;
+            for (int j = gl; j < span; j += 8) {
+                int2 v = make_int2(-1, 0);
+                if (j < len) {
+                    const int c = __ldg(I.B_col + s + j);
+                    if ((unsigned)c < (unsigned)I.d) {
+                        const float x = I.B_val ? __ldg(I.B_val + s + j) : 0.0f;
+                        v = make_int2(c, __float_as_int(x));
+                        if (dense) {
+                            r[c] = x;
+                            atomicOr(bw + (c >> 5), 1u << (c & 31));
+                        }
+                    } else {
+                        bad_b = true;
+                    }
+                }
+                Q[j] = v;
+            }
+        }
+        __syncwarp();
     }
-    for (long long e = t0; e < I.bnnz; e += stride) {
-        const int c = I.B_col[e];
-        Bi[I.bnnz_off + e] = ((unsigned)c < (unsigned)I.d) ? c : -1;
-        if (Bx) Bx[I.bnnz_off + e] = I.B_val[e];
+    if (bad_a) atomicOr(&ctl->err, ERR_A_COL);
+    if (bad_b) atomicOr(&ctl->err, ERR_B_COL);
+}
+
+// Instance of 32-row chunk c (the last instance whose first chunk is <= c).
+__device__ __forceinline__ int inst_of_chunk(const InstDesc* __restrict__ inst, int count, long long c) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&inst[mid].chunk_off) <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Ascending bitonic sort of one key per lane across the warp, carrying val.
+__device__ __forceinline__ void warp_sort_asc(int& key, int& val) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int pk = __shfl_xor_sync(FULL, key, j), pv = __shfl_xor_sync(FULL, val, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            if (keep_min ? pk < key : pk > key) {
+                key = pk;
+                val = pv;
+            }
+        }
     }
 }
 
-// Scatter rows of the concatenated C back into each instance's C: rebased row
-// pointers, then the instance's range of columns and values.  An instance
-// whose C does not fit its capacity gets ERR_CAPACITY and its rowptr only.
-__global__ void __launch_bounds__(256) k_batch_scatter(const InstDesc* __restrict__ inst, const long long* Cp,
-                                                       const int* Ci, const float* Cx, unsigned long long* err) {
-    const InstDesc I = inst[blockIdx.y];
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long base = Cp[I.row_off], end = Cp[I.row_off + I.n];
-    const long long cnt = end - base;
-    for (long long i = t0; i <= I.n; i += stride) I.C_rowptr[i] = Cp[I.row_off + i] - base;
-    if (cnt > I.cap) {
-        if (t0 == 0) atomicOr(err, ERR_CAPACITY);
-        return;
+// Light rows of one 32-row chunk of instance I, sorted by products
+// (heaviest first) so that the four rows a warp takes side by side have
+// nearly equal lengths: returns the count L; sorted position t of the warp
+// holds row base + srt (lanes >= L hold no row).
+__device__ __forceinline__ int chunk_light_sorted(const InstDesc& I, const long long* __restrict__ flops,
+                                                  long long i0, int& srt) {
+    const int lane = lane_id();
+    const long long i = i0 + lane;
+    const long long f = i < I.n ? __ldg(flops + I.row_off + i) : 0;
+    const bool light = f > 0 && f < I.heavy_min;
+    int key = light ? -(int)(f < (1LL << 30) ? f : (1LL << 30)) : 0x7FFFFFFF;
+    srt = lane;
+    warp_sort_asc(key, srt);
+    return __popc(__ballot_sync(FULL, light));
+}
+
+// Whether global row g (lane's row of a 32-row chunk) is a light row: it
+// has products and fewer than its instance's threshold.
+__device__ __forceinline__ bool bat_light(const InstDesc* inst, int count, const long long* flops, long long g,
+                                          long long g1, int& b) {
+    b = 0;
+    if (g >= g1) return false;
+    const long long f = __ldg(flops + g);
+    if (f <= 0) return false;
+    b = inst_of(inst, count, g);
+    return f < __ldg(&inst[b].heavy_min);
+}
+
+// ---------------------------------------------------------------------------
+// symbolic: row counts into each C_b's row pointers (C_b.rowptr[i + 1])
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict__ inst, int count, long long c0,
+                                                      long long c1, const long long* __restrict__ flops,
+                                                      const int* __restrict__ heavy, BatchCtl* ctl) {
+    __shared__ unsigned s_bm[9][33];   // the block's bitmap (heavy rows) in s_bm[8]
+    __shared__ unsigned s_rg[8][4 * 33];  // four slot bitmaps per warp (light rows)
+    __shared__ long long s_item;
+    const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    for (int x = tid; x < 9 * 33; x += blockDim.x) (&s_bm[0][0])[x] = 0u;
+    for (int x = tid; x < 8 * 4 * 33; x += blockDim.x) (&s_rg[0][0])[x] = 0u;
+    __syncthreads();
+    unsigned long long* err = &ctl->err;
+    const long long nheavy = (long long)ctl->nheavy;
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&ctl->q_sym, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const long long g = heavy[h];
+        const InstDesc& I = inst[inst_of(inst, count, g)];
+        const long long i = g - I.row_off;
+        const NumParams p = inst_params(I);
+        const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+        // chunk by chunk, stopping once the row's bitmap holds all d columns
+        // (its count is then d whatever products remain)
+        const int nwd = I.W >> 5;
+        const unsigned last = (I.d & 31) ? (1u << (I.d & 31)) - 1u : 0xFFFFFFFFu;
+        for (long long e = a0 + 32LL * warp; e < a1; e += 32LL * nwarps) {
+            wide_range(p, AddMark{s_bm[8]}, e, e + 32 < a1 ? e + 32 : a1, 32, err);
+            __syncwarp();
+            const unsigned want = lane < nwd - 1 ? 0xFFFFFFFFu : (lane == nwd - 1 ? last : 0u);
+            if (__all_sync(FULL, lane >= nwd || (s_bm[8][lane] & want) == want)) break;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = I.W >> 5;
+            const int c = warp_sum(lane < nw ? __popc(s_bm[8][lane]) : 0);
+            if (lane == 0) I.C_rowptr[i + 1] = c;
+            if (lane < nw) s_bm[8][lane] = 0u;
+        }
+        __syncthreads();
     }
-    for (long long e = t0; e < cnt; e += stride) {
-        I.C_col[e] = Ci[base + e];
-        if (I.C_val && Cx) I.C_val[e] = Cx[base + e];
+    // light rows in row groups: four rows per warp (eight lanes each, the
+    // chunk's rows sorted by products), each marking its own bitmap
+    unsigned* rbm = s_rg[warp];
+    const int lanes = lane & 7, slot = lane >> 3;
+    unsigned* mybm = rbm + 33 * slot;
+    for (long long c = c0 + (long long)blockIdx.x * nwarps + warp; c < c1; c += (long long)gridDim.x * nwarps) {
+        const InstDesc& I = inst[inst_of_chunk(inst, count, c)];
+        const long long i0 = (c - I.chunk_off) * 32;
+        {
+            const long long i = i0 + lane;
+            if (i < I.n && __ldg(flops + I.row_off + i) <= 0) I.C_rowptr[i + 1] = 0;
+        }
+        int srt;
+        const int L = chunk_light_sorted(I, flops, i0, srt);
+        const NumParams p = inst_params(I);
+        const int nw = I.W >> 5;
+        for (int t = 0; t < L; t += 4) {
+            const int pos = t + slot;
+            const int r = __shfl_sync(FULL, srt, pos & 31);
+            const bool active = pos < L;
+            const long long i = i0 + r;
+            long long a0 = 0;
+            int len = 0;
+            if (active) {
+                a0 = clampll(I.A_rowptr[i], 0, I.annz);
+                len = (int)(clampll(I.A_rowptr[i + 1], a0, I.annz) - a0);
+            }
+            const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+            int k0, k1;
+            float x0, x1;
+            rg_load_a(p, a0 + lanes, lanes < len, k0, x0);
+            rg_load_a(p, a0 + 8 + lanes, 8 + lanes < len, k1, x1);
+            rgp_tile<8, 2>(p, I.Bq, AddMark{mybm}, a0, len, lmax, err, k0, x0, k1, x1);
+            __syncwarp();
+            int cnt = 0;
+            for (int w = lanes; w < nw; w += 8) {
+                cnt += __popc(mybm[w]);
+                mybm[w] = 0u;
+            }
+            cnt += __shfl_xor_sync(FULL, cnt, 1);
+            cnt += __shfl_xor_sync(FULL, cnt, 2);
+            cnt += __shfl_xor_sync(FULL, cnt, 4);
+            if (active && lanes == 0) I.C_rowptr[i + 1] = cnt;
+            __syncwarp();
+        }
     }
 }
 
-// Upper bound on nnz(C_b): sum over its rows of min(d_b, flops_i), from the
-// flops of the concatenated product.  Block per instance.
+// ---------------------------------------------------------------------------
+// scan: one block of 1024 threads per instance, in place over C_b.rowptr
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_bat_scan(const InstDesc* __restrict__ inst, BatchCtl* ctl) {
+    __shared__ long long s_w[32];
+    __shared__ long long s_carry;
+    const InstDesc& I = inst[blockIdx.x];
+    long long* rp = I.C_rowptr;
+    const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
+    if (tid == 0) {
+        s_carry = 0;
+        rp[0] = 0;
+    }
+    __syncthreads();
+    constexpr int ITEMS = 4;
+    for (long long base = 1; base <= I.n; base += 1024LL * ITEMS) {
+        long long v[ITEMS];
+        long long t = 0;
+#pragma unroll
+        for (int u = 0; u < ITEMS; ++u) {
+            const long long x = base + (long long)tid * ITEMS + u;
+            v[u] = x <= I.n ? rp[x] : 0;
+            t += v[u];
+            v[u] = t;  // running sum inside the thread
+        }
+        const long long wi = warp_incl_scan(t);
+        if (lane == 31) s_w[warp] = wi;
+        __syncthreads();
+        if (warp == 0) {
+            const long long y = warp_incl_scan(s_w[lane]);
+            s_w[lane] = y;
+        }
+        __syncthreads();
+        const long long before = s_carry + (warp ? s_w[warp - 1] : 0) + wi - t;
+#pragma unroll
+        for (int u = 0; u < ITEMS; ++u) {
+            const long long x = base + (long long)tid * ITEMS + u;
+            if (x <= I.n) rp[x] = before + v[u];
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += s_w[31];
+        __syncthreads();
+    }
+    if (tid == 0 && s_carry > I.cap) atomicOr(&ctl->err, ERR_CAPACITY);
+}
+
+// ---------------------------------------------------------------------------
+// numeric
+// ---------------------------------------------------------------------------
+// Row i of a dense-B instance summed by `first`/`stride` chunks of this warp
+// (registers), V = Wd / 32 columns per lane.
+template <int V>
+__device__ __forceinline__ void bat_dense_row(const NumParams& p, const InstDesc& I, long long i, long long a0,
+                                              long long a1, bool team, float* s_rows, unsigned* s_mask,
+                                              unsigned long long* err) {
+    float acc[V];
+    unsigned m = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+    const int nwarps = blockDim.x >> 5;
+    if (team) {
+        dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0 + 32LL * warp_id(), a1, 32LL * nwarps, acc, m, err);
+        dense_block_sum<V>(acc, m, s_rows, s_mask);
+        if (warp_id() != 0) return;
+    } else {
+        dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0, a1, 32, acc, m, err);
+    }
+    const long long out = clampll(I.C_rowptr[i], 0, I.cap);
+    const long long out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
+    const int tot = dense_emit<V>(acc, m, out, out_end, I.C_col, I.C_val);
+    if (lane_id() == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+}
+
+__device__ __forceinline__ void bat_dense_any(const NumParams& p, const InstDesc& I, long long i, long long a0,
+                                              long long a1, bool team, float* s_rows, unsigned* s_mask,
+                                              unsigned long long* err) {
+    switch (I.Wd) {
+        case 32: bat_dense_row<1>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
+        case 64: bat_dense_row<2>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
+        case 128: bat_dense_row<4>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
+        default: bat_dense_row<8>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
+    }
+}
+
+// Words of shared memory per warp in the numeric kernel: a shared
+// accumulator of Wmax + 8 floats and Wmax/32 + 1 bitmap words, or, for
+// plus-times with Wmax <= 256, four row-group accumulators of Wmax + 8.
+__host__ __device__ inline int bat_per_warp(int Wmax, bool values) {
+    const int wide = (Wmax + 8) + Wmax / 32 + 1;
+    const int rg = 4 * (Wmax + 8);
+    return (values && Wmax <= 256 && rg > wide) ? rg : wide;
+}
+
+// Heavy rows (one block each, per-warp shared accumulators summed by the
+// block, or the dense-B form), then light rows (one warp each, in row
+// order).  Dynamic shared memory per warp: Wmax + 8 floats of accumulator
+// and Wmax/32 + 1 bitmap words.
+__global__ void __launch_bounds__(256, 3) k_bat_numeric(const InstDesc* __restrict__ inst, int count, long long c0,
+                                                        long long c1, const long long* __restrict__ flops,
+                                                        const int* __restrict__ heavy, BatchCtl* ctl, int Wmax,
+                                                        bool values) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_rows[8 * 256];
+    __shared__ unsigned s_mask[8 * 32];
+    __shared__ long long s_item;
+    const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    const int ld = Wmax + 8;
+    const int per_warp = bat_per_warp(Wmax, values);  // 4-byte words
+    // plus-times with every width <= 256: row groups (accumulators start
+    // RG_EMPTY; 32 slots of Wmax + 8, then a summed row of Wmax for heavy
+    // rows); otherwise per-warp shared accumulators (start at 0)
+    const bool rg = values && Wmax <= 256;
+    for (int x = tid; x < nwarps * per_warp + (rg ? Wmax : 0); x += blockDim.x)
+        reinterpret_cast<unsigned*>(smem)[x] = rg ? RG_EMPTY : 0u;
+    __shared__ int s_wcnt[256 / 32 + 1];
+    __syncthreads();
+    unsigned long long* err = &ctl->err;
+    float* wacc = reinterpret_cast<float*>(smem) + (size_t)warp * per_warp;
+    unsigned* wbm = reinterpret_cast<unsigned*>(wacc) + ld;
+    const AddShared wadd{wacc, wbm};
+    float* acc0 = reinterpret_cast<float*>(smem);
+    unsigned* bm0 = reinterpret_cast<unsigned*>(smem) + ld;
+    const long long nheavy = (long long)ctl->nheavy;
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&ctl->q_num, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const long long g = heavy[h];
+        const InstDesc& I = inst[inst_of(inst, count, g)];
+        const long long i = g - I.row_off;
+        const NumParams p = inst_params(I);
+        const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+        if (I.accum == BAT_DENSE_B && I.Bd && I.C_val) {
+            bat_dense_any(p, I, i, a0, a1, true, s_rows, s_mask, err);
+            __syncthreads();
+            continue;
+        }
+        if (rg) {
+            // 32 slots of eight lanes, each a contiguous share of the row's
+            // entries on its own accumulator; the block sums the slots
+            const int S = nwarps * 4, sl = warp * 4 + (lane >> 3), gl = lane & 7;
+            const long long n = a1 - a0, q = n / S, r = n % S;
+            const long long s0 = a0 + q * sl + (sl < r ? sl : r);
+            const int len = (int)(q + (sl < r ? 1 : 0));
+            const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+            float* sacc = reinterpret_cast<float*>(smem) + (size_t)sl * ld;
+            float* sum = reinterpret_cast<float*>(smem) + (size_t)nwarps * per_warp;
+            int k0, k1;
+            float x0, x1;
+            rg_load_a(p, s0 + gl, gl < len, k0, x0);
+            rg_load_a(p, s0 + 8 + gl, 8 + gl < len, k1, x1);
+            rgp_tile<8, 2>(p, I.Bq, AddPlain{sacc}, s0, len, lmax, err, k0, x0, k1, x1);
+            __syncthreads();
+            for (int c = tid; c < I.W; c += blockDim.x) sum[c] = __uint_as_float(rgcta_sum(sacc - (size_t)sl * ld, ld, S, c));
+            if (gl == 0) sacc[I.W] = __uint_as_float(RG_EMPTY);  // the spare column (pads)
+            __syncthreads();
+            long long out = clampll(I.C_rowptr[i], 0, I.cap);
+            const long long out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
+            rgcta_emit(sum, I.W, 0, out, out_end, I.C_col, I.C_val, s_wcnt, err);
+            if (tid == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
+            continue;
+        }
+        wide_range(p, wadd, a0 + 32LL * warp, a1, 32LL * nwarps, err);
+        __syncthreads();
+        const int nw = I.W >> 5;
+        for (int c = tid; c < I.W; c += blockDim.x) {  // the warps' columns summed into warp 0's
+            float v = 0.0f;
+            bool any = false;
+            for (int w = 0; w < nwarps; ++w) {
+                float* aw = reinterpret_cast<float*>(smem) + (size_t)w * per_warp;
+                const unsigned* bw = reinterpret_cast<const unsigned*>(aw) + ld;
+                if ((bw[c >> 5] >> (c & 31)) & 1u) {
+                    v += aw[c];
+                    any = true;
+                    if (w) aw[c] = 0.0f;
+                }
+            }
+            if (any) acc0[c] = v;
+        }
+        __syncthreads();
+        for (int x = tid; x < nw; x += blockDim.x) {
+            unsigned u = 0;
+            for (int w = 0; w < nwarps; ++w) u |= reinterpret_cast<const unsigned*>(smem)[(size_t)w * per_warp + ld + x];
+            bm0[x] = u;
+        }
+        __syncthreads();
+        const long long out = clampll(I.C_rowptr[i], 0, I.cap);
+        const long long out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
+        const int tot = wide_emit(acc0, bm0, nw, out, out_end, I.C_col, I.C_val, warp, nwarps, err);
+        __syncthreads();
+        for (int x = tid; x < nwarps * nw; x += blockDim.x)
+            reinterpret_cast<unsigned*>(smem)[(size_t)(x / nw) * per_warp + ld + (x % nw)] = 0u;
+        if (tid == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+        __syncthreads();
+    }
+    // light rows, by 32-row chunks of one instance.  Plus-times with every
+    // width <= 256: four rows per warp in row groups (eight lanes, private
+    // accumulators that start RG_EMPTY, rows sorted by products); dense-B
+    // instances one row per warp in registers; otherwise one row per warp on
+    // the warp's shared accumulator.
+    const int lanes = lane & 7, slot = lane >> 3;
+    for (long long c = c0 + (long long)blockIdx.x * nwarps + warp; c < c1; c += (long long)gridDim.x * nwarps) {
+        const InstDesc& I = inst[inst_of_chunk(inst, count, c)];
+        const long long i0 = (c - I.chunk_off) * 32;
+        const NumParams p = inst_params(I);
+        const bool dense = I.accum == BAT_DENSE_B && I.Bd && I.C_val;
+        if (rg && !dense) {
+            int srt;
+            const int L = chunk_light_sorted(I, flops, i0, srt);
+            const int Wi = I.W;
+            float* myacc = wacc + (size_t)slot * (Wi + 8);
+            for (int t = 0; t < L; t += 4) {
+                const int pos = t + slot;
+                const int r = __shfl_sync(FULL, srt, pos & 31);
+                const bool active = pos < L;
+                const long long i = i0 + r;
+                long long a0 = 0, out = 0, out_end = 0;
+                int len = 0;
+                if (active) {
+                    a0 = clampll(I.A_rowptr[i], 0, I.annz);
+                    len = (int)(clampll(I.A_rowptr[i + 1], a0, I.annz) - a0);
+                    out = clampll(I.C_rowptr[i], 0, I.cap);
+                    out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
+                }
+                const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+                int k0, k1;
+                float x0, x1;
+                rg_load_a(p, a0 + lanes, lanes < len, k0, x0);
+                rg_load_a(p, a0 + 8 + lanes, 8 + lanes < len, k1, x1);
+                rgp_tile<8, 2>(p, I.Bq, AddPlain{myacc}, a0, len, lmax, err, k0, x0, k1, x1);
+                rg_emit<8>(wacc, Wi, 0, out, out_end, I.C_col, I.C_val, err);
+                // the spare column (pads) back to empty, for the next rows
+                if (lanes == 0) myacc[Wi] = __uint_as_float(RG_EMPTY);
+                if (active && lanes == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
+                __syncwarp();
+            }
+            continue;
+        }
+        const long long g = I.row_off + i0 + lane;
+        const long long f = i0 + lane < I.n ? __ldg(flops + g) : 0;
+        unsigned rows = __ballot_sync(FULL, f > 0 && f < I.heavy_min);
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const long long i = i0 + src;
+            const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+            if (dense) {
+                bat_dense_any(p, I, i, a0, a1, false, nullptr, nullptr, err);
+                continue;
+            }
+            wide_range(p, wadd, a0, a1, 32, err);
+            __syncwarp();
+            const long long out = clampll(I.C_rowptr[i], 0, I.cap);
+            const long long out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
+            const int tot = wide_emit(wacc, wbm, I.W >> 5, out, out_end, I.C_col, I.C_val, 0, 1, err);
+            if (lane == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+            __syncwarp();
+            if (lane < (I.W >> 5)) wbm[lane] = 0u;
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward: dA(i,k) = sum_j dC(i,j) B(k,j) on A's pattern, dB(k,j) += A(i,k)
+// dC(i,j) on B's pattern.  Row i's dC is scattered into a dense shared row;
+// groups of four lanes take one entry of A each (its segment of B on the
+// packed copy), reduce dA within the group and add the dB terms with float
+// atomics.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bat_zero_grads(const InstDesc* __restrict__ inst) {
+    const InstDesc& I = inst[blockIdx.y];
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    if (I.dA)
+        for (long long e = t0; e < I.annz; e += st) I.dA[e] = 0.0f;
+    if (I.dB)
+        for (long long e = t0; e < I.bnnz; e += st) I.dB[e] = 0.0f;
+}
+
+// Entries [first, e1) of A's row i, in chunks first, first + stride, ...,
+// against the dense dC row gr.
+__device__ __forceinline__ void bat_bwd_range(const InstDesc& I, const float* gr, long long first, long long e1,
+                                              long long stride, unsigned long long* err) {
+    const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
+    const int2* Q = reinterpret_cast<const int2*>(I.Bq);
+    for (long long e = first; e < e1; e += stride) {
+        const int nv = e1 - e < 32 ? (int)(e1 - e) : 32;
+        int k = -1;
+        float a = 0.0f;
+        long long s = 0;
+        unsigned q0 = 0;
+        int len = 0;
+        if (lane < nv) {
+            k = I.A_col[e + lane];
+            a = I.A_val[e + lane];
+            if ((unsigned)k < (unsigned)I.n) padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, k, s, len, q0);
+            else atomicOr(err, ERR_A_COL);
+        }
+        for (int s0 = 0; s0 < nv; s0 += 8) {
+            const int src = s0 + grp;  // < 32
+            const long long bs = shfl64(s, src);
+            const unsigned bq = __shfl_sync(FULL, q0, src);
+            const int bl = __shfl_sync(FULL, len, src);  // 0 past the chunk
+            const float ba = __shfl_sync(FULL, a, src);
+            float part = 0.0f;
+            for (int j = gl; j < bl; j += 4) {
+                const int2 v = __ldg(Q + 2 * (size_t)bq + j);
+                if ((unsigned)v.x < (unsigned)I.W) {
+                    const float t = gr[v.x];
+                    part = fmaf(t, __int_as_float(v.y), part);
+                    if (I.dB) atomicAdd(I.dB + bs + j, ba * t);
+                }
+            }
+            part += __shfl_xor_sync(FULL, part, 1);
+            part += __shfl_xor_sync(FULL, part, 2);
+            if (gl == 0 && src < nv && I.dA) I.dA[e + src] = part;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 4) k_bat_backward(const InstDesc* __restrict__ inst, int count, long long g0,
+                                                         long long g1, const long long* __restrict__ flops,
+                                                         const int* __restrict__ heavy, BatchCtl* ctl, int Wmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    for (int x = tid; x < nwarps * Wmax; x += blockDim.x) reinterpret_cast<float*>(smem)[x] = 0.0f;
+    __syncthreads();
+    unsigned long long* err = &ctl->err;
+    float* wrow = reinterpret_cast<float*>(smem) + (size_t)warp * Wmax;
+    float* trow = reinterpret_cast<float*>(smem);  // the block's row (warp 0's)
+    const long long nheavy = (long long)ctl->nheavy;
+    // dC of row i scattered into (or cleared from) a dense row
+    auto scatter = [&](const InstDesc& I, long long i, float* row, int t0, int nt, bool clear) {
+        const long long c0 = clampll(I.C_rowptr[i], 0, I.cap), c1 = clampll(I.C_rowptr[i + 1], c0, I.cap);
+        for (long long x = c0 + t0; x < c1; x += nt) {
+            const int c = I.C_col[x];
+            if ((unsigned)c < (unsigned)I.W) row[c] = clear ? 0.0f : I.dC[x];
+        }
+    };
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&ctl->q_bwd, 1ull);
+        __syncthreads();
+        const long long h = s_item;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const long long g = heavy[h];
+        const InstDesc& I = inst[inst_of(inst, count, g)];
+        const long long i = g - I.row_off;
+        if (!I.dC) continue;
+        scatter(I, i, trow, tid, blockDim.x, false);
+        __syncthreads();
+        const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+        bat_bwd_range(I, trow, a0 + 32LL * warp, a1, 32LL * nwarps, err);
+        __syncthreads();
+        scatter(I, i, trow, tid, blockDim.x, true);
+        __syncthreads();
+    }
+    const long long nchunks = (g1 - g0 + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * nwarps + warp; ch < nchunks; ch += (long long)gridDim.x * nwarps) {
+        const long long g = g0 + ch * 32 + lane;
+        int b;
+        unsigned rows = __ballot_sync(FULL, bat_light(inst, count, flops, g, g1, b));
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const InstDesc& I = inst[__shfl_sync(FULL, b, src)];
+            if (!I.dC) continue;
+            const long long i = g0 + ch * 32 + src - I.row_off;
+            scatter(I, i, wrow, lane, 32, false);
+            __syncwarp();
+            const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
+            bat_bwd_range(I, wrow, a0, a1, 32, err);
+            __syncwarp();
+            scatter(I, i, wrow, lane, 32, true);
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bounds: sum over the rows of min(d_b, flops_i); block per instance
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_batch_bounds(const InstDesc* __restrict__ inst, const long long* flops,
                                                       long long* bound) {
-    const InstDesc I = inst[blockIdx.x];
+    const InstDesc& I = inst[blockIdx.x];
     long long s = 0;
     for (long long i = threadIdx.x; i < I.n; i += blockDim.x) {
         const long long f = flops[I.row_off + i];
@@ -78,50 +693,76 @@ __global__ void __launch_bounds__(256) k_batch_bounds(const InstDesc* __restrict
     }
 }
 
-// dC of every instance into the concatenated layout (C's rows of instance b
-// start at Cp[row_off]).
-__global__ void __launch_bounds__(256) k_batch_gather_dc(const InstDesc* __restrict__ inst, const long long* Cp,
-                                                         float* dC) {
-    const InstDesc I = inst[blockIdx.y];
-    if (!I.dC) return;
-    const long long base = Cp[I.row_off], cnt = Cp[I.row_off + I.n] - base;
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = t0; e < cnt && e < I.cap; e += stride) dC[base + e] = I.dC[e];
-}
-
-// dA and dB of the concatenated product back to the instances.
-__global__ void __launch_bounds__(256) k_batch_scatter_grads(const InstDesc* __restrict__ inst, const float* dA,
-                                                             const float* dB) {
-    const InstDesc I = inst[blockIdx.y];
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    if (I.dA && dA)
-        for (long long e = t0; e < I.annz; e += stride) I.dA[e] = dA[I.annz_off + e];
-    if (I.dB && dB)
-        for (long long e = t0; e < I.bnnz; e += stride) I.dB[e] = dB[I.bnnz_off + e];
-}
-
-static unsigned grid_x(long long max_work) {
-    long long g = (max_work + 255) / 256;
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static unsigned row_grid(long long rows, int sms) {
+    long long g = (rows + 255) / 256;
     if (g < 1) g = 1;
-    if (g > 64) g = 64;
+    if (g > (long long)sms * 8) g = (long long)sms * 8;
     return (unsigned)g;
 }
 
-cudaError_t launch_batch_gather(const InstDesc* inst, int count, long long max_work, long long* Ap, int* Ai,
-                                float* Ax, long long* Bp, int* Bi, float* Bx, cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
+cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
+                               int* heavy, BatchCtl* ctl, int sms, cudaStream_t st) {
+    if (g1 <= g0) return cudaSuccess;
     count_launch();
-    k_batch_gather<<<dim3(grid_x(max_work), count), 256, 0, st>>>(inst, Ap, Ai, Ax, Bp, Bi, Bx);
+    k_bat_prepare<<<row_grid(8 * (g1 - g0), sms), 256, 0, st>>>(inst, count, g0, g1, flops, heavy, ctl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_scatter(const InstDesc* inst, int count, long long max_work, const long long* Cp,
-                                 const int* Ci, const float* Cx, unsigned long long* err, cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
+cudaError_t launch_bat_symbolic(const InstDesc* inst, int count, long long c0, long long c1, long long,
+                                const long long* flops, const int* heavy, BatchCtl* ctl, int, int sms,
+                                cudaStream_t st) {
+    if (c1 <= c0) return cudaSuccess;
+    const int grid = persistent_grid((const void*)k_bat_symbolic, 256, 0, sms);
     count_launch();
-    k_batch_scatter<<<dim3(grid_x(max_work), count), 256, 0, st>>>(inst, Cp, Ci, Cx, err);
+    k_bat_symbolic<<<grid, 256, 0, st>>>(inst, count, c0, c1, flops, heavy, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bat_scan(const InstDesc* inst, int count, BatchCtl* ctl, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    count_launch();
+    k_bat_scan<<<count, 1024, 0, st>>>(inst, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bat_numeric(const InstDesc* inst, int count, long long c0, long long c1, long long values,
+                               const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
+                               cudaStream_t st) {
+    if (c1 <= c0) return cudaSuccess;
+    if (Wmax < 32 || Wmax > 1024 || (Wmax & 31)) return cudaErrorInvalidValue;
+    const size_t smem = 4 * (8 * (size_t)bat_per_warp(Wmax, values != 0) + (values && Wmax <= 256 ? Wmax : 0));
+    cudaError_t e;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute((const void*)k_bat_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid((const void*)k_bat_numeric, 256, smem, sms);
+    count_launch();
+    k_bat_numeric<<<grid, 256, smem, st>>>(inst, count, c0, c1, flops, heavy, ctl, Wmax, values != 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bat_backward(const InstDesc* inst, int count, long long g0, long long g1, long long max_work,
+                                const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
+                                cudaStream_t st) {
+    if (g1 <= g0 || count < 1) return cudaSuccess;
+    if (Wmax < 32 || Wmax > 1024 || (Wmax & 31)) return cudaErrorInvalidValue;
+    long long gx = (max_work + 255) / 256;
+    if (gx < 1) gx = 1;
+    if (gx > 64) gx = 64;
+    count_launch();
+    k_bat_zero_grads<<<dim3((unsigned)gx, count), 256, 0, st>>>(inst);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    const size_t smem = 8 * 4 * (size_t)Wmax;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute((const void*)k_bat_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int grid = persistent_grid((const void*)k_bat_backward, 256, smem, sms);
+    count_launch();
+    k_bat_backward<<<grid, 256, smem, st>>>(inst, count, g0, g1, flops, heavy, ctl, Wmax);
     return cudaGetLastError();
 }
 
@@ -130,22 +771,6 @@ cudaError_t launch_batch_bounds(const InstDesc* inst, int count, const long long
     if (count == 0) return cudaSuccess;
     count_launch();
     k_batch_bounds<<<count, 256, 0, st>>>(inst, flops, bound);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_gather_dc(const InstDesc* inst, int count, long long max_work, const long long* Cp,
-                                   float* dC, cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
-    count_launch();
-    k_batch_gather_dc<<<dim3(grid_x(max_work), count), 256, 0, st>>>(inst, Cp, dC);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_scatter_grads(const InstDesc* inst, int count, long long max_work, const float* dA,
-                                       const float* dB, cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
-    count_launch();
-    k_batch_scatter_grads<<<dim3(grid_x(max_work), count), 256, 0, st>>>(inst, dA, dB);
     return cudaGetLastError();
 }
 

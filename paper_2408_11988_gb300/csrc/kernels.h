@@ -156,10 +156,16 @@ cudaError_t launch_msbfs_init_parents(long long n, int d, const int* src, int* p
 cudaError_t launch_msbfs_emit(long long n, int d, const unsigned* newbits, const long long* rp,
                               int* col, long long cap, WsHeader* hdr, cudaStream_t st);
 
-// One instance of a batched product (device-side descriptor).
+// One instance of a batched product (device-side descriptor), with its own
+// tuning: accumulator width W (d padded to 32, at most 1024), accumulator
+// kind (BAT_SPARSE: shared accumulator with occupancy bits; BAT_DENSE_B:
+// the dense-B form, d <= 256) and heavy-row threshold; Bq, Bd and Bbits
+// point into the workspace (its packed and dense copies of B).
+constexpr int BAT_SPARSE = 0;
+constexpr int BAT_DENSE_B = 1;
 struct InstDesc {
     long long n, d, annz, bnnz, cap;
-    long long row_off, annz_off, bnnz_off;
+    long long row_off;  // first row of this instance in the batch's numbering
     const long long* A_rowptr;
     const int* A_col;
     const float* A_val;
@@ -172,17 +178,34 @@ struct InstDesc {
     const float* dC;
     float* dA;
     float* dB;
+    long long heavy_min;
+    long long chunk_off;  // first 32-row chunk of this instance in the batch's chunk numbering
+    int W, accum, Wd, pad;
+    int4* Bq;
+    float* Bd;
+    unsigned* Bbits;
 };
-cudaError_t launch_batch_gather(const InstDesc* inst, int count, long long max_work, long long* Ap, int* Ai,
-                                float* Ax, long long* Bp, int* Bi, float* Bx, cudaStream_t st);
-cudaError_t launch_batch_scatter(const InstDesc* inst, int count, long long max_work, const long long* Cp,
-                                 const int* Ci, const float* Cx, unsigned long long* err, cudaStream_t st);
+// Counters and error bits of a batched call (in the workspace).
+struct BatchCtl {
+    unsigned long long nheavy, q_sym, q_num, q_bwd, err;
+};
+// Rows [g0, g1) of the batch's numbering over the instances inst[0..count).
+cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
+                               int* heavy, BatchCtl* ctl, int sms, cudaStream_t st);
+// symbolic / numeric: 32-row chunks [c0, c1) of the batch's chunk numbering
+// (every chunk lies in one instance); `values` = plus-times
+cudaError_t launch_bat_symbolic(const InstDesc* inst, int count, long long c0, long long c1, long long unused,
+                                const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
+                                cudaStream_t st);
+cudaError_t launch_bat_scan(const InstDesc* inst, int count, BatchCtl* ctl, cudaStream_t st);
+cudaError_t launch_bat_numeric(const InstDesc* inst, int count, long long c0, long long c1, long long values,
+                               const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
+                               cudaStream_t st);
+cudaError_t launch_bat_backward(const InstDesc* inst, int count, long long g0, long long g1, long long max_work,
+                                const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
+                                cudaStream_t st);
 cudaError_t launch_batch_bounds(const InstDesc* inst, int count, const long long* flops, long long* bound,
                                 cudaStream_t st);
-cudaError_t launch_batch_gather_dc(const InstDesc* inst, int count, long long max_work, const long long* Cp,
-                                   float* dC, cudaStream_t st);
-cudaError_t launch_batch_scatter_grads(const InstDesc* inst, int count, long long max_work, const float* dA,
-                                       const float* dB, cudaStream_t st);
 
 // Sparse Force2Vec step (force2vec.cu): W's pattern (count + scan, fill),
 // the Z layout check, the weights on W's pattern, and update + top-k +

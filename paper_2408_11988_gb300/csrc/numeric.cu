@@ -15,6 +15,8 @@
 #include "kernels.h"
 #include "numeric.cuh"
 #include "staged.cuh"
+#include "wide.cuh"
+#include "rowgroup.cuh"
 
 namespace ts {
 
@@ -292,16 +294,6 @@ struct NumRowBody {
 // are read out together: lane l of a slot takes four columns of every
 // 4*RG-column block, so all 32 lanes work in every read-out step.
 // ---------------------------------------------------------------------------
-constexpr unsigned RG_EMPTY = 0xFFBADBADu;  // exponent all ones, quiet bit clear
-static_assert((RG_EMPTY & 0x7F800000u) == 0x7F800000u && (RG_EMPTY & 0x00400000u) == 0 && (RG_EMPTY & 0x003FFFFFu),
-              "RG_EMPTY must be a signalling NaN");
-
-// acc[lc] += v, lc already checked against [0, W) and d.
-__device__ __forceinline__ void rg_add(float* acc, int lc, float v) {
-    const float old = acc[lc];
-    acc[lc] = __float_as_uint(old) == RG_EMPTY ? v : old + v;
-}
-
 // A segment of B as a slot walks it: its first position rounded down to a
 // multiple of E (qbase), the positions to skip before the segment (lead),
 // the positions covered from qbase (span) and A's value a.  E consecutive
@@ -362,58 +354,6 @@ __device__ __forceinline__ void rg_segment(const int4* __restrict__ P4, float* a
         int4 w0 = make_int4(0, 0, 0, 0), w1 = make_int4(0, 0, 0, 0);
         rg_fetch<E>(P4, sg, q, w0, w1);
         rg_apply<E>(acc, sg, q, w0, w1, Wd, W, c0, bad);
-    }
-}
-
-// Read-out of tile c0 of every slot (all lanes converged): the warp reads
-// the slots out one after another, lane l taking column l of every 32-column
-// stripe, so that each store instruction writes consecutive positions of one
-// row of C (whole sectors) and a stripe's offsets come from one ballot.  A
-// slot's output offsets are 32-bit (a row holds at most d entries); a row
-// that would pass its end in C stores nothing more and is reported by the
-// caller (out != out_end).
-template <int RG>
-__device__ __forceinline__ void rg_emit(float* racc, int W, int c0, long long& out, long long out_end, int* Ci,
-                                        float* Cx, unsigned long long*) {
-    constexpr int R = 32 / RG;
-    const int lane = lane_id(), g = lane / RG;
-    const unsigned lt = lanemask_lt();
-#pragma unroll 1
-    for (int h = 0; h < R; ++h) {
-        const long long o0 = shfl64(out, h * RG), e0 = shfl64(out_end, h * RG);
-        const long long r = e0 - o0;
-        const int room = r < 0x7FFFFFFFLL ? (int)r : 0x7FFFFFFF;
-        int* ci = Ci + o0;
-        float* cx = Cx + o0;
-        float* acc = racc + h * (W + 8);
-        int o = 0;
-#pragma unroll 4
-        for (int base = 0; base < W; base += 32) {
-            const int c = base + lane;
-            const unsigned x = __float_as_uint(acc[c]);
-            const bool take = x != RG_EMPTY;
-            const unsigned bal = __ballot_sync(FULL, take);
-            if (take) {
-                const int pos = o + __popc(bal & lt);
-                if (pos < room) {
-                    ci[pos] = c0 + c;
-                    cx[pos] = __uint_as_float(x);
-                }
-                acc[c] = __uint_as_float(RG_EMPTY);
-            }
-            o += __popc(bal);
-        }
-        if (g == h) out += o;
-    }
-}
-
-// Column index and value of entry ei of A (k = -1 past the row's end).
-__device__ __forceinline__ void rg_load_a(const NumParams& p, long long ei, bool ok, int& k, float& a) {
-    k = -1;
-    a = 0.0f;
-    if (ok) {
-        k = __ldg(p.Ai + ei);
-        a = __ldg(p.Ax + ei);
     }
 }
 
@@ -480,148 +420,6 @@ __device__ __forceinline__ void rg_tile(const NumParams& p, const Seg& seg, cons
         }
         s = ns;
         L = nL;
-        x0 = x1;
-        k1 = k2;
-        x1 = x2;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Row-aligned packed copy of B (one column tile, T = 1).  Row k's entries
-// start at entry S(k) = E * ceil((Bp[k] + (E-1) k) / E) of the copy, so every
-// row begins a group of E entries (one or two 16-byte loads) and
-// S(k) + len_k <= S(k+1) holds without a scan over the row lengths.  The
-// last group of a row is completed with pad entries (column -1, value 0),
-// and a column outside [0, d) (an input error, reported once by the packing
-// kernel) is stored as -1 too.  A slot maps a column c to accumulator index
-// min((unsigned)c, W): pads and bad columns land in the spare column W,
-// which is never read out, so the gather needs no per-entry segment or
-// range test.  Groups are numbered with 32 bits (the host checks the copy's
-// size).
-// ---------------------------------------------------------------------------
-// Row k of B as the copy holds it: its first entry s and length len in B
-// (clamped like SegWhole) and its first group g0 in the copy.
-template <int E>
-__device__ __forceinline__ void padded_row(const long long* __restrict__ Bp, long long nnzB, int d, int k,
-                                           long long& s, int& len, unsigned& g0) {
-    s = clampll(__ldg(Bp + k), 0, nnzB);
-    const long long e = clampll(__ldg(Bp + k + 1), s, nnzB);
-    len = (int)(e - s < d ? e - s : d);
-    g0 = (unsigned)((s + (long long)(E - 1) * k + (E - 1)) / E);
-}
-
-template <int E>
-__device__ __forceinline__ void padded_seg(const long long* __restrict__ Bp, long long nnzB, int d, int k,
-                                           unsigned& g0, int& ng) {
-    long long s;
-    int len;
-    padded_row<E>(Bp, nnzB, d, k, s, len, g0);
-    ng = (len + E - 1) / E;
-}
-
-// Segment (first group, groups) of B's row k for entry k of A (empty when
-// !ok; a bad k is an input error).
-template <int E>
-__device__ __forceinline__ void rgp_seg(const NumParams& p, int k, bool ok, unsigned& g0, int& ng,
-                                        unsigned long long* err) {
-    g0 = 0;
-    ng = 0;
-    if (!ok) return;
-    if ((unsigned)k < (unsigned)p.nB) padded_seg<E>(p.Bp, p.nnzB, p.d, k, g0, ng);
-    else atomicOr(err, ERR_A_COL);
-}
-
-// Group g of the copy (E = 2: one 16-byte load; E = 4: two).
-template <int E>
-__device__ __forceinline__ void rgp_load(const int4* __restrict__ Q, unsigned g, int4& v0, int4& v1) {
-    v0 = __ldg(Q + (size_t)g * (E / 2));
-    if constexpr (E == 4) v1 = __ldg(Q + (size_t)g * 2 + 1);
-}
-
-// How a slot adds a product into its accumulator.  AddPlain: the slot's own
-// accumulator (row groups): a column outside [0, W) (a pad) goes to the
-// spare column W.  AddShared: one accumulator shared by several slots (see
-// the wide kernel below): pads are skipped, the value is added with a
-// shared-memory float reduction and the column's occupancy bit is set.
-struct AddPlain {
-    float* acc;
-    __device__ __forceinline__ void operator()(int c, unsigned W, float v) const {
-        rg_add(acc, (unsigned)c < W ? c : (int)W, v);
-    }
-};
-
-struct AddShared {
-    float* acc;
-    unsigned* bm;
-    __device__ __forceinline__ void operator()(int c, unsigned W, float v) const {
-        if ((unsigned)c < W) {
-            atomicAdd(acc + c, v);
-            atomicOr(bm + (c >> 5), 1u << (c & 31));
-        }
-    }
-};
-
-template <int E, class Add>
-__device__ __forceinline__ void rgp_apply(const Add& add, const int4& v0, const int4& v1, float a, unsigned W) {
-    const int cs[4] = {v0.x, v0.z, v1.x, v1.z};
-    const int bs[4] = {v0.y, v0.w, v1.y, v1.w};
-#pragma unroll
-    for (int u = 0; u < E; ++u) add(cs[u], W, a * __int_as_float(bs[u]));
-}
-
-// rg_tile on the row-aligned copy: chunks of RG entries of every slot's row,
-// software-pipelined the same way (the next segment's description and first
-// group load while the current segment is accumulated).  The caller has
-// loaded the first two chunks of A (k0/x0: entry a0 + gl, k1/x1: entry
-// a0 + RG + gl, as rg_load_a gives them).
-template <int RG, int E, class Add>
-__device__ __forceinline__ void rgp_tile(const NumParams& p, const int4* __restrict__ Q, const Add& acc, long long a0,
-                                         int len, int lmax, unsigned long long* err, int k0, float x0, int k1,
-                                         float x1) {
-    const int lane = lane_id(), gl = lane % RG, src0 = (lane / RG) * RG;
-    const unsigned W = (unsigned)p.W;
-    unsigned g0;
-    int n0;
-    rgp_seg<E>(p, k0, gl < len, g0, n0, err);
-    unsigned ng = __shfl_sync(FULL, g0, src0);
-    int nn = __shfl_sync(FULL, n0, src0);
-    float na = __shfl_sync(FULL, x0, src0);
-    int4 v0 = make_int4(0, 0, 0, 0), v1 = make_int4(0, 0, 0, 0);
-    if (gl < nn) rgp_load<E>(Q, ng + gl, v0, v1);
-    for (int e = 0; e < lmax; e += RG) {
-        int k2;
-        float x2;
-        unsigned g1;
-        int n1;
-        rg_load_a(p, a0 + e + 2 * RG + gl, e + 2 * RG + gl < len, k2, x2);
-        rgp_seg<E>(p, k1, e + RG + gl < len, g1, n1, err);
-        if (n1 > 0) prefetch_l2(Q + (size_t)g1 * (E / 2));  // the next chunk's rows of B into L2
-        const int nu = lmax - e < RG ? lmax - e : RG;
-        for (int u = 0; u < nu; ++u) {
-            const unsigned cg = ng;
-            const int cn = nn;
-            const float ca = na;
-            const int4 c0v = v0, c1v = v1;
-            // describe and start loading the segment after this one (the
-            // first of the next chunk after the last of this one)
-            const bool more = u + 1 < nu;
-            const int su = more ? src0 + u + 1 : src0;
-            ng = __shfl_sync(FULL, more ? g0 : g1, su);
-            nn = __shfl_sync(FULL, more ? n0 : n1, su);
-            na = __shfl_sync(FULL, more ? x0 : x1, su);
-            if (gl < nn) rgp_load<E>(Q, ng + gl, v0, v1);
-            if (gl < cn) {
-                rgp_apply<E>(acc, c0v, c1v, ca, W);
-                for (int q = gl + RG; q < cn; q += RG) {
-                    int4 w0, w1;
-                    rgp_load<E>(Q, cg + q, w0, w1);
-                    rgp_apply<E>(acc, w0, w1, ca, W);
-                }
-            }
-            __syncwarp();
-        }
-        g0 = g1;
-        n0 = n1;
         x0 = x1;
         k1 = k2;
         x1 = x2;
@@ -804,59 +602,6 @@ __device__ __forceinline__ void rgcta_tile(const NumParams& p, const int4* P4, f
     else rg_tile<RG>(p, SegTile{p.tp, p.T + 1, t, p.W}, P4, acc, a0, len, lmax, c0, Wd, err, bad);
 }
 
-// Column c of the S slots summed (RG_EMPTY if no slot reached it); every
-// slot's column is reset.  Called by one thread per column after a barrier.
-__device__ __forceinline__ unsigned rgcta_sum(float* racc, int ld, int S, int c) {
-    unsigned x = RG_EMPTY;
-#pragma unroll 8
-    for (int k = 0; k < S; ++k) {
-        float* a = racc + (size_t)k * ld + c;
-        const unsigned y = __float_as_uint(*a);
-        if (y != RG_EMPTY) {
-            x = x == RG_EMPTY ? y : __float_as_uint(__uint_as_float(x) + __uint_as_float(y));
-            *a = __uint_as_float(RG_EMPTY);
-        }
-    }
-    return x;
-}
-
-// Block-wide read-out of a heavy row's tile from the summed columns held in
-// sum[0..W) (reset to RG_EMPTY); wcnt has W/32 + 1 entries.
-__device__ __forceinline__ void rgcta_emit(float* sum, int W, int c0, long long& out, long long out_end, int* Ci,
-                                           float* Cx, int* wcnt, unsigned long long* err) {
-    const int nw = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
-    const int words = W >> 5;
-    const unsigned lt = lanemask_lt();
-    for (int w = warp; w < words; w += nw) {
-        const unsigned bal = __ballot_sync(FULL, __float_as_uint(sum[w * 32 + lane]) != RG_EMPTY);
-        if (lane == 0) wcnt[w] = __popc(bal);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int tot = warp_excl_scan_smem(wcnt, words);
-        if (lane == 0) wcnt[words] = tot;
-    }
-    __syncthreads();
-    for (int w = warp; w < words; w += nw) {
-        const int c = w * 32 + lane;
-        const unsigned x = __float_as_uint(sum[c]);
-        const bool f = x != RG_EMPTY;
-        const unsigned bal = __ballot_sync(FULL, f);
-        if (f) {
-            const long long pos = out + wcnt[w] + __popc(bal & lt);
-            if (pos < out_end) {
-                Ci[pos] = c0 + c;
-                Cx[pos] = __uint_as_float(x);
-            } else {
-                atomicOr(err, ERR_C_ROW);
-            }
-            sum[c] = __uint_as_float(RG_EMPTY);
-        }
-    }
-    out += wcnt[words];
-    __syncthreads();
-}
-
 // Split parts, then heavy rows, in row groups (plus-times, padded packed B).
 // Shared memory: S accumulators of W + 8 floats (the slots), then W floats
 // for the summed tile.  Launched ahead of k_numeric_light, which takes the
@@ -927,177 +672,6 @@ __global__ void __launch_bounds__(256, 5) k_numeric_rgcta(NumParams p) {
         if (out != out_end && tid == 0) atomicOr(err, ERR_C_ROW);
     }
     if (bad) atomicOr(err, ERR_B_COL);
-}
-
-// ---------------------------------------------------------------------------
-// Wide rows (plus-times, one column tile of 256 < W <= 1024 columns: for
-// d = 1024 the four 256-column tiles of B side by side, so that A is walked
-// once instead of once per tile).  Private accumulators of W floats per row
-// group would leave too few rows in flight per SM, and reading a W-wide
-// accumulator out costs W/32 steps per row although a row of C holds only
-// a few dozen of its W columns.  Here a team -- one warp for a light row,
-// the whole block for a heavy row or a part of a split row -- owns ONE
-// accumulator of W floats and a bitmap of W/32 occupancy words.  The team's
-// slots of 8 lanes take contiguous shares of the item's entries of A and
-// walk their segments of B on the row-aligned copy as the row-group kernels
-// do (pairs of entries per lane, next segment in flight), but all add into
-// the shared accumulator: a shared-memory float reduction for the value and
-// an OR of the column's bit.  The read-out visits the occupied columns only:
-// output positions are dealt to the lanes 32 at a time, so every store
-// writes 32 consecutive entries of C, and lane l finds the column of rank j
-// by a search over the words' running counts and a select inside the word.
-// ---------------------------------------------------------------------------
-
-// Position of the k-th (0-based) set bit of x (k < popc(x)): binary search
-// over halves, quarters, ... of the word by population counts.
-__device__ __forceinline__ int select_bit(unsigned x, int k) {
-    int pos = 0;
-    int c = __popc(x & 0xFFFFu);
-    if (k >= c) { k -= c; x >>= 16; pos += 16; }
-    c = __popc(x & 0xFFu);
-    if (k >= c) { k -= c; x >>= 8; pos += 8; }
-    c = __popc(x & 0xFu);
-    if (k >= c) { k -= c; x >>= 4; pos += 4; }
-    c = __popc(x & 0x3u);
-    if (k >= c) { k -= c; x >>= 2; pos += 2; }
-    if (k >= (int)(x & 1u)) pos += 1;
-    return pos;
-}
-
-// Read-out of a shared accumulator acc[0..32*nw) with bitmap bm[0..nw)
-// (nw <= 32) into C[out, out_end): positions 32*r + lane for rounds
-// r = r0, r0 + rstep, ... (a block team splits the rounds over its warps);
-// every emitted column of acc is reset to 0.  Returns the row's count.
-// Called with all 32 lanes converged; the caller clears the bitmap after
-// every warp of the team has passed.
-__device__ __forceinline__ int wide_emit(float* acc, const unsigned* bm, int nw, long long out, long long out_end,
-                                         int* Ci, float* Cx, int r0, int rstep, unsigned long long* err) {
-    const int lane = lane_id();
-    const unsigned word = lane < nw ? bm[lane] : 0u;
-    const int cnt = __popc(word);
-    const int incl = warp_incl_scan(cnt);
-    const int total = __shfl_sync(FULL, incl, 31);
-    const long long r = out_end - out;
-    const int room = r < (long long)total ? (int)r : total;
-    bool over = false;
-    for (int base = 32 * r0; base < total; base += 32 * rstep) {
-        const int j = base + lane;
-        // word of rank j: the number of words whose running count is <= j
-        int w = 0;
-#pragma unroll
-        for (int st = 16; st >= 1; st >>= 1)
-            if (__shfl_sync(FULL, incl, w + st - 1) <= j) w += st;
-        const unsigned x = __shfl_sync(FULL, word, w);
-        const int before = __shfl_sync(FULL, incl - cnt, w);
-        if (j < total) {
-            const int c = 32 * w + select_bit(x, j - before);
-            const float v = acc[c];
-            acc[c] = 0.0f;
-            if (j < room) {
-                Ci[out + j] = c;
-                Cx[out + j] = v;
-            } else {
-                over = true;
-            }
-        }
-    }
-    if (over) atomicOr(err, ERR_C_ROW);
-    return total;
-}
-
-// Segments of one chunk of up to 32 entries of A (lane l: entry l, its
-// segment of B in the row-aligned copy as first pair g0 and pairs np, and
-// A's value a; np = 0 past the chunk) added into the shared accumulator.
-// Groups of four lanes take one segment each, lane gl its pairs gl, gl + 4,
-// ...; two steps of eight segments are in flight at once (up to four
-// 16-byte loads per lane before any is used).
-__device__ __forceinline__ void wide_chunk_walk(const int4* __restrict__ Q, const AddShared& add, unsigned W,
-                                                unsigned g0, int np, float a, int nvalid) {
-    const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
-    for (int s0 = 0; s0 < nvalid; s0 += 16) {
-        const int ea = s0 + grp, eb = s0 + 8 + grp;
-        const unsigned ga = __shfl_sync(FULL, g0, ea & 31), gb = __shfl_sync(FULL, g0, eb & 31);
-        int na = __shfl_sync(FULL, np, ea & 31), nb = __shfl_sync(FULL, np, eb & 31);
-        const float xa = __shfl_sync(FULL, a, ea & 31), xb = __shfl_sync(FULL, a, eb & 31);
-        if (ea >= nvalid) na = 0;
-        if (eb >= nvalid) nb = 0;
-        int4 u0 = make_int4(-1, 0, -1, 0), u1 = u0, v0 = u0, v1 = u0;
-        if (gl < na) u0 = __ldg(Q + ga + gl);
-        if (gl < nb) v0 = __ldg(Q + gb + gl);
-        if (gl + 4 < na) u1 = __ldg(Q + ga + gl + 4);
-        if (gl + 4 < nb) v1 = __ldg(Q + gb + gl + 4);
-        add(u0.x, W, xa * __int_as_float(u0.y));
-        add(u0.z, W, xa * __int_as_float(u0.w));
-        add(v0.x, W, xb * __int_as_float(v0.y));
-        add(v0.z, W, xb * __int_as_float(v0.w));
-        add(u1.x, W, xa * __int_as_float(u1.y));
-        add(u1.z, W, xa * __int_as_float(u1.w));
-        add(v1.x, W, xb * __int_as_float(v1.y));
-        add(v1.z, W, xb * __int_as_float(v1.w));
-        // rows of B longer than 16 entries
-        for (int q = gl + 8; q < na; q += 4) {
-            const int4 w = __ldg(Q + ga + q);
-            add(w.x, W, xa * __int_as_float(w.y));
-            add(w.z, W, xa * __int_as_float(w.w));
-        }
-        for (int q = gl + 8; q < nb; q += 4) {
-            const int4 w = __ldg(Q + gb + q);
-            add(w.x, W, xb * __int_as_float(w.y));
-            add(w.z, W, xb * __int_as_float(w.w));
-        }
-    }
-}
-
-// Entry e of A for this lane (ok: inside the chunk): its column k (-1 if
-// none) and value a.
-__device__ __forceinline__ void wide_load_a(const NumParams& p, long long e, bool ok, int& k, float& a) {
-    k = -1;
-    a = 0.0f;
-    if (ok) {
-        k = __ldg(p.Ai + e);
-        a = __ldg(p.Ax + e);
-    }
-}
-
-// Segment (first pair, pairs) of B's row k in the row-aligned copy (none
-// for k = -1; a column of A outside [0, n) is an input error).
-__device__ __forceinline__ void wide_seg(const NumParams& p, int k, unsigned& g0, int& np, unsigned long long* err) {
-    g0 = 0;
-    np = 0;
-    if (k < 0) return;
-    if (k < p.nB) padded_seg<2>(p.Bp, p.nnzB, p.d, k, g0, np);
-    else atomicOr(err, ERR_A_COL);
-}
-
-// Chunks first, first + stride, ... (< e1) of 32 entries of A walked by
-// one warp into the shared accumulator, in three stages: while chunk c is
-// walked, the row pointers of B for chunk c + 1 and the entries of A of
-// chunk c + 2 are in flight.
-__device__ __forceinline__ void wide_range(const NumParams& p, const AddShared& add, long long first, long long e1,
-                                           long long stride, unsigned long long* err) {
-    const int lane = lane_id();
-    const unsigned W = (unsigned)p.W;
-    int k;
-    float a;
-    wide_load_a(p, first + lane, first + lane < e1, k, a);
-    unsigned g0;
-    int np;
-    wide_seg(p, k, g0, np, err);
-    float ca = a;
-    wide_load_a(p, first + stride + lane, first + stride + lane < e1, k, a);
-    for (long long e = first; e < e1; e += stride) {
-        const int nv = e1 - e < 32 ? (int)(e1 - e) : 32;
-        unsigned g1;
-        int np1;
-        wide_seg(p, k, g1, np1, err);  // chunk c + 1
-        const float ca1 = a;
-        const long long e2 = e + 2 * stride;
-        wide_load_a(p, e2 + lane, e2 + lane < e1, k, a);  // chunk c + 2
-        wide_chunk_walk(p.Bq, add, W, g0, np, ca, nv);
-        g0 = g1;
-        np = np1;
-        ca = ca1;
-    }
 }
 
 // A light row as the pipeline holds it: its row id (-1: none), first entry

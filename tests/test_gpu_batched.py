@@ -114,3 +114,48 @@ def test_batched_full_size_sampled():
         it = torch.as_tensor(idx, device="cuda")
         np.testing.assert_array_equal(C.col[it].cpu().numpy(), Si)
         assert_values_close(C.val[it].cpu().numpy(), Sx, Sb)
+
+
+def _mixed_instances(seed=5):
+    # uneven instances, two of them with dense B (the dense-B form applies)
+    out = _instances(seed=seed, count=6)
+    A, B = synth.rmat_embedding(scale=10, edge_factor=12, d=128, density=0.7, seed=seed * 10 + 1,
+                                b_values="uniform")
+    out.append((A, B))
+    A, B = synth.rmat_embedding(scale=9, edge_factor=20, d=256, density=0.6, seed=seed * 10 + 2,
+                                b_values="uniform")
+    out.append((A, B))
+    return out
+
+
+@pytest.mark.parametrize("tuning", [None, {"accum": 4}, {"accum": 1, "cta_min_flops": 32}])
+def test_batched_per_instance_tuning_and_autotune(tuning):
+    inst = _mixed_instances()
+    As = [DeviceCSR.from_host(A) for A, _ in inst]
+    Bs = [DeviceCSR.from_host(B) for _, B in inst]
+    bp = BatchedProduct(As, Bs, tuning=tuning)
+    summary = bp.tuning_summary()
+    assert len(summary["per_instance"]) == len(inst)
+    if tuning is None:   # the two dense instances take the dense-B form by default
+        assert [x["accum"] for x in summary["per_instance"]][-2:] == ["dense_b", "dense_b"]
+    Cs = bp.forward()
+    bp.check()
+    for (A, B), C in zip(inst, Cs):
+        _check(C, A, B)
+    bp.autotune(reps=1)
+    after = bp.tuning_summary()["per_instance"]
+    assert all(x["heavy_min_flops"] in (1024, 4096, 16384, 1 << 50) for x in after)
+    Cs = bp.forward()
+    bp.check()
+    for (A, B), C in zip(inst, Cs):
+        _check(C, A, B)
+    dCs = [torch.as_tensor(synth.grad_output(int(C.rowptr[-1].item()), 30 + i), device="cuda")
+           for i, C in enumerate(Cs)]
+    bp.bind_grads(dCs)
+    dAs, dBs = bp.backward()
+    bp.check()
+    for i, ((A, B), C) in enumerate(zip(inst, Cs)):
+        Cp, Ci = _check(C, A, B)
+        rA, bA, rB, bB = oracle.backward(A, B, Cp, Ci, dCs[i].double().cpu().numpy())
+        assert np.all(np.abs(dAs[i][:A.nnz].cpu().numpy() - rA) <= REL * bA)
+        assert np.all(np.abs(dBs[i][:B.nnz].cpu().numpy() - rB) <= REL * bB)
