@@ -175,3 +175,37 @@ def test_backward_split_rows():
         rA, bA, rB, bB = oracle.backward(A, B, rp, ci, dC.astype(np.float64))
         assert np.all(np.abs(dA - rA) <= REL * bA)
         assert np.all(np.abs(dB - rB) <= REL * bB)
+
+
+@pytest.mark.parametrize("d", [1024, 700, 288])
+@pytest.mark.parametrize("tuning", [None, {"cta_min_flops": 1 << 20}, {"cta_min_flops": 64, "warps_per_cta": 4},
+                                    {"bwd_group": 16}, {"row_lanes": 32}])
+def test_backward_wide_rows(d, tuning):
+    # products of one column tile of 256 < W <= 1024 (the wide numeric
+    # kernel's range), their backward under several tunings
+    A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=d, density=0.01, seed=57 + d % 5, b_values="uniform")
+    rp, col, dC, dA, dB = _run(A, B, tuning)
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
+    assert np.all(np.abs(dA - rA) <= REL * bA)
+    assert np.all(np.abs(dB - rB) <= REL * bB)
+
+
+def test_backward_wide_rows_long_b_rows_and_hub():
+    # rows of B of about 30 entries and a hub row of A split into parts
+    rng = np.random.default_rng(58)
+    n, d = 3000, 512
+    A = synth.er(n, 6, 59)
+    A.val = synth.uniform(A.nnz, 60)
+    hub = np.sort(rng.choice(n, 2500, replace=False)).astype(np.int32)
+    rows = [A.col[A.rowptr[i]:A.rowptr[i + 1]] if i != 5 else hub for i in range(n)]
+    vals = [A.val[A.rowptr[i]:A.rowptr[i + 1]] if i != 5 else rng.random(hub.size, dtype=np.float32) for i in range(n)]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    from synth import CSR
+    A2 = CSR(n, n, rp, np.concatenate(rows), np.concatenate(vals))
+    B = synth.tall_skinny(n, d, 0.06, 61)
+    B.val = synth.normal(B.nnz, 62)
+    rp, col, dC, dA, dB = _run(A2, B)
+    rA, bA, rB, bB = oracle.backward(A2, B, rp, col, dC.astype(np.float64))
+    assert np.all(np.abs(dA - rA) <= REL * bA)
+    assert np.all(np.abs(dB - rB) <= REL * bB)
