@@ -132,6 +132,16 @@ typedef struct ts_csr_desc {
  *                 tile of at most 256 columns, else 32.  Any value but 32
  *                 also runs the symbolic pass's light rows in row groups of
  *                 four lanes (d <= 512, B.col 16-byte aligned).
+ *  dB_mode        how the backward forms dB (dA is the same either way):
+ *                 1 = option S, the dB terms of every product scattered
+ *                 with float atomics in the forward's row order (fast; the
+ *                 order of the additions, and so the last bits of dB, may
+ *                 differ from run to run); 2 = option T, deterministic: the
+ *                 transpose of A's pattern (a stable radix sort of A's
+ *                 column indices in the workspace), then each row k of dB
+ *                 summed over column k of A in ascending row order, dC(i, j)
+ *                 found by binary search in the sorted row i of C; no
+ *                 atomics, dB identical bit for bit on every run.  Default 1.
  *  stage          1 = gather B's entries into shared memory with asynchronous
  *                 copies, a window of 256 products per warp in flight (implies
  *                 pack_b = 1 for plus-times); 2 = load them into registers.
@@ -148,6 +158,7 @@ typedef struct ts_tuning {
     int32_t sym_group;
     int32_t bwd_group;
     int32_t row_lanes;
+    int32_t dB_mode;
 } ts_tuning;
 
 typedef struct ts_plan ts_plan;

@@ -42,7 +42,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("accum", c_int32), ("col_tile", c_int32), ("cta_min_flops", c_int64),
                 ("warps_per_cta", c_int32), ("hash_slots", c_int32), ("group", c_int32),
                 ("pack_b", c_int32), ("stage", c_int32), ("sym_group", c_int32), ("bwd_group", c_int32),
-                ("row_lanes", c_int32)]
+                ("row_lanes", c_int32), ("dB_mode", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

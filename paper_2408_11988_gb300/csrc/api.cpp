@@ -201,6 +201,8 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
     // row groups of 8 lanes (pairs) where four rows' accumulators fit well
     // (one tile, W <= 256); one warp per light row otherwise
     t.row_lanes = force.row_lanes ? force.row_lanes : 0;
+    t.dB_mode = force.dB_mode ? force.dB_mode : 1;
+    if (t.dB_mode != 1 && t.dB_mode != 2) return fail(TS_ERR_INVALID_ARG, "tuning: dB_mode must be 1 or 2");
     if (t.stage != 1 && t.stage != 2) return fail(TS_ERR_INVALID_ARG, "tuning: stage must be 1 or 2");
     if (t.stage == 1) t.pack_b = 1;
     if (!valid_group(t.group) || !valid_group(t.sym_group) || !valid_group(t.bwd_group))
@@ -242,7 +244,7 @@ static ts_status resolve_tuning(long long d, const ts_tuning& force, ts_tuning& 
 
 struct Layout {
     size_t hdr = 0, flops = 0, perm = 0, partial = 0, items = 0, blen = 0, tp = 0, bpk = 0, bq = 0, denseb = 0,
-           total = 0;
+           bt = 0, total = 0;
     size_t split_rows = 0, split_done = 0, split_items = 0, stg_bits = 0, stg_vals = 0, stg_flags = 0;
     int dw = 0, dpad = 0;
     int W = 0, T = 1;
@@ -293,6 +295,9 @@ static Layout plan_layout(long long n, long long d, const ts_tuning& t, long lon
     if ((t.pack_b == 1 && L.T == 1 && t.row_lanes != 32) || cover_autotune) L.bq = take(padded_b_bytes(n, nnzB, d, 4));
     // dense copy of B and its pattern bitmap (dense-B form only)
     if (t.accum == TS_ACC_DENSE_B) L.denseb = take(dense_b_bytes(n, d));
+    // the deterministic dB's transpose, chunk offsets and partial sums
+    // (covered for the autotuner too, which may try it)
+    if (t.dB_mode == 2 || cover_autotune) L.bt = take(backward_t_bytes(n, nnzA, nnzB, d));
     L.total = off;
     return L;
 }
@@ -599,9 +604,15 @@ static ts_status run_backward(ts_plan* plan, const ts_csr_desc* A, const ts_csr_
     LaunchCfg bcfg = cfg_of(plan->cur);
     bcfg.group = plan->cur.bwd_group;
     if (bcfg.group == 2 && (!bpk || (reinterpret_cast<uintptr_t>(dB) & 15))) bcfg.group = 16;  // no quads
+    // option T: dA from the kernels (dB skipped), dB by the ordered pull
+    const bool det = plan->cur.dB_mode == 2 && dB && L.bt;
     TS_CUDA(launch_backward(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC,
-                            dA, dB, bpk, sc, bcfg, (cudaStream_t)stream),
+                            dA, det ? nullptr : dB, bpk, sc, bcfg, (cudaStream_t)stream),
             fn);
+    if (det)
+        TS_CUDA(launch_backward_t(dev(A), dev(B), plan->d, (const long long*)C->rowptr, C->col, C->nnz, dC, dB,
+                                  (char*)ws + L.bt, sc.hdr, (cudaStream_t)stream),
+                fn);
     return ok();
 }
 
@@ -706,7 +717,7 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
         if (w <= dpad && w >= std::max<long long>(64, round_up(dpad / 8, 32))) tiles.push_back(w);
     if (tiles.empty() || tiles.back() < std::min<long long>(dpad, 4096))
         tiles.push_back((int)std::min<long long>(dpad, 4096));
-    for (int field = 0; field < 9 && s == TS_OK; ++field) {
+    for (int field = 0; field < 10 && s == TS_OK; ++field) {
         std::vector<ts_tuning> cands;
         ts_tuning c = best;
         switch (field) {
@@ -743,6 +754,10 @@ extern "C" ts_status ts_plan_autotune(ts_plan* plan, const ts_csr_desc* A, const
             case 7:
                 if (plan->force.bwd_group || !do_bwd) break;
                 for (int g : {1, 2, 8, 16, 32}) { c.bwd_group = g; cands.push_back(c); }
+                break;
+            case 9:
+                if (plan->force.dB_mode || !do_bwd) break;
+                for (int m : {1, 2}) { c.dB_mode = m; cands.push_back(c); }
                 break;
             case 8:
                 if (plan->force.row_lanes || !vals) break;

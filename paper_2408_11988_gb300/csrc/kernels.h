@@ -142,6 +142,12 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
                             const int2* Bpk, const Sched& s, const LaunchCfg& cfg, cudaStream_t st);
 size_t backward_smem(long long d, int warps);
 
+// Deterministic dB (option T): workspace bytes, and the pass (transpose of
+// A's pattern by a stable radix sort, pull over B's rows, ordered sums).
+size_t backward_t_bytes(long long n, long long nnzA, long long nnzB, long long d);
+cudaError_t launch_backward_t(const DevCsr& A, const DevCsr& B, long long d, const long long* Cp, const int* Ci,
+                              long long nnzC, const float* dC, float* dB, void* ws, WsHeader* hdr, cudaStream_t st);
+
 // Multi-source BFS (Alg. 3) levels.
 cudaError_t launch_msbfs_init(long long n, int d, const int* src, unsigned* S, int* levels,
                               long long* rp, int* col, cudaStream_t st);

@@ -85,9 +85,10 @@ def test_backward_unaligned_db_and_b_tail():
         assert np.all(rest == 7.0)  # nothing written outside dB
 
 
-def test_backward_finite_differences():
+@pytest.mark.parametrize("tuning", [None, {"dB_mode": 2}])
+def test_backward_finite_differences(tuning):
     A, B = synth.rmat_embedding(scale=9, edge_factor=8, d=64, density=0.1, seed=52)
-    rp, col, dC, dA, dB = _run(A, B, seed=3)
+    rp, col, dC, dA, dB = _run(A, B, tuning=tuning, seed=3)
     dC64 = dC.astype(np.float64)
     Cp, Ci, Cx, _ = oracle.spgemm(A, B)
 
@@ -134,11 +135,13 @@ def test_autograd_function():
     assert np.all(np.abs(b.grad.cpu().numpy() - rB) <= REL * bB)
 
 
-def test_backward_full_size_sampled():
-    # sparse-embedding workload at full size (R-MAT scale 22, d = 256, 5 %)
+@pytest.mark.parametrize("tuning", [None, {"dB_mode": 2}])
+def test_backward_full_size_sampled(tuning):
+    # sparse-embedding workload at full size (R-MAT scale 22, d = 256, 5 %),
+    # dB by float atomics and by the deterministic transpose pull
     A, B = synth.rmat_embedding()
     Ad, Bd = dev(A), dev(B)
-    plan = Plan(Ad, Bd)
+    plan = Plan(Ad, Bd, tuning=tuning)
     C = plan.forward(Ad, Bd)
     dC = synth.grad_output(C.nnz, 11)
     dA, dB = plan.backward(Ad, Bd, C, torch.as_tensor(dC, device="cuda"))
@@ -209,3 +212,42 @@ def test_backward_wide_rows_long_b_rows_and_hub():
     rA, bA, rB, bB = oracle.backward(A2, B, rp, col, dC.astype(np.float64))
     assert np.all(np.abs(dA - rA) <= REL * bA)
     assert np.all(np.abs(dB - rB) <= REL * bB)
+
+
+@pytest.mark.parametrize("case", ["rmat256", "rmat1024", "er64", "hub"])
+def test_backward_deterministic_db(case):
+    # option T: dB without float atomics, identical bit for bit on repeated
+    # calls, and within the bound of the FP64 oracle like option S
+    if case == "rmat256":
+        A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=256, density=0.05, seed=70)
+    elif case == "rmat1024":
+        A, B = synth.rmat_embedding(scale=12, edge_factor=16, d=1024, density=0.01, seed=71, b_values="uniform")
+    elif case == "er64":
+        A, B = synth.er_product(n=3000, k=5, d=64, density=0.1, seed=72)
+    else:  # a column of A with thousands of entries (several chunks of the pull) and empty rows of B
+        n = 5000
+        rng = np.random.default_rng(73)
+        rows = [np.unique(np.concatenate([[7], rng.choice(n, 4, replace=False)])) for _ in range(n)]
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        rowptr[1:] = np.cumsum([len(r) for r in rows])
+        from synth import CSR
+        A = CSR(n, n, rowptr, np.concatenate(rows).astype(np.int32), synth.uniform(int(rowptr[-1]), 74))
+        B = synth.tall_skinny(n, 128, 0.05, 75)
+        B.val = synth.normal(B.nnz, 76)
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd, tuning={"dB_mode": 2})
+    C = plan.forward(Ad, Bd)
+    dC = torch.as_tensor(synth.grad_output(C.nnz, 77), device="cuda")
+    dA1, dB1 = plan.backward(Ad, Bd, C, dC)
+    dA2, dB2 = plan.backward(Ad, Bd, C, dC)
+    plan.check()
+    assert torch.equal(dB1, dB2)
+    rp, col, _ = C.to_host()
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.double().cpu().numpy())
+    assert np.all(np.abs(dA1.cpu().numpy() - rA) <= REL * bA)
+    assert np.all(np.abs(dB1.cpu().numpy() - rB) <= REL * bB)
+    # option S on the same product agrees within the bound
+    plan_s = Plan(Ad, Bd, tuning={"dB_mode": 1})
+    Cs = plan_s.forward(Ad, Bd)
+    _, dBs = plan_s.backward(Ad, Bd, Cs, dC)
+    assert np.all(np.abs(dBs.cpu().numpy() - rB) <= REL * bB)
