@@ -187,11 +187,22 @@ def dist_env():
     return world()
 
 
-def make_inputs(name, seed_offset=0, scale=None):
+def _override_tag(args):
+    """Suffix of the workload name for a run with a shape override ('' without)."""
+    tag = ""
+    for key in ("scale", "d", "density"):
+        v = getattr(args, key, None)
+        if v is not None:
+            tag += f"@{key}{v}"
+    return tag
+
+
+def make_inputs(name, seed_offset=0, scale=None, d=None, density=None):
     import synth
     desc, kw, tuning, bwd = WORKLOADS[name]
-    if scale is not None and kw is not None:
-        kw = dict(kw, scale=scale)
+    if kw is not None:
+        over = {k: v for k, v in (("scale", scale), ("d", d), ("density", density)) if v is not None}
+        kw = dict(kw, **over)
     if name == "er-16k":
         A, B = synth.er_product(seed=synth.BASE_SEED + 1 + 1000 * seed_offset)
     else:
@@ -297,7 +308,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
     desc, _, wl_tuning, want_bwd = WORKLOADS[name]
     steps = steps or args.steps
     warmup = warmup or args.warmup
-    A, B = make_inputs(name, seed_offset=rank, scale=args.scale)
+    A, B = make_inputs(name, seed_offset=rank, scale=args.scale, d=args.d, density=args.density)
     flops_row = products_per_row(A, B)
     F = int(flops_row.sum())
     Ad, Bd = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
@@ -395,7 +406,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
         "ms_per_step_median": round(statistics.median([a + b + c for a, b, c in zip(sym, num, bwd)]), 4),
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": product_config(name + (f"@scale{args.scale}" if args.scale else ""), desc, A, B, F, ws),
+        "config": product_config(name + _override_tag(args), desc, A, B, F, ws),
         "nnz_C": nnzC,
         "tuning": plan.tuning,
         "roofline": {"bound": "hbm", "kernel": "numeric pass (every kernel of ts_spgemm_numeric: packing of B, accumulating kernels)",
@@ -403,7 +414,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "bytes_per_launch": num_bytes,
                      "bytes_formula": "tiles*(16(n+1)+24 nnz_A) + 8 products + 8 nnz_C",
-                     "traffic": None if args.scale else _traffic(name),
+                     "traffic": None if _override_tag(args) else _traffic(name),
                      "column_tiles": tiles, "compulsory_bytes": comp_bytes,
                      "compulsory_frac": round(comp_bytes / (num_ms * 1e-3) / 1e9 / peak, 4)},
         "phases_ms": {"symbolic": round(statistics.mean(sym), 4), "numeric": round(num_ms, 4),
@@ -442,6 +453,8 @@ def main():
     ap.add_argument("--tuning", default=None, help="JSON dict of forced tuning fields")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT scale override (smaller copies of a workload for profiling)")
+    ap.add_argument("--d", type=int, default=None, help="columns of B override (profiling)")
+    ap.add_argument("--density", type=float, default=None, help="density of B override (profiling)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     desc, _, wl_tuning, want_bwd = WORKLOADS[args.workload]
@@ -459,7 +472,7 @@ def main():
     dist = _dist_setup(ws, local)
     line = measure_product(args, args.workload, ws, rank, local, dist, tuning_json=args.tuning)
     failed = line["verified"] is not None and not line["verified"]["ok"]
-    if args.workload == "embed-s22" and ws == 1 and not args.no_extra and args.scale is None and not args.tuning:
+    if args.workload == "embed-s22" and ws == 1 and not args.no_extra and not _override_tag(args) and not args.tuning:
         # the other two configurations the target names, as nested records
         sub = argparse.Namespace(**vars(args))
         sub.autotune = False
@@ -891,7 +904,7 @@ def run_reference(args, ws, rank, desc, want_bwd):
         return
     if args.workload in ("msbfs-s20", "msbfs-parents-s20", "force2vec-s20", "batched-64"):
         return _reference_other(args, ws, desc)
-    A, B = make_inputs(args.workload)
+    A, B = make_inputs(args.workload, scale=args.scale, d=args.d, density=args.density)
     F = int(products_per_row(A, B).sum())
     import oracle  # noqa: F401
     for _ in range(args.warmup):
@@ -910,7 +923,7 @@ def run_reference(args, ws, rank, desc, want_bwd):
         "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": product_config(args.workload, desc, A, B, F, ws),
+        "config": product_config(args.workload + _override_tag(args), desc, A, B, F, ws),
         "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": sample, "host": host_info()},
         "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
