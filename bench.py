@@ -197,6 +197,12 @@ def _override_tag(args):
     return tag
 
 
+def _override_desc(args, desc):
+    """The workload's description, with the overridden shape named after it."""
+    tag = _override_tag(args)
+    return desc if not tag else desc + " [overridden: " + ", ".join(tag[1:].split("@")) + "]"
+
+
 def make_inputs(name, seed_offset=0, scale=None, d=None, density=None):
     import synth
     desc, kw, tuning, bwd = WORKLOADS[name]
@@ -406,7 +412,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
         "ms_per_step_median": round(statistics.median([a + b + c for a, b, c in zip(sym, num, bwd)]), 4),
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": product_config(name + _override_tag(args), desc, A, B, F, ws),
+        "config": product_config(name + _override_tag(args), _override_desc(args, desc), A, B, F, ws),
         "nnz_C": nnzC,
         "tuning": plan.tuning,
         "roofline": {"bound": "hbm", "kernel": "numeric pass (every kernel of ts_spgemm_numeric: packing of B, accumulating kernels)",
@@ -923,7 +929,7 @@ def run_reference(args, ws, rank, desc, want_bwd):
         "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": product_config(args.workload + _override_tag(args), desc, A, B, F, ws),
+        "config": product_config(args.workload + _override_tag(args), _override_desc(args, desc), A, B, F, ws),
         "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": sample, "host": host_info()},
         "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
