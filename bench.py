@@ -459,6 +459,8 @@ def main():
     ap.add_argument("--tuning", default=None, help="JSON dict of forced tuning fields")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT scale override (smaller copies of a workload for profiling)")
+    ap.add_argument("--batched-autotune", default="instance", choices=["instance", "none"],
+                    help="batched-64: per-instance autotuning (default) or the plan's default tuning")
     ap.add_argument("--d", type=int, default=None, help="columns of B override (profiling)")
     ap.add_argument("--density", type=float, default=None, help="density of B override (profiling)")
     args = ap.parse_args()
@@ -658,7 +660,8 @@ def batched_record(args, ws, rank, local, dist, steps=None, warmup=None):
     # per-instance tuning (accumulator kind, heavy-row threshold) by the
     # batched autotuner, each instance timed on its own
     t_at = time.perf_counter()
-    bp.autotune(reps=1)
+    if args.batched_autotune != "none":
+        bp.autotune(reps=1)
     autotune_s = time.perf_counter() - t_at
     Cs = bp.forward()
     torch.cuda.synchronize()

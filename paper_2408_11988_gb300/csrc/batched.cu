@@ -557,9 +557,11 @@ __global__ void __launch_bounds__(256, 3) k_bat_numeric(const InstDesc* __restri
 // ---------------------------------------------------------------------------
 // backward: dA(i,k) = sum_j dC(i,j) B(k,j) on A's pattern, dB(k,j) += A(i,k)
 // dC(i,j) on B's pattern.  Row i's dC is scattered into a dense shared row;
-// groups of four lanes take one entry of A each (its segment of B on the
-// packed copy), reduce dA within the group and add the dB terms with float
-// atomics.
+// groups of four lanes take two entries of A at a time (their segments of B
+// on the row-aligned copy, 16-byte loads), reduce dA within the group and
+// add the dB terms with float atomics.  A row's entries go in chunks through
+// a three-stage pipeline (entries of A, then B's row pointers, then the
+// walk), as in the forward's wide rows.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_bat_zero_grads(const InstDesc* __restrict__ inst) {
     const InstDesc& I = inst[blockIdx.y];
@@ -570,44 +572,147 @@ __global__ void __launch_bounds__(256) k_bat_zero_grads(const InstDesc* __restri
         for (long long e = t0; e < I.bnnz; e += st) I.dB[e] = 0.0f;
 }
 
-// Entries [first, e1) of A's row i, in chunks first, first + stride, ...,
-// against the dense dC row gr.
-__device__ __forceinline__ void bat_bwd_range(const InstDesc& I, const float* gr, long long first, long long e1,
-                                              long long stride, unsigned long long* err) {
+// Both terms of one 16-byte group of the row-aligned copy (entries j and
+// j + 1 of B): dB(k, .) += a * dC(i, col) with float atomics, and the dA
+// part B(k, .) * dC(i, col) returned.  Pads carry column -1 and add nothing.
+__device__ __forceinline__ float bat_bwd_group(const InstDesc& I, const float* gr, const int4& v, float a,
+                                               long long j, unsigned W) {
+    float part = 0.0f;
+    if ((unsigned)v.x < W) {
+        const float g = gr[v.x];
+        part = __int_as_float(v.y) * g;
+        if (I.dB) atomicAdd(I.dB + j, a * g);
+    }
+    if ((unsigned)v.z < W) {
+        const float g = gr[v.z];
+        part = fmaf(__int_as_float(v.w), g, part);
+        if (I.dB) atomicAdd(I.dB + j + 1, a * g);
+    }
+    return part;
+}
+
+// The segments of up to 32 entries of A held by the lanes (lane l: entry
+// e0 + l, the first group g0 and groups ng of its row of B in the row-aligned
+// copy, B's index s of that row's first entry, A's value a) against the
+// dense dC row gr.  Groups of four lanes take two segments at a time, lane
+// gl their groups gl, gl + 4 (four 16-byte loads in flight before any is
+// used); the dA sum of each segment is reduced over its four lanes.
+__device__ __forceinline__ void bat_bwd_walk(const InstDesc& I, const float* gr, unsigned g0, int ng, long long s,
+                                             float a, int nv, long long e0) {
     const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
-    const int2* Q = reinterpret_cast<const int2*>(I.Bq);
+    const unsigned W = (unsigned)I.W;
+    const int4* Q = reinterpret_cast<const int4*>(I.Bq);
+    const int4 none = make_int4(-1, 0, -1, 0);
+    for (int s0 = 0; s0 < nv; s0 += 16) {
+        const int ea = s0 + grp, eb = s0 + 8 + grp;
+        const unsigned ga = __shfl_sync(FULL, g0, ea & 31), gb = __shfl_sync(FULL, g0, eb & 31);
+        int na = __shfl_sync(FULL, ng, ea & 31), nb = __shfl_sync(FULL, ng, eb & 31);
+        const long long sa = shfl64(s, ea & 31), sb = shfl64(s, eb & 31);
+        const float xa = __shfl_sync(FULL, a, ea & 31), xb = __shfl_sync(FULL, a, eb & 31);
+        if (ea >= nv) na = 0;
+        if (eb >= nv) nb = 0;
+        const int nm = na > nb ? na : nb;
+        float pa = 0.0f, pb = 0.0f;
+        for (int q = gl; q < nm; q += 8) {
+            int4 u0 = none, u1 = none, v0 = none, v1 = none;
+            if (q < na) u0 = __ldg(Q + ga + q);
+            if (q < nb) v0 = __ldg(Q + gb + q);
+            if (q + 4 < na) u1 = __ldg(Q + ga + q + 4);
+            if (q + 4 < nb) v1 = __ldg(Q + gb + q + 4);
+            pa += bat_bwd_group(I, gr, u0, xa, sa + 2LL * q, W);
+            pb += bat_bwd_group(I, gr, v0, xb, sb + 2LL * q, W);
+            pa += bat_bwd_group(I, gr, u1, xa, sa + 2LL * (q + 4), W);
+            pb += bat_bwd_group(I, gr, v1, xb, sb + 2LL * (q + 4), W);
+        }
+        pa += __shfl_xor_sync(FULL, pa, 1);
+        pb += __shfl_xor_sync(FULL, pb, 1);
+        pa += __shfl_xor_sync(FULL, pa, 2);
+        pb += __shfl_xor_sync(FULL, pb, 2);
+        if (gl == 0 && I.dA) {
+            if (ea < nv) I.dA[e0 + ea] = pa;
+            if (eb < nv) I.dA[e0 + eb] = pb;
+        }
+    }
+}
+
+// Entry e of A for this lane (ok: inside the chunk) and its row of B in the
+// row-aligned copy (ng = 0 when none; a column outside [0, n) is an input
+// error).
+__device__ __forceinline__ void bat_bwd_entry(const InstDesc& I, long long e, bool ok, int& k, float& a) {
+    k = -1;
+    a = 0.0f;
+    if (ok) {
+        k = __ldg(I.A_col + e);
+        a = __ldg(I.A_val + e);
+    }
+}
+
+__device__ __forceinline__ void bat_bwd_seg(const InstDesc& I, int k, unsigned& g0, int& ng, long long& s,
+                                            unsigned long long* err) {
+    g0 = 0;
+    ng = 0;
+    s = 0;
+    if (k < 0) return;
+    if (k < I.n) {
+        int len;
+        padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, k, s, len, g0);
+        ng = (len + 1) >> 1;
+    } else {
+        atomicOr(err, ERR_A_COL);
+    }
+}
+
+// Entries [first, e1) of A's row i, in chunks of cs <= 32 entries at first,
+// first + stride, ..., against the dense dC row gr, in three stages: while
+// chunk c is walked, the row pointers of B for chunk c + 1 and the entries
+// of A of chunk c + 2 are in flight.
+__device__ __forceinline__ void bat_bwd_range(const InstDesc& I, const float* gr, long long first, long long e1,
+                                              long long stride, int cs, unsigned long long* err) {
+    const int lane = lane_id();
+    const bool mine = lane < cs;
+    int k;
+    float a;
+    bat_bwd_entry(I, first + lane, mine && first + lane < e1, k, a);
+    unsigned g0;
+    int ng;
+    long long s;
+    bat_bwd_seg(I, k, g0, ng, s, err);
+    float ca = a;
+    bat_bwd_entry(I, first + stride + lane, mine && first + stride + lane < e1, k, a);
     for (long long e = first; e < e1; e += stride) {
-        const int nv = e1 - e < 32 ? (int)(e1 - e) : 32;
-        int k = -1;
-        float a = 0.0f;
-        long long s = 0;
-        unsigned q0 = 0;
-        int len = 0;
-        if (lane < nv) {
-            k = I.A_col[e + lane];
-            a = I.A_val[e + lane];
-            if ((unsigned)k < (unsigned)I.n) padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, k, s, len, q0);
-            else atomicOr(err, ERR_A_COL);
+        const int nv = e1 - e < cs ? (int)(e1 - e) : cs;
+        unsigned g1;
+        int ng1;
+        long long s1;
+        bat_bwd_seg(I, k, g1, ng1, s1, err);  // chunk c + 1
+        const float ca1 = a;
+        const long long e2 = e + 2 * stride;
+        bat_bwd_entry(I, e2 + lane, mine && e2 + lane < e1, k, a);  // chunk c + 2
+        bat_bwd_walk(I, gr, g0, ng, s, ca, nv, e);
+        g0 = g1;
+        ng = ng1;
+        s = s1;
+        ca = ca1;
+    }
+}
+
+// Row i of dC scattered into the dense row (or cleared from it) by nt
+// threads from t0, four entries per thread in flight.
+__device__ __forceinline__ void bat_scatter_dc(const InstDesc& I, long long i, float* row, int t0, int nt,
+                                               bool clear) {
+    const long long c0 = clampll(I.C_rowptr[i], 0, I.cap), c1 = clampll(I.C_rowptr[i + 1], c0, I.cap);
+    for (long long x = c0 + t0; x < c1; x += 4LL * nt) {
+        int cc[4];
+        float vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long xu = x + (long long)u * nt;
+            cc[u] = xu < c1 ? __ldg(I.C_col + xu) : -1;
+            vv[u] = (xu < c1 && !clear) ? __ldg(I.dC + xu) : 0.0f;
         }
-        for (int s0 = 0; s0 < nv; s0 += 8) {
-            const int src = s0 + grp;  // < 32
-            const long long bs = shfl64(s, src);
-            const unsigned bq = __shfl_sync(FULL, q0, src);
-            const int bl = __shfl_sync(FULL, len, src);  // 0 past the chunk
-            const float ba = __shfl_sync(FULL, a, src);
-            float part = 0.0f;
-            for (int j = gl; j < bl; j += 4) {
-                const int2 v = __ldg(Q + 2 * (size_t)bq + j);
-                if ((unsigned)v.x < (unsigned)I.W) {
-                    const float t = gr[v.x];
-                    part = fmaf(t, __int_as_float(v.y), part);
-                    if (I.dB) atomicAdd(I.dB + bs + j, ba * t);
-                }
-            }
-            part += __shfl_xor_sync(FULL, part, 1);
-            part += __shfl_xor_sync(FULL, part, 2);
-            if (gl == 0 && src < nv && I.dA) I.dA[e + src] = part;
-        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if ((unsigned)cc[u] < (unsigned)I.W) row[cc[u]] = vv[u];
     }
 }
 
@@ -623,14 +728,6 @@ __global__ void __launch_bounds__(256, 4) k_bat_backward(const InstDesc* __restr
     float* wrow = reinterpret_cast<float*>(smem) + (size_t)warp * Wmax;
     float* trow = reinterpret_cast<float*>(smem);  // the block's row (warp 0's)
     const long long nheavy = (long long)ctl->nheavy;
-    // dC of row i scattered into (or cleared from) a dense row
-    auto scatter = [&](const InstDesc& I, long long i, float* row, int t0, int nt, bool clear) {
-        const long long c0 = clampll(I.C_rowptr[i], 0, I.cap), c1 = clampll(I.C_rowptr[i + 1], c0, I.cap);
-        for (long long x = c0 + t0; x < c1; x += nt) {
-            const int c = I.C_col[x];
-            if ((unsigned)c < (unsigned)I.W) row[c] = clear ? 0.0f : I.dC[x];
-        }
-    };
     for (;;) {
         if (tid == 0) s_item = (long long)atomicAdd(&ctl->q_bwd, 1ull);
         __syncthreads();
@@ -641,12 +738,15 @@ __global__ void __launch_bounds__(256, 4) k_bat_backward(const InstDesc* __restr
         const InstDesc& I = inst[inst_of(inst, count, g)];
         const long long i = g - I.row_off;
         if (!I.dC) continue;
-        scatter(I, i, trow, tid, blockDim.x, false);
+        bat_scatter_dc(I, i, trow, tid, blockDim.x, false);
         __syncthreads();
         const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
-        bat_bwd_range(I, trow, a0 + 32LL * warp, a1, 32LL * nwarps, err);
+        // chunks of 16 entries when the row has too few for every warp to
+        // take two chunks of 32
+        const int cs = a1 - a0 >= 64LL * nwarps ? 32 : 16;
+        bat_bwd_range(I, trow, a0 + (long long)cs * warp, a1, (long long)cs * nwarps, cs, err);
         __syncthreads();
-        scatter(I, i, trow, tid, blockDim.x, true);
+        bat_scatter_dc(I, i, trow, tid, blockDim.x, true);
         __syncthreads();
     }
     const long long nchunks = (g1 - g0 + 31) / 32;
@@ -660,12 +760,12 @@ __global__ void __launch_bounds__(256, 4) k_bat_backward(const InstDesc* __restr
             const InstDesc& I = inst[__shfl_sync(FULL, b, src)];
             if (!I.dC) continue;
             const long long i = g0 + ch * 32 + src - I.row_off;
-            scatter(I, i, wrow, lane, 32, false);
+            bat_scatter_dc(I, i, wrow, lane, 32, false);
             __syncwarp();
             const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
-            bat_bwd_range(I, wrow, a0, a1, 32, err);
+            bat_bwd_range(I, wrow, a0, a1, 32, 32, err);
             __syncwarp();
-            scatter(I, i, wrow, lane, 32, true);
+            bat_scatter_dc(I, i, wrow, lane, 32, true);
             __syncwarp();
         }
     }
@@ -706,8 +806,12 @@ static unsigned row_grid(long long rows, int sms) {
 cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
                                int* heavy, BatchCtl* ctl, int sms, cudaStream_t st) {
     if (g1 <= g0) return cudaSuccess;
+    // no more blocks than stay resident: the blocks share the rows evenly,
+    // so a second wave would double the time of its blocks' shares
+    const unsigned rg = row_grid(8 * (g1 - g0), sms);
+    const unsigned pg = (unsigned)persistent_grid((const void*)k_bat_prepare, 256, 0, sms);
     count_launch();
-    k_bat_prepare<<<row_grid(8 * (g1 - g0), sms), 256, 0, st>>>(inst, count, g0, g1, flops, heavy, ctl);
+    k_bat_prepare<<<rg < pg ? rg : pg, 256, 0, st>>>(inst, count, g0, g1, flops, heavy, ctl);
     return cudaGetLastError();
 }
 
