@@ -1465,7 +1465,7 @@ extern "C" ts_status ts_spgemm_batched_backward(ts_batched_plan* plan, int32_t c
     char* w = (char*)ws;
     BatchCtl* ctl = (BatchCtl*)(w + L.ctl);
     // the backward reuses the forward's row flops, heavy list and C pattern
-    TS_CUDA(cudaMemsetAsync(&ctl->q_bwd, 0, sizeof ctl->q_bwd, st), fn);
+    TS_CUDA(cudaMemsetAsync(&ctl->q_bwd, 0, 2 * sizeof ctl->q_bwd, st), fn);  // q_bwd, l_bwd
     TS_CUDA(launch_bat_backward((const InstDesc*)(w + L.inst), plan->count, 0, plan->N, plan->max_work,
                                 (const long long*)(w + L.flops), (const int*)(w + L.heavy), ctl, plan->Wmax,
                                 sm_count(), st),

@@ -196,18 +196,40 @@ __device__ __forceinline__ bool bat_light(const InstDesc* inst, int count, const
     return f < __ldg(&inst[b].heavy_min);
 }
 
+// This warp's next 32-row chunk from queue q: chunks are dealt c0, c0 + 1,
+// ... in order as warps ask for them (>= the caller's end when none is
+// left), so a warp that drew heavy chunks takes fewer of them.
+__device__ __forceinline__ long long bat_next_chunk(unsigned long long* q, long long c0) {
+    unsigned long long t = 0;
+    if (lane_id() == 0) t = atomicAdd(q, 1ull);
+    return c0 + (long long)__shfl_sync(FULL, t, 0);
+}
+
+// Byte marks (symbolic light rows): column c of the slot's row is reached.
+// Lanes that reach the same column store the same byte, so no atomic is
+// needed.
+struct AddByte {
+    unsigned char* m;
+    __device__ __forceinline__ void operator()(int c, unsigned W, float) const {
+        if ((unsigned)c < W) m[c] = 1;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // symbolic: row counts into each C_b's row pointers (C_b.rowptr[i + 1])
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict__ inst, int count, long long c0,
                                                       long long c1, const long long* __restrict__ flops,
-                                                      const int* __restrict__ heavy, BatchCtl* ctl) {
-    __shared__ unsigned s_bm[9][33];   // the block's bitmap (heavy rows) in s_bm[8]
-    __shared__ unsigned s_rg[8][4 * 33];  // four slot bitmaps per warp (light rows)
+                                                      const int* __restrict__ heavy, BatchCtl* ctl, int Wmax) {
+    __shared__ unsigned s_bm[9][33];  // the block's bitmap (heavy rows) in s_bm[8]
+    // four slots of byte marks per warp (light rows), Wmax + 32 bytes each
+    // (the pad puts the slots' words on different banks)
+    extern __shared__ __align__(16) unsigned char s_marks[];
     __shared__ long long s_item;
     const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
+    const int mstride = Wmax + 32;
     for (int x = tid; x < 9 * 33; x += blockDim.x) (&s_bm[0][0])[x] = 0u;
-    for (int x = tid; x < 8 * 4 * 33; x += blockDim.x) (&s_rg[0][0])[x] = 0u;
+    for (int x = tid; x < nwarps * 4 * mstride / 4; x += blockDim.x) reinterpret_cast<unsigned*>(s_marks)[x] = 0u;
     __syncthreads();
     unsigned long long* err = &ctl->err;
     const long long nheavy = (long long)ctl->nheavy;
@@ -242,11 +264,10 @@ __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict
         __syncthreads();
     }
     // light rows in row groups: four rows per warp (eight lanes each, the
-    // chunk's rows sorted by products), each marking its own bitmap
-    unsigned* rbm = s_rg[warp];
+    // chunk's rows sorted by products), each marking its own bytes
     const int lanes = lane & 7, slot = lane >> 3;
-    unsigned* mybm = rbm + 33 * slot;
-    for (long long c = c0 + (long long)blockIdx.x * nwarps + warp; c < c1; c += (long long)gridDim.x * nwarps) {
+    unsigned char* mym = s_marks + (size_t)(warp * 4 + slot) * mstride;
+    for (long long c = bat_next_chunk(&ctl->l_sym, c0); c < c1; c = bat_next_chunk(&ctl->l_sym, c0)) {
         const InstDesc& I = inst[inst_of_chunk(inst, count, c)];
         const long long i0 = (c - I.chunk_off) * 32;
         {
@@ -273,12 +294,13 @@ __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict
             float x0, x1;
             rg_load_a(p, a0 + lanes, lanes < len, k0, x0);
             rg_load_a(p, a0 + 8 + lanes, 8 + lanes < len, k1, x1);
-            rgp_tile<8, 2>(p, I.Bq, AddMark{mybm}, a0, len, lmax, err, k0, x0, k1, x1);
+            rgp_tile<8, 2>(p, I.Bq, AddByte{mym}, a0, len, lmax, err, k0, x0, k1, x1);
             __syncwarp();
             int cnt = 0;
-            for (int w = lanes; w < nw; w += 8) {
-                cnt += __popc(mybm[w]);
-                mybm[w] = 0u;
+            unsigned* mw = reinterpret_cast<unsigned*>(mym);
+            for (int w = lanes; w < nw * 8; w += 8) {  // bytes are 0 or 1
+                cnt += __popc(mw[w]);
+                mw[w] = 0u;
             }
             cnt += __shfl_xor_sync(FULL, cnt, 1);
             cnt += __shfl_xor_sync(FULL, cnt, 2);
@@ -338,28 +360,34 @@ __global__ void __launch_bounds__(1024) k_bat_scan(const InstDesc* __restrict__ 
 // ---------------------------------------------------------------------------
 // numeric
 // ---------------------------------------------------------------------------
-// Row i of a dense-B instance summed by `first`/`stride` chunks of this warp
-// (registers), V = Wd / 32 columns per lane.
+// Row i of a dense-B instance: the warp (team: the block, its warps taking
+// the row's chunks in turn and summing their partial rows) holds V columns
+// per lane in registers.  A copy wider than 32 V columns (Wd = 256 with
+// V = 4) is walked in bands of 32 V columns, each written out in turn, so
+// that no lane holds more than four columns.
 template <int V>
 __device__ __forceinline__ void bat_dense_row(const NumParams& p, const InstDesc& I, long long i, long long a0,
                                               long long a1, bool team, float* s_rows, unsigned* s_mask,
                                               unsigned long long* err) {
-    float acc[V];
-    unsigned m = 0;
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.0f;
     const int nwarps = blockDim.x >> 5;
-    if (team) {
-        dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0 + 32LL * warp_id(), a1, 32LL * nwarps, acc, m, err);
-        dense_block_sum<V>(acc, m, s_rows, s_mask);
-        if (warp_id() != 0) return;
-    } else {
-        dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0, a1, 32, acc, m, err);
-    }
+    const bool writer = !team || warp_id() == 0;
     const long long out = clampll(I.C_rowptr[i], 0, I.cap);
     const long long out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
-    const int tot = dense_emit<V>(acc, m, out, out_end, I.C_col, I.C_val);
-    if (lane_id() == 0 && out + tot != out_end) atomicOr(err, ERR_C_ROW);
+    long long pos = out;
+    for (int cb = 0; cb < I.Wd; cb += 32 * V) {
+        float acc[V];
+        unsigned m = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+        if (team) {
+            dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0 + 32LL * warp_id(), a1, 32LL * nwarps, acc, m, err, cb);
+            dense_block_sum<V>(acc, m, s_rows, s_mask);
+        } else {
+            dense_accumulate<V>(p, I.Bd, I.Bbits, I.Wd, a0, a1, 32, acc, m, err, cb);
+        }
+        if (writer) pos += dense_emit<V>(acc, m, pos, out_end, I.C_col, I.C_val, cb);
+    }
+    if (writer && lane_id() == 0 && pos != out_end) atomicOr(err, ERR_C_ROW);
 }
 
 __device__ __forceinline__ void bat_dense_any(const NumParams& p, const InstDesc& I, long long i, long long a0,
@@ -368,8 +396,7 @@ __device__ __forceinline__ void bat_dense_any(const NumParams& p, const InstDesc
     switch (I.Wd) {
         case 32: bat_dense_row<1>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
         case 64: bat_dense_row<2>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
-        case 128: bat_dense_row<4>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
-        default: bat_dense_row<8>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;
+        default: bat_dense_row<4>(p, I, i, a0, a1, team, s_rows, s_mask, err); break;  // 128, 256
     }
 }
 
@@ -391,7 +418,7 @@ __global__ void __launch_bounds__(256, 3) k_bat_numeric(const InstDesc* __restri
                                                         const int* __restrict__ heavy, BatchCtl* ctl, int Wmax,
                                                         bool values) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float s_rows[8 * 256];
+    __shared__ float s_rows[8 * 128];  // dense-B partial rows (V <= 4)
     __shared__ unsigned s_mask[8 * 32];
     __shared__ long long s_item;
     const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
@@ -492,7 +519,7 @@ __global__ void __launch_bounds__(256, 3) k_bat_numeric(const InstDesc* __restri
     // instances one row per warp in registers; otherwise one row per warp on
     // the warp's shared accumulator.
     const int lanes = lane & 7, slot = lane >> 3;
-    for (long long c = c0 + (long long)blockIdx.x * nwarps + warp; c < c1; c += (long long)gridDim.x * nwarps) {
+    for (long long c = bat_next_chunk(&ctl->l_num, c0); c < c1; c = bat_next_chunk(&ctl->l_num, c0)) {
         const InstDesc& I = inst[inst_of_chunk(inst, count, c)];
         const long long i0 = (c - I.chunk_off) * 32;
         const NumParams p = inst_params(I);
@@ -750,7 +777,7 @@ __global__ void __launch_bounds__(256, 4) k_bat_backward(const InstDesc* __restr
         __syncthreads();
     }
     const long long nchunks = (g1 - g0 + 31) / 32;
-    for (long long ch = (long long)blockIdx.x * nwarps + warp; ch < nchunks; ch += (long long)gridDim.x * nwarps) {
+    for (long long ch = bat_next_chunk(&ctl->l_bwd, 0); ch < nchunks; ch = bat_next_chunk(&ctl->l_bwd, 0)) {
         const long long g = g0 + ch * 32 + lane;
         int b;
         unsigned rows = __ballot_sync(FULL, bat_light(inst, count, flops, g, g1, b));
@@ -816,12 +843,14 @@ cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, lo
 }
 
 cudaError_t launch_bat_symbolic(const InstDesc* inst, int count, long long c0, long long c1, long long,
-                                const long long* flops, const int* heavy, BatchCtl* ctl, int, int sms,
+                                const long long* flops, const int* heavy, BatchCtl* ctl, int Wmax, int sms,
                                 cudaStream_t st) {
     if (c1 <= c0) return cudaSuccess;
-    const int grid = persistent_grid((const void*)k_bat_symbolic, 256, 0, sms);
+    if (Wmax < 32 || Wmax > 1024 || (Wmax & 31)) return cudaErrorInvalidValue;
+    const size_t smem = 8 * 4 * (size_t)(Wmax + 32);
+    const int grid = persistent_grid((const void*)k_bat_symbolic, 256, smem, sms);
     count_launch();
-    k_bat_symbolic<<<grid, 256, 0, st>>>(inst, count, c0, c1, flops, heavy, ctl);
+    k_bat_symbolic<<<grid, 256, smem, st>>>(inst, count, c0, c1, flops, heavy, ctl, Wmax);
     return cudaGetLastError();
 }
 

@@ -10,12 +10,13 @@
 namespace ts {
 
 // V columns of row k of the dense copy for this lane, and their pattern bits
-// (bit v = column V * lane + v).
+// (bit v = column cb + V * lane + v; cb, a multiple of 32 V, selects a band
+// of a row wider than 32 V).
 template <int V>
 __device__ __forceinline__ void dense_row_load(const float* __restrict__ Bd, const unsigned* __restrict__ bits,
-                                               int dpad, int k, float (&b)[V], unsigned& m) {
+                                               int dpad, int k, float (&b)[V], unsigned& m, int cb = 0) {
     const int lane = lane_id();
-    const float* r = Bd + (size_t)k * dpad + V * lane;
+    const float* r = Bd + (size_t)k * dpad + cb + V * lane;
     if constexpr (V == 8) {
         const float4 x = __ldg(reinterpret_cast<const float4*>(r));
         const float4 y = __ldg(reinterpret_cast<const float4*>(r) + 1);
@@ -30,17 +31,18 @@ __device__ __forceinline__ void dense_row_load(const float* __restrict__ Bd, con
         b[0] = __ldg(r);
     }
     const int dw = dpad >> 5;
-    const unsigned w = __ldg(bits + (size_t)k * dw + ((V * lane) >> 5));
+    const unsigned w = __ldg(bits + (size_t)k * dw + ((cb + V * lane) >> 5));
     m = (w >> ((V * lane) & 31)) & ((V == 32 ? 0u : (1u << V)) - 1u);
 }
 
 // Entries [e0, e1) of A (this warp takes e0 + lane, e0 + lane + 32 * stride... in
-// chunks): row sums into acc and the union of the patterns into m.
+// chunks): row sums into acc and the union of the patterns into m (columns
+// cb .. cb + 32 V - 1).
 template <int V>
 __device__ __forceinline__ void dense_accumulate(const NumParams& p, const float* __restrict__ Bd,
                                                  const unsigned* __restrict__ bits, int dpad, long long first,
                                                  long long e1, long long stride, float (&acc)[V], unsigned& m,
-                                                 unsigned long long* err) {
+                                                 unsigned long long* err, int cb = 0) {
     const int lane = lane_id();
     for (long long e = first; e < e1; e += stride) {
         const int nv = e1 - e < 32 ? (int)(e1 - e) : 32;
@@ -61,8 +63,8 @@ __device__ __forceinline__ void dense_accumulate(const NumParams& p, const float
             const float a0 = __shfl_sync(FULL, a, u), a1 = __shfl_sync(FULL, a, u + 1);
             float b0[V], b1[V];
             unsigned m0 = 0, m1 = 0;
-            if (k0 >= 0) dense_row_load<V>(Bd, bits, dpad, k0, b0, m0);
-            if (k1 >= 0) dense_row_load<V>(Bd, bits, dpad, k1, b1, m1);
+            if (k0 >= 0) dense_row_load<V>(Bd, bits, dpad, k0, b0, m0, cb);
+            if (k1 >= 0) dense_row_load<V>(Bd, bits, dpad, k1, b1, m1, cb);
             if (k0 >= 0) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = fmaf(a0, b0[v], acc[v]);
@@ -80,7 +82,7 @@ __device__ __forceinline__ void dense_accumulate(const NumParams& p, const float
             if (k0 >= 0) {
                 float b0[V];
                 unsigned m0 = 0;
-                dense_row_load<V>(Bd, bits, dpad, k0, b0, m0);
+                dense_row_load<V>(Bd, bits, dpad, k0, b0, m0, cb);
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = fmaf(a0, b0[v], acc[v]);
                 m |= m0;
@@ -89,11 +91,11 @@ __device__ __forceinline__ void dense_accumulate(const NumParams& p, const float
     }
 }
 
-// The warp's occupied columns written to C[out, out_end) in ascending order;
-// returns the count.
+// The warp's occupied columns (cb + V * lane + v) written to C[out, out_end)
+// in ascending order; returns the count.
 template <int V>
 __device__ __forceinline__ int dense_emit(const float (&acc)[V], unsigned m, long long out, long long out_end,
-                                          int* Ci, float* Cx) {
+                                          int* Ci, float* Cx, int cb = 0) {
     const int lane = lane_id();
     const int cnt = __popc(m);
     const int incl = warp_incl_scan(cnt);
@@ -102,7 +104,7 @@ __device__ __forceinline__ int dense_emit(const float (&acc)[V], unsigned m, lon
     for (int v = 0; v < V; ++v) {
         if ((m >> v) & 1u) {
             if (pos < out_end) {
-                Ci[pos] = V * lane + v;
+                Ci[pos] = cb + V * lane + v;
                 Cx[pos] = acc[v];
             }
             ++pos;

@@ -192,8 +192,12 @@ struct InstDesc {
     unsigned* Bbits;
 };
 // Counters and error bits of a batched call (in the workspace).
+// Counters of one batched forward (+ backward): heavy rows found, the
+// heavy-row queues of the three passes (q_*) and their light-chunk queues
+// (l_*), and the error flags.  The forward zeroes all of it, the backward
+// q_bwd and l_bwd.
 struct BatchCtl {
-    unsigned long long nheavy, q_sym, q_num, q_bwd, err;
+    unsigned long long nheavy, q_sym, q_num, q_bwd, l_bwd, l_sym, l_num, err;
 };
 // Rows [g0, g1) of the batch's numbering over the instances inst[0..count).
 cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
