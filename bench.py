@@ -658,7 +658,8 @@ def batched_record(args, ws, rank, local, dist, steps=None, warmup=None):
     del plans
     bp = BatchedProduct(As, Bs, tuning=tuning)
     # per-instance tuning (accumulator kind, heavy-row threshold) by the
-    # batched autotuner, each instance timed on its own
+    # batched autotuner: each instance timed on its own, then a few
+    # whole-batch tunings built from those choices
     t_at = time.perf_counter()
     if args.batched_autotune != "none":
         bp.autotune(reps=1)

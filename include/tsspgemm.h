@@ -405,8 +405,11 @@ TS_API ts_status msbfs_emit(const ts_csr_desc* F_next, int64_t F_next_capacity, 
  *  ts_batched_check synchronises and reports device-side errors.
  *  ts_batched_autotune times, instance by instance, every accumulator kind
  *  it may use and heavy thresholds of 1024, 4096, 16384 products and none
- *  on that instance alone, keeps the fastest in its descriptor, and leaves
- *  every C_b computed with the chosen tunings; `chosen` (may be NULL)
+ *  on that instance alone; then it times the whole batch under those
+ *  choices, under the tuning it started from, and under the instances' own
+ *  accumulators with one heavy threshold (1024, 4096 or 16384) for all, and
+ *  keeps the fastest of these.  It leaves every C_b computed with the
+ *  chosen tunings; `chosen` (may be NULL)
  *  receives instance 0's.  ts_batched_get_tuning reports instance b's
  *  tuning (accum TS_ACC_DENSE or TS_ACC_DENSE_B, col_tile = its accumulator
  *  width, cta_min_flops = its heavy threshold).

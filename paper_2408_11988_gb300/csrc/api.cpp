@@ -1315,20 +1315,18 @@ extern "C" ts_status ts_batched_get_tuning(const ts_batched_plan* plan, int32_t 
     return ok();
 }
 
-// The forward passes over instances [b0, b0 + nb) (rows g0 .. g1 - 1).
+// The forward passes over instances [b0, b0 + nb) (32-row chunks c0 .. c1 - 1).
 static ts_status bat_forward(ts_batched_plan* plan, char* w, const BLayout& L, int b0, int nb, cudaStream_t st,
                              const char* fn, bool numeric = true) {
     const InstDesc* inst = (const InstDesc*)(w + L.inst) + b0;
     BatchCtl* ctl = (BatchCtl*)(w + L.ctl);
     long long* flops = (long long*)(w + L.flops);
     int* heavy = (int*)(w + L.heavy);
-    const long long g0 = plan->row_off[b0];
-    const long long g1 = plan->row_off[b0 + nb - 1] + plan->n[b0 + nb - 1];
     const long long c0 = plan->chunk_off[b0];
     const long long c1 = plan->chunk_off[b0 + nb - 1] + (plan->n[b0 + nb - 1] + 31) / 32;
     const int sms = sm_count();
     TS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(BatchCtl), st), fn);
-    TS_CUDA(launch_bat_prepare(inst, nb, g0, g1, flops, heavy, ctl, sms, st), fn);
+    TS_CUDA(launch_bat_prepare(inst, nb, c0, c1, flops, heavy, ctl, sms, st), fn);
     if (!numeric) return TS_OK;
     TS_CUDA(launch_bat_symbolic(inst, nb, c0, c1, 0, flops, heavy, ctl, plan->Wmax, sms, st), fn);
     TS_CUDA(launch_bat_scan(inst, nb, ctl, st), fn);
@@ -1485,7 +1483,8 @@ extern "C" ts_status ts_batched_check(ts_batched_plan* plan, void* ws, size_t ws
 
 // Per instance, every candidate (accumulator kind x heavy-row threshold) is
 // timed on that instance alone (its four forward launches over its rows
-// only) and the fastest kept in its descriptor.
+// only) and the fastest kept in its descriptor; then a few whole-batch
+// tunings built from those choices are timed and the fastest kept.
 extern "C" ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts_tuning* chosen, void* ws,
                                          size_t ws_bytes, void* stream) {
     const char* fn = "ts_batched_autotune";
@@ -1500,6 +1499,8 @@ extern "C" ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts
     TS_CUDA(cudaEventCreate(&e0), fn);
     TS_CUDA(cudaEventCreate(&e1), fn);
     const long long mins[] = {1024, 4096, 16384, 1LL << 50};
+    const std::vector<int> start_acc = plan->accum;
+    const std::vector<long long> start_min = plan->heavy_min;
     for (int b = 0; b < plan->count && s == TS_OK; ++b) {
         if (plan->n[b] == 0) continue;
         int best_acc = plan->accum[b];
@@ -1536,9 +1537,47 @@ extern "C" ts_status ts_batched_autotune(ts_batched_plan* plan, int32_t reps, ts
         plan->accum[b] = best_acc;
         plan->heavy_min[b] = best_min;
     }
+    // An instance timed alone favours a low heavy threshold (more blocks on
+    // a GPU it cannot fill); in the batch the GPU is full and the tail is
+    // short.  So the whole batch is timed under (a) every instance's own
+    // choice, (b) the tuning the autotuner started from and (c) the
+    // instances' own accumulators with one heavy threshold for all, and the
+    // fastest is kept.
+    struct Cand {
+        std::vector<int> acc;
+        std::vector<long long> hm;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({plan->accum, plan->heavy_min});
+    cands.push_back({start_acc, start_min});
+    for (long long hm : {1024LL, 4096LL, 16384LL})
+        cands.push_back({plan->accum, std::vector<long long>((size_t)plan->count, hm)});
+    size_t best = 0;
+    float best_ms = 1e30f;
+    for (size_t c = 0; c < cands.size() && s == TS_OK; ++c) {
+        plan->accum = cands[c].acc;
+        plan->heavy_min = cands[c].hm;
+        if ((s = upload_insts(plan, plan->bA.data(), plan->bB.data(), plan->bC.data(), w, L, st, fn)) != TS_OK) break;
+        float tot = 0.0f;
+        for (int r = 0; r <= reps && s == TS_OK; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+            if (s == TS_OK) s = bat_forward(plan, w, L, 0, plan->count, st, fn);
+            if (s == TS_OK && cudaEventRecord(e1, st) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+            if (s == TS_OK && cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), fn);
+            float ms = 0.0f;
+            if (s == TS_OK) cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) tot += ms;
+        }
+        if (s == TS_OK && tot / reps < best_ms) {
+            best_ms = tot / reps;
+            best = c;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != TS_OK) return s;
+    plan->accum = cands[best].acc;
+    plan->heavy_min = cands[best].hm;
     if ((s = upload_insts(plan, plan->bA.data(), plan->bB.data(), plan->bC.data(), w, L, st, fn)) != TS_OK) return s;
     // leave every C_b holding the product of the chosen tunings
     if ((s = bat_forward(plan, w, L, 0, plan->count, st, fn)) != TS_OK) return s;

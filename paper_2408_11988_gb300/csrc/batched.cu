@@ -61,85 +61,6 @@ __device__ __forceinline__ NumParams inst_params(const InstDesc& I) {
     return p;
 }
 
-// ---------------------------------------------------------------------------
-// prepare: four rows per warp, eight lanes per row (coalesced reads of the
-// row's entries)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bat_prepare(const InstDesc* __restrict__ inst, int count, long long g0,
-                                                     long long g1, long long* __restrict__ flops,
-                                                     int* __restrict__ heavy, BatchCtl* ctl) {
-    const int lane = lane_id(), gl = lane & 7, slot = lane >> 3;
-    bool bad_a = false, bad_b = false;
-    const long long step = ((long long)gridDim.x * blockDim.x >> 5) * 4;
-    for (long long base = g0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; base < g1;
-         base += step) {
-        const long long g = base + slot;
-        const bool act = g < g1;
-        const InstDesc& I = inst[act ? inst_of(inst, count, g) : 0];
-        const long long i = act ? g - I.row_off : 0;
-        // products of row i of A_b: eight lanes over its entries, summed
-        long long f = 0;
-        if (act) {
-            const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
-            for (long long e = a0 + gl; e < a1; e += 8) {
-                const int k = __ldg(I.A_col + e);
-                if ((unsigned)k < (unsigned)I.n) {
-                    const long long s = clampll(__ldg(I.B_rowptr + k), 0, I.bnnz);
-                    const long long t = clampll(__ldg(I.B_rowptr + k + 1), s, I.bnnz);
-                    f += t - s < I.d ? t - s : I.d;
-                } else {
-                    bad_a = true;
-                }
-            }
-        }
-        f += __shfl_xor_sync(FULL, f, 1);
-        f += __shfl_xor_sync(FULL, f, 2);
-        f += __shfl_xor_sync(FULL, f, 4);
-        if (act && gl == 0) {
-            flops[g] = f;
-            if (f > 0 && f >= I.heavy_min) heavy[atomicAdd(&ctl->nheavy, 1ull)] = (int)g;
-        }
-        // row i of B_b: its packed pairs (pads and bad columns as -1), and
-        // for a dense-B instance its dense row and pattern words
-        long long s = 0;
-        int len = 0;
-        unsigned q0 = 0;
-        if (act) padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, (int)i, s, len, q0);
-        const bool dense = act && I.accum == BAT_DENSE_B && I.Bd;
-        float* r = dense ? I.Bd + (size_t)i * I.Wd : nullptr;
-        unsigned* bw = dense ? I.Bbits + (size_t)i * (I.Wd >> 5) : nullptr;
-        if (dense) {  // cleared before the entries land
-            for (int c = 4 * gl; c < I.Wd; c += 32) *reinterpret_cast<float4*>(r + c) = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int x = gl; x < (I.Wd >> 5); x += 8) bw[x] = 0u;
-        }
-        __syncwarp();
-        if (act) {
-            int2* Q = reinterpret_cast<int2*>(I.Bq) + 2 * (size_t)q0;
-            const int span = (len + 1) & ~1;
-            for (int j = gl; j < span; j += 8) {
-                int2 v = make_int2(-1, 0);
-                if (j < len) {
-                    const int c = __ldg(I.B_col + s + j);
-                    if ((unsigned)c < (unsigned)I.d) {
-                        const float x = I.B_val ? __ldg(I.B_val + s + j) : 0.0f;
-                        v = make_int2(c, __float_as_int(x));
-                        if (dense) {
-                            r[c] = x;
-                            atomicOr(bw + (c >> 5), 1u << (c & 31));
-                        }
-                    } else {
-                        bad_b = true;
-                    }
-                }
-                Q[j] = v;
-            }
-        }
-        __syncwarp();
-    }
-    if (bad_a) atomicOr(&ctl->err, ERR_A_COL);
-    if (bad_b) atomicOr(&ctl->err, ERR_B_COL);
-}
-
 // Instance of 32-row chunk c (the last instance whose first chunk is <= c).
 __device__ __forceinline__ int inst_of_chunk(const InstDesc* __restrict__ inst, int count, long long c) {
     int lo = 0, hi = count - 1;
@@ -149,6 +70,178 @@ __device__ __forceinline__ int inst_of_chunk(const InstDesc* __restrict__ inst, 
         else hi = mid - 1;
     }
     return lo;
+}
+
+// This warp's next 32-row chunk from queue q: chunks are dealt c0, c0 + 1,
+// ... in order as warps ask for them (>= the caller's end when none is
+// left), so a warp that drew heavy chunks takes fewer of them.
+__device__ __forceinline__ long long bat_next_chunk(unsigned long long* q, long long c0) {
+    unsigned long long t = 0;
+    if (lane_id() == 0) t = atomicAdd(q, 1ull);
+    return c0 + (long long)__shfl_sync(FULL, t, 0);
+}
+
+// Products of row k of B for the flops (its length, at most d).
+__device__ __forceinline__ long long bat_brow_len(const InstDesc& I, int k) {
+    const long long s = clampll(__ldg(I.B_rowptr + k), 0, I.bnnz);
+    const long long e = clampll(__ldg(I.B_rowptr + k + 1), s, I.bnnz);
+    return e - s < I.d ? e - s : I.d;
+}
+
+// ---------------------------------------------------------------------------
+// prepare: one warp per 32-row chunk of one instance (chunks dealt from a
+// queue), lane l owning row i0 + l of A_b and of B_b.
+//  * flops: the entries of the chunk's rows of A with at most PREP_SHORT
+//    entries are numbered across the rows and read 32 at a time, four
+//    rounds in flight (coalesced); each entry's B row length goes to its row
+//    by a segmented sum over the lanes.  A longer row is then summed by the
+//    whole warp, eight loads per lane in flight.  Rows at or above their
+//    instance's threshold go on the heavy list.
+//  * the chunk's rows of B are copied into the row-aligned packed copy the
+//    same way (entries numbered across the rows, pads as column -1), and for
+//    a dense-B instance into its dense copy and pattern bits, cleared first.
+// ---------------------------------------------------------------------------
+constexpr int PREP_SHORT = 256;
+
+__global__ void __launch_bounds__(256) k_bat_prepare(const InstDesc* __restrict__ inst, int count, long long c0,
+                                                     long long c1, long long* __restrict__ flops,
+                                                     int* __restrict__ heavy, BatchCtl* ctl) {
+    __shared__ long long s_f[8][32];
+    const int lane = lane_id(), warp = warp_id();
+    long long* wf = s_f[warp];
+    wf[lane] = 0;
+    __syncwarp();
+    bool bad_a = false, bad_b = false;
+    for (long long c = bat_next_chunk(&ctl->l_prep, c0); c < c1; c = bat_next_chunk(&ctl->l_prep, c0)) {
+        const InstDesc& I = inst[inst_of_chunk(inst, count, c)];
+        const long long i0 = (c - I.chunk_off) * 32;
+        const long long i = i0 + lane;
+        const bool act = i < I.n;
+        long long a0 = 0, a1 = 0;
+        if (act) {
+            a0 = clampll(__ldg(I.A_rowptr + i), 0, I.annz);
+            a1 = clampll(__ldg(I.A_rowptr + i + 1), a0, I.annz);
+        }
+        // short rows, numbered across the chunk
+        const int slen = a1 - a0 <= PREP_SHORT ? (int)(a1 - a0) : 0;
+        const int incl = warp_incl_scan(slen), excl = incl - slen;
+        const int total = __shfl_sync(FULL, incl, 31);
+        const long long shift = a0 - excl;  // entry of number p in row q: shift(q) + p
+        for (int p0 = 0; p0 < total; p0 += 128) {
+            int q[4], k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + 32 * u + lane;
+                q[u] = owner_lane(excl, p);
+                const long long e = shfl64(shift, q[u]) + p;
+                k[u] = p < total ? __ldg(I.A_col + e) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + 32 * u + lane;
+                long long v = 0;
+                if (p < total) {
+                    if ((unsigned)k[u] < (unsigned)I.n) v = bat_brow_len(I, k[u]);
+                    else bad_a = true;
+                }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {  // sum over this lane's run of equal q, from this lane on
+                    const long long t = shfl64_down(v, o);
+                    const int qo = __shfl_down_sync(FULL, q[u], o);
+                    if (lane + o < 32 && qo == q[u]) v += t;
+                }
+                const int qp = __shfl_up_sync(FULL, q[u], 1);
+                if (p < total && (lane == 0 || qp != q[u])) wf[q[u]] += v;  // one lane per row and round
+                __syncwarp();
+            }
+        }
+        long long f = wf[lane];
+        wf[lane] = 0;
+        // long rows, one at a time by the whole warp
+        unsigned longs = __ballot_sync(FULL, a1 - a0 > PREP_SHORT);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const long long la0 = shfl64(a0, src), la1 = shfl64(a1, src);
+            long long sum = 0;
+            for (long long e = la0 + lane; e < la1; e += 256) {
+                int k[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) k[u] = e + 32 * u < la1 ? __ldg(I.A_col + e + 32 * u) : 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (e + 32 * u < la1) {
+                        if ((unsigned)k[u] < (unsigned)I.n) sum += bat_brow_len(I, k[u]);
+                        else bad_a = true;
+                    }
+                }
+            }
+            sum = warp_sum(sum);
+            if (lane == src) f = sum;
+        }
+        if (act) {
+            flops[I.row_off + i] = f;
+            if (f > 0 && f >= I.heavy_min) heavy[atomicAdd(&ctl->nheavy, 1ull)] = (int)(I.row_off + i);
+        }
+        // the chunk's rows of B into the copies
+        long long bs = 0;
+        int blen = 0;
+        unsigned g0 = 0;
+        if (act) padded_row<2>(I.B_rowptr, I.bnnz, (int)I.d, (int)i, bs, blen, g0);
+        const bool dense = I.accum == BAT_DENSE_B && I.Bd;
+        if (dense) {  // cleared before the entries land
+            const long long nr = I.n - i0 < 32 ? I.n - i0 : 32;
+            float4* r4 = reinterpret_cast<float4*>(I.Bd + (size_t)i0 * I.Wd);
+            for (long long x = lane; x < nr * (I.Wd >> 2); x += 32) r4[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned* bw = I.Bbits + (size_t)i0 * (I.Wd >> 5);
+            for (long long x = lane; x < nr * (I.Wd >> 5); x += 32) bw[x] = 0u;
+            __syncwarp();
+        }
+        const int span = (blen + 1) & ~1;
+        const int bincl = warp_incl_scan(span), bexcl = bincl - span;
+        const int btotal = __shfl_sync(FULL, bincl, 31);
+        int2* Q = reinterpret_cast<int2*>(I.Bq);
+        for (int p0 = 0; p0 < btotal; p0 += 128) {
+            int q[4], j[4], cc[4];
+            unsigned gq[4];
+            bool ent[4];
+            float xx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + 32 * u + lane;
+                q[u] = owner_lane(bexcl, p);
+                j[u] = p - __shfl_sync(FULL, bexcl, q[u]);
+                gq[u] = __shfl_sync(FULL, g0, q[u]);
+                const long long sq = shfl64(bs, q[u]);
+                const int lq = __shfl_sync(FULL, blen, q[u]);
+                ent[u] = p < btotal && j[u] < lq;  // an entry of B (else a pad)
+                cc[u] = ent[u] ? __ldg(I.B_col + sq + j[u]) : -1;
+                xx[u] = ent[u] && I.B_val ? __ldg(I.B_val + sq + j[u]) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + 32 * u + lane;
+                if (p >= btotal) continue;
+                int2 v = make_int2(-1, 0);  // pad
+                const int c = cc[u];
+                if (ent[u]) {
+                    if ((unsigned)c < (unsigned)I.d) {
+                        v = make_int2(c, __float_as_int(xx[u]));
+                        if (dense) {
+                            const long long row = i0 + q[u];
+                            I.Bd[(size_t)row * I.Wd + c] = xx[u];
+                            atomicOr(I.Bbits + (size_t)row * (I.Wd >> 5) + (c >> 5), 1u << (c & 31));
+                        }
+                    } else {
+                        bad_b = true;
+                    }
+                }
+                Q[2 * (size_t)gq[u] + j[u]] = v;
+            }
+        }
+    }
+    if (bad_a) atomicOr(&ctl->err, ERR_A_COL);
+    if (bad_b) atomicOr(&ctl->err, ERR_B_COL);
 }
 
 // Ascending bitonic sort of one key per lane across the warp, carrying val.
@@ -194,15 +287,6 @@ __device__ __forceinline__ bool bat_light(const InstDesc* inst, int count, const
     if (f <= 0) return false;
     b = inst_of(inst, count, g);
     return f < __ldg(&inst[b].heavy_min);
-}
-
-// This warp's next 32-row chunk from queue q: chunks are dealt c0, c0 + 1,
-// ... in order as warps ask for them (>= the caller's end when none is
-// left), so a warp that drew heavy chunks takes fewer of them.
-__device__ __forceinline__ long long bat_next_chunk(unsigned long long* q, long long c0) {
-    unsigned long long t = 0;
-    if (lane_id() == 0) t = atomicAdd(q, 1ull);
-    return c0 + (long long)__shfl_sync(FULL, t, 0);
 }
 
 // Byte marks (symbolic light rows): column c of the slot's row is reached.
@@ -823,22 +907,13 @@ __global__ void __launch_bounds__(256) k_batch_bounds(const InstDesc* __restrict
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static unsigned row_grid(long long rows, int sms) {
-    long long g = (rows + 255) / 256;
-    if (g < 1) g = 1;
-    if (g > (long long)sms * 8) g = (long long)sms * 8;
-    return (unsigned)g;
-}
-
-cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
+cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long c0, long long c1, long long* flops,
                                int* heavy, BatchCtl* ctl, int sms, cudaStream_t st) {
-    if (g1 <= g0) return cudaSuccess;
-    // no more blocks than stay resident: the blocks share the rows evenly,
-    // so a second wave would double the time of its blocks' shares
-    const unsigned rg = row_grid(8 * (g1 - g0), sms);
-    const unsigned pg = (unsigned)persistent_grid((const void*)k_bat_prepare, 256, 0, sms);
+    if (c1 <= c0) return cudaSuccess;
+    long long grid = persistent_grid((const void*)k_bat_prepare, 256, 0, sms);
+    if (grid > (c1 - c0 + 7) / 8) grid = (c1 - c0 + 7) / 8;
     count_launch();
-    k_bat_prepare<<<rg < pg ? rg : pg, 256, 0, st>>>(inst, count, g0, g1, flops, heavy, ctl);
+    k_bat_prepare<<<(unsigned)grid, 256, 0, st>>>(inst, count, c0, c1, flops, heavy, ctl);
     return cudaGetLastError();
 }
 

@@ -197,10 +197,11 @@ struct InstDesc {
 // (l_*), and the error flags.  The forward zeroes all of it, the backward
 // q_bwd and l_bwd.
 struct BatchCtl {
-    unsigned long long nheavy, q_sym, q_num, q_bwd, l_bwd, l_sym, l_num, err;
+    unsigned long long nheavy, q_sym, q_num, q_bwd, l_bwd, l_sym, l_num, l_prep, err;
 };
-// Rows [g0, g1) of the batch's numbering over the instances inst[0..count).
-cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long g0, long long g1, long long* flops,
+// 32-row chunks [c0, c1) of the batch's chunk numbering over the instances
+// inst[0..count) (every chunk lies in one instance).
+cudaError_t launch_bat_prepare(const InstDesc* inst, int count, long long c0, long long c1, long long* flops,
                                int* heavy, BatchCtl* ctl, int sms, cudaStream_t st);
 // symbolic / numeric: 32-row chunks [c0, c1) of the batch's chunk numbering
 // (every chunk lies in one instance); `values` = plus-times
