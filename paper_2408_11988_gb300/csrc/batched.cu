@@ -305,14 +305,14 @@ struct AddByte {
 __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict__ inst, int count, long long c0,
                                                       long long c1, const long long* __restrict__ flops,
                                                       const int* __restrict__ heavy, BatchCtl* ctl, int Wmax) {
-    __shared__ unsigned s_bm[9][33];  // the block's bitmap (heavy rows) in s_bm[8]
+    __shared__ __align__(16) unsigned char s_hb[1024];  // the block's byte marks (heavy rows)
     // four slots of byte marks per warp (light rows), Wmax + 32 bytes each
     // (the pad puts the slots' words on different banks)
     extern __shared__ __align__(16) unsigned char s_marks[];
     __shared__ long long s_item;
     const int nwarps = blockDim.x >> 5, warp = warp_id(), lane = lane_id(), tid = threadIdx.x;
     const int mstride = Wmax + 32;
-    for (int x = tid; x < 9 * 33; x += blockDim.x) (&s_bm[0][0])[x] = 0u;
+    for (int x = tid; x < 1024 / 4; x += blockDim.x) reinterpret_cast<unsigned*>(s_hb)[x] = 0u;
     for (int x = tid; x < nwarps * 4 * mstride / 4; x += blockDim.x) reinterpret_cast<unsigned*>(s_marks)[x] = 0u;
     __syncthreads();
     unsigned long long* err = &ctl->err;
@@ -328,22 +328,27 @@ __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict
         const long long i = g - I.row_off;
         const NumParams p = inst_params(I);
         const long long a0 = clampll(I.A_rowptr[i], 0, I.annz), a1 = clampll(I.A_rowptr[i + 1], a0, I.annz);
-        // chunk by chunk, stopping once the row's bitmap holds all d columns
-        // (its count is then d whatever products remain)
-        const int nwd = I.W >> 5;
-        const unsigned last = (I.d & 31) ? (1u << (I.d & 31)) - 1u : 0xFFFFFFFFu;
-        for (long long e = a0 + 32LL * warp; e < a1; e += 32LL * nwarps) {
-            wide_range(p, AddMark{s_bm[8]}, e, e + 32 < a1 ? e + 32 : a1, 32, err);
-            __syncwarp();
-            const unsigned want = lane < nwd - 1 ? 0xFFFFFFFFu : (lane == nwd - 1 ? last : 0u);
-            if (__all_sync(FULL, lane >= nwd || (s_bm[8][lane] & want) == want)) break;
-        }
+        // the warps take the row's chunks in turn, each stopping once the
+        // marks hold all d columns (the count is then d whatever products
+        // remain); a warp reads marks other warps may still be storing, which
+        // can only delay its stop
+        const int nw4 = I.W >> 2;  // words of marks
+        const long long d = I.d;
+        auto full = [&]() {
+            int cnt = 0;
+            for (int x = lane; x < nw4; x += 32) cnt += __popc(reinterpret_cast<const volatile unsigned*>(s_hb)[x]);
+            return warp_sum(cnt) >= d;
+        };
+        wide_range(p, AddByte{s_hb}, a0 + 32LL * warp, a1, 32LL * nwarps, err, full);
         __syncthreads();
         if (warp == 0) {
-            const int nw = I.W >> 5;
-            const int c = warp_sum(lane < nw ? __popc(s_bm[8][lane]) : 0);
-            if (lane == 0) I.C_rowptr[i + 1] = c;
-            if (lane < nw) s_bm[8][lane] = 0u;
+            int cnt = 0;
+            for (int x = lane; x < nw4; x += 32) {  // bytes are 0 or 1
+                cnt += __popc(reinterpret_cast<unsigned*>(s_hb)[x]);
+                reinterpret_cast<unsigned*>(s_hb)[x] = 0u;
+            }
+            cnt = warp_sum(cnt);
+            if (lane == 0) I.C_rowptr[i + 1] = cnt;
         }
         __syncthreads();
     }

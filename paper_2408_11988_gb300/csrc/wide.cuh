@@ -206,13 +206,19 @@ __device__ __forceinline__ void wide_seg(const NumParams& p, int k, unsigned& g0
     else atomicOr(err, ERR_A_COL);
 }
 
+// The default stop test of wide_range: walk every chunk.
+struct NeverFull {
+    __device__ __forceinline__ bool operator()() const { return false; }
+};
+
 // Chunks first, first + stride, ... (< e1) of 32 entries of A walked by
 // one warp into the shared accumulator, in three stages: while chunk c is
 // walked, the row pointers of B for chunk c + 1 and the entries of A of
-// chunk c + 2 are in flight.
-template <class Add>
+// chunk c + 2 are in flight.  After each chunk the warp-uniform test full()
+// may end the walk (a symbolic row whose marks hold every column).
+template <class Add, class Full = NeverFull>
 __device__ __forceinline__ void wide_range(const NumParams& p, const Add& add, long long first, long long e1,
-                                           long long stride, unsigned long long* err) {
+                                           long long stride, unsigned long long* err, const Full& full = Full()) {
     const int lane = lane_id();
     const unsigned W = (unsigned)p.W;
     int k;
@@ -232,6 +238,7 @@ __device__ __forceinline__ void wide_range(const NumParams& p, const Add& add, l
         const long long e2 = e + 2 * stride;
         wide_load_a(p, e2 + lane, e2 + lane < e1, k, a);  // chunk c + 2
         wide_chunk_walk(p.Bq, add, W, g0, np, ca, nv);
+        if (full()) break;
         g0 = g1;
         np = np1;
         ca = ca1;
