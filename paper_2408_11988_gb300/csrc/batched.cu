@@ -277,6 +277,30 @@ __device__ __forceinline__ int chunk_light_sorted(const InstDesc& I, const long 
     return __popc(__ballot_sync(FULL, light));
 }
 
+// This slot's row of the group at sorted position t of a chunk (eight
+// lanes per slot, four slots; i = -1 past the chunk's L light rows): its
+// first entry of A and length, and with want_out its range in C_b.
+struct BatRow {
+    long long i, a0, out, out_end;
+    int len;
+};
+
+__device__ __forceinline__ BatRow bat_row(const InstDesc& I, long long i0, int srt, int L, int t, bool want_out) {
+    const int pos = t + (lane_id() >> 3);
+    const int r = __shfl_sync(FULL, srt, pos & 31);
+    BatRow b{-1, 0, 0, 0, 0};
+    if (pos < L) {
+        b.i = i0 + r;
+        b.a0 = clampll(__ldg(I.A_rowptr + b.i), 0, I.annz);
+        b.len = (int)(clampll(__ldg(I.A_rowptr + b.i + 1), b.a0, I.annz) - b.a0);
+        if (want_out) {
+            b.out = clampll(__ldg(I.C_rowptr + b.i), 0, I.cap);
+            b.out_end = clampll(__ldg(I.C_rowptr + b.i + 1), b.out, I.cap);
+        }
+    }
+    return b;
+}
+
 // Whether global row g (lane's row of a 32-row chunk) is a light row: it
 // has products and fewer than its instance's threshold.
 __device__ __forceinline__ bool bat_light(const InstDesc* inst, int count, const long long* flops, long long g,
@@ -367,23 +391,19 @@ __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict
         const int L = chunk_light_sorted(I, flops, i0, srt);
         const NumParams p = inst_params(I);
         const int nw = I.W >> 5;
+        // pipelined over the chunk's groups: the next group's row bounds load
+        // before this group's walk, its first entries of A before the count
+        BatRow cur = bat_row(I, i0, srt, L, 0, false);
+        int k0, k1;
+        float x0, x1;
+        rg_load_a(p, cur.a0 + lanes, lanes < cur.len, k0, x0);
+        rg_load_a(p, cur.a0 + 8 + lanes, 8 + lanes < cur.len, k1, x1);
         for (int t = 0; t < L; t += 4) {
-            const int pos = t + slot;
-            const int r = __shfl_sync(FULL, srt, pos & 31);
-            const bool active = pos < L;
-            const long long i = i0 + r;
-            long long a0 = 0;
-            int len = 0;
-            if (active) {
-                a0 = clampll(I.A_rowptr[i], 0, I.annz);
-                len = (int)(clampll(I.A_rowptr[i + 1], a0, I.annz) - a0);
-            }
-            const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
-            int k0, k1;
-            float x0, x1;
-            rg_load_a(p, a0 + lanes, lanes < len, k0, x0);
-            rg_load_a(p, a0 + 8 + lanes, 8 + lanes < len, k1, x1);
-            rgp_tile<8, 2>(p, I.Bq, AddByte{mym}, a0, len, lmax, err, k0, x0, k1, x1);
+            const BatRow nxt = bat_row(I, i0, srt, L, t + 4, false);
+            const int lmax = (int)__reduce_max_sync(FULL, (unsigned)cur.len);
+            rgp_tile<8, 2>(p, I.Bq, AddByte{mym}, cur.a0, cur.len, lmax, err, k0, x0, k1, x1);
+            rg_load_a(p, nxt.a0 + lanes, lanes < nxt.len, k0, x0);
+            rg_load_a(p, nxt.a0 + 8 + lanes, 8 + lanes < nxt.len, k1, x1);
             __syncwarp();
             int cnt = 0;
             unsigned* mw = reinterpret_cast<unsigned*>(mym);
@@ -394,8 +414,9 @@ __global__ void __launch_bounds__(256) k_bat_symbolic(const InstDesc* __restrict
             cnt += __shfl_xor_sync(FULL, cnt, 1);
             cnt += __shfl_xor_sync(FULL, cnt, 2);
             cnt += __shfl_xor_sync(FULL, cnt, 4);
-            if (active && lanes == 0) I.C_rowptr[i + 1] = cnt;
+            if (cur.i >= 0 && lanes == 0) I.C_rowptr[cur.i + 1] = cnt;
             __syncwarp();
+            cur = nxt;
         }
     }
 }
@@ -619,28 +640,18 @@ __global__ void __launch_bounds__(256, 3) k_bat_numeric(const InstDesc* __restri
             const int Wi = I.W;
             float* myacc = wacc + (size_t)slot * (Wi + 8);
             for (int t = 0; t < L; t += 4) {
-                const int pos = t + slot;
-                const int r = __shfl_sync(FULL, srt, pos & 31);
-                const bool active = pos < L;
-                const long long i = i0 + r;
-                long long a0 = 0, out = 0, out_end = 0;
-                int len = 0;
-                if (active) {
-                    a0 = clampll(I.A_rowptr[i], 0, I.annz);
-                    len = (int)(clampll(I.A_rowptr[i + 1], a0, I.annz) - a0);
-                    out = clampll(I.C_rowptr[i], 0, I.cap);
-                    out_end = clampll(I.C_rowptr[i + 1], out, I.cap);
-                }
-                const int lmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+                const BatRow cur = bat_row(I, i0, srt, L, t, true);
+                const int lmax = (int)__reduce_max_sync(FULL, (unsigned)cur.len);
                 int k0, k1;
                 float x0, x1;
-                rg_load_a(p, a0 + lanes, lanes < len, k0, x0);
-                rg_load_a(p, a0 + 8 + lanes, 8 + lanes < len, k1, x1);
-                rgp_tile<8, 2>(p, I.Bq, AddPlain{myacc}, a0, len, lmax, err, k0, x0, k1, x1);
-                rg_emit<8>(wacc, Wi, 0, out, out_end, I.C_col, I.C_val, err);
+                rg_load_a(p, cur.a0 + lanes, lanes < cur.len, k0, x0);
+                rg_load_a(p, cur.a0 + 8 + lanes, 8 + lanes < cur.len, k1, x1);
+                rgp_tile<8, 2>(p, I.Bq, AddPlain{myacc}, cur.a0, cur.len, lmax, err, k0, x0, k1, x1);
+                long long out = cur.out;
+                rg_emit<8>(wacc, Wi, 0, out, cur.out_end, I.C_col, I.C_val, err);
                 // the spare column (pads) back to empty, for the next rows
                 if (lanes == 0) myacc[Wi] = __uint_as_float(RG_EMPTY);
-                if (active && lanes == 0 && out != out_end) atomicOr(err, ERR_C_ROW);
+                if (cur.i >= 0 && lanes == 0 && out != cur.out_end) atomicOr(err, ERR_C_ROW);
                 __syncwarp();
             }
             continue;
