@@ -227,8 +227,13 @@ TS_API ts_status ts_spgemm_symbolic(ts_plan* plan, const ts_csr_desc* A, const t
 /*
  * Numeric pass (Eq. 1 with values): fills C->col (and C->val for plus-times)
  * for the C->rowptr of the preceding symbolic call on this plan and ws.
- * C->nnz must equal the symbolic total.  Plus-times sums in float32 in an
- * unspecified order; columns are ascending per row.  Does not synchronise.
+ * C->nnz is the room in C->col / C->val: the symbolic total, or any capacity
+ * at least that large (a symbolic call without nnzC_host followed by this
+ * call then runs with no host synchronisation at all, so both can be
+ * captured in a CUDA graph; nnz(C) is C->rowptr[n]).  Entries past the
+ * capacity are not written and are reported as a C row error.  Plus-times
+ * sums in float32 in an unspecified order; columns are ascending per row.
+ * Does not synchronise.
  * Errors: INVALID_ARG, STATE (no symbolic pass on this plan/ws before),
  * WORKSPACE_TOO_SMALL, CUDA; device-side checks as described at the top.
  */

@@ -153,6 +153,34 @@ class Plan:
         C = self.alloc_c(rowptr, nnz)
         return self.numeric(A, B, C, stream=stream)
 
+    def forward_into(self, A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=None) -> DeviceCSR:
+        """Symbolic + numeric into preallocated C (C.col / C.val hold
+        C.nnz >= nnz(C) entries) with no host synchronisation: nnz(C) ends up
+        in C.rowptr[n].  Capturable in a CUDA graph."""
+        ws = self.workspace(A.rowptr.device)
+        dA, dB = A.desc(), B.desc()
+        N.call("ts_spgemm_symbolic", self._h, ctypes.byref(dA), ctypes.byref(dB), _ptr(C.rowptr), None,
+               _ptr(ws), ws.numel(), _stream(stream))
+        return self.numeric(A, B, C, stream=stream)
+
+    def capture_forward(self, A: DeviceCSR, B: DeviceCSR, capacity: Optional[int] = None):
+        """A CUDA graph of forward_into (for small products, where launches
+        and the host synchronisation dominate).  C is sized by one eager
+        forward (or `capacity`); returns (graph, C).  Replaying recomputes C
+        from the current values of A and B; their patterns may change only
+        while nnz(C) stays within C's capacity (else plan.check() raises)."""
+        if capacity is None:
+            capacity = self.forward(A, B).nnz
+        rowptr = torch.empty(self.n + 1, dtype=torch.int64, device=A.rowptr.device)
+        C = self.alloc_c(rowptr, capacity)
+        self.workspace(A.rowptr.device)
+        self.forward_into(A, B, C)  # warm-up outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.forward_into(A, B, C, stream=torch.cuda.current_stream())
+        return g, C
+
     def backward(self, A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, dC_val: torch.Tensor,
                  want_dA: bool = True, want_dB: bool = True, out_dA=None, out_dB=None, stream=None):
         ws = self.workspace(A.rowptr.device)

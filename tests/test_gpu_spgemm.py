@@ -513,3 +513,50 @@ def test_dense_b_split_hub_and_boolean():
     compare_full(spgemm(Ad, Bd, tuning={"accum": ACC_DENSE_B}), A, B)
     C = spgemm(Ad.pattern(), Bd.pattern(), semiring=OR_SELECT2ND, tuning={"accum": ACC_DENSE_B})
     compare_full(C, A, B, semiring=oracle.OR_SELECT2ND)
+
+
+@pytest.mark.parametrize("tuning", [None, {"accum": ACC_HASH}, {"row_lanes": 1}, {"cta_min_flops": 1}])
+def test_capture_forward_replays(er_case, tuning):
+    # symbolic + numeric captured once in a CUDA graph (no host synchronisation
+    # inside), replayed: C from scratch each time, and new values of B picked
+    # up by a replay with the same pattern
+    A, B = er_case
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd, tuning=tuning)
+    g, C = plan.capture_forward(Ad, Bd)
+    C.rowptr.fill_(0)
+    C.col.fill_(-1)
+    C.val.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    compare_full(C, A, B)
+    Bd.val.mul_(2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    compare_full(C, A, CSR(B.nrows, B.ncols, B.rowptr, B.col, (B.val * np.float32(2.0)).astype(np.float32)))
+
+
+def test_capture_forward_capacity_overflow(er_case):
+    # a C too small for the product: nothing is written past its capacity and
+    # the check reports the rows that did not fit
+    A, B = er_case
+    Ad, Bd = dev(A), dev(B)
+    plan = Plan(Ad, Bd)
+    nnz = plan.forward(Ad, Bd).nnz
+    guard = 64
+    g, C = plan.capture_forward(Ad, Bd, capacity=nnz - 7)
+    # the graph writes through C.col / C.val; a longer buffer behind them
+    # shows that nothing lands past the capacity
+    big_col = torch.full((nnz - 7 + guard,), -5, dtype=torch.int32, device="cuda")
+    big_val = torch.full((nnz - 7 + guard,), 3.0, dtype=torch.float32, device="cuda")
+    C2 = DeviceCSR(C.nrows, C.ncols, C.rowptr, big_col[: nnz - 7], big_val[: nnz - 7])
+    plan.forward_into(Ad, Bd, C2)
+    with pytest.raises(TSError):
+        plan.check()
+    assert int(C2.rowptr[-1].item()) == nnz
+    assert bool((big_col[nnz - 7:] == -5).all()) and bool((big_val[nnz - 7:] == 3.0).all())
+    g.replay()
+    with pytest.raises(TSError):
+        plan.check()
