@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtsspgemm.so")
 
-SOURCES = ["api.cpp", "spgemm.cu", "numeric.cu", "numeric_copies.cu", "numeric_denseb.cu", "hash.cu", "backward.cu", "backward_t.cu", "msbfs.cu", "batched.cu", "validate.cu", "noalloc.cu", "force2vec.cu"]
+SOURCES = ["api.cpp", "spgemm.cu", "numeric.cu", "numeric_copies.cu", "numeric_denseb.cu", "numeric_tiny.cu", "hash.cu", "backward.cu", "backward_t.cu", "msbfs.cu", "batched.cu", "validate.cu", "noalloc.cu", "force2vec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE]

@@ -127,6 +127,9 @@ size_t numeric_rgcta_smem(int W, int warps, int row_lanes);
 // Dynamic shared memory of the wide kernel (row_lanes = 1: one accumulator
 // of W <= 1024 floats and its occupancy bitmap per warp).
 size_t numeric_wide_smem(int W, int warps);
+struct NumParams;
+// Rows with 1 .. TINY_MAX products of the wide pass (numeric_tiny.cu).
+cudaError_t launch_numeric_tiny(const NumParams& p, int sms, cudaStream_t st);
 size_t numeric_hash_smem(int slots, int warps, bool values);
 
 // Numeric pass with B expanded dense (plus-times, d <= 256): dense_ws holds

@@ -702,7 +702,10 @@ struct LightRows {
     long long base;
     unsigned mask;
     long long f_next;  // this lane's row of chunk `chunk + step`
-    __device__ __forceinline__ static bool light(long long f, int cc) { return f > 0 && flops_class(f) < cc; }
+    // light and not left to the tiny-row kernel (tiny = 0: none is)
+    __device__ __forceinline__ static bool light(long long f, int cc, int tiny) {
+        return f > tiny && f > 0 && flops_class(f) < cc;
+    }
     __device__ __forceinline__ static long long flops_of(const NumParams& p, long long c, long long nchunks) {
         const long long row = c * 32 + lane_id();
         return (c < nchunks && row < p.nB) ? __ldg(p.s.flops + row) : 0;
@@ -712,7 +715,7 @@ struct LightRows {
         nchunks = ((long long)p.nB + 31) / 32;
         chunk = c0;
         base = c0 * 32;
-        mask = __ballot_sync(FULL, light(flops_of(p, c0, nchunks), cc));
+        mask = __ballot_sync(FULL, light(flops_of(p, c0, nchunks), cc, p.tiny_max));
         f_next = flops_of(p, c0 + st, nchunks);
     }
     // next light row of this warp, -1 when none is left (warp-uniform)
@@ -721,7 +724,7 @@ struct LightRows {
             if (chunk >= nchunks) return -1;
             chunk += step;
             base = chunk * 32;
-            mask = __ballot_sync(FULL, light(f_next, cc));
+            mask = __ballot_sync(FULL, light(f_next, cc, p.tiny_max));
             f_next = flops_of(p, chunk + step, nchunks);
         }
         const int b = __ffs(mask) - 1;
@@ -1058,11 +1061,14 @@ static cudaError_t launch_rgcta(const NumParams& p, int warps, int sms, cudaStre
     return cudaGetLastError();
 }
 
-static cudaError_t launch_wide(const NumParams& p, int warps, int sms, cudaStream_t st) {
+static cudaError_t launch_wide(NumParams p, int warps, int sms, cudaStream_t st) {
     const void* k = (const void*)k_numeric_wide;
     const size_t smem = numeric_wide_smem(p.W, warps);
     cudaError_t e;
     if (p.W > 1024 || p.T != 1 || !p.Bq || smem > 220 * 1024) return cudaErrorInvalidValue;
+    // rows with at most TINY_MAX products first, in registers
+    if ((e = launch_numeric_tiny(p, sms, st))) return e;
+    p.tiny_max = TINY_MAX;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;

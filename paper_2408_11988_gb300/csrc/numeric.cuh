@@ -36,7 +36,12 @@ struct NumParams {
     Sched s;
     long long item_cap;
     int skip_light;  // 1: split and heavy rows only (light rows run in a kernel of their own)
+    int tiny_max;    // wide kernel: light rows with at most this many products run in k_numeric_tiny
 };
+
+// Rows with at most this many products go to the tiny-row kernel on the
+// wide path (one product per lane).
+constexpr int TINY_MAX = 32;
 
 inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                 const long long* tp, const int2* Bpk, const Sched& s, const LaunchCfg& cfg,
@@ -67,6 +72,7 @@ inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, i
     p.s = s;
     p.item_cap = split_item_capacity(A.nnz);
     p.skip_light = 0;
+    p.tiny_max = 0;
     return p;
 }
 
