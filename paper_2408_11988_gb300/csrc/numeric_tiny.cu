@@ -65,80 +65,86 @@ __device__ __forceinline__ void tiny_emit(const NumParams& p, int key, float val
     if (lane == 0 && out + __popc(hb) != out_end) atomicOr(err, ERR_C_ROW);
 }
 
-// Entry e of A (warp-uniform): its row of B in the row-aligned copy (first
-// pair g0, entries len; none for a bad column) and value a.
-__device__ __forceinline__ void tiny_entry(const NumParams& p, long long e, unsigned& g0, int& len, float& a,
-                                           unsigned long long* err) {
-    const int k = __ldg(p.Ai + e);
-    a = p.Ax ? __ldg(p.Ax + e) : 1.0f;
-    g0 = 0;
-    len = 0;
-    long long s;
-    if ((unsigned)k < (unsigned)p.nB) padded_row<2>(p.Bp, p.nnzB, p.d, k, s, len, g0);
-    else if (lane_id() == 0) atomicOr(err, ERR_A_COL);
-}
+// Row [a0, a1) of A with at most 32 products.  Rows of up to TINY_ENT
+// entries arrive with their rows of B described (first pair g[u], entries
+// n[u], value x[u], loaded for the whole chunk at once), so only the rows of
+// B themselves remain to be read.  One entry: its row of B, scaled, is the
+// row of C (already sorted, no duplicates).  Two entries: the two sorted
+// rows of B side by side, the second reversed at the top lanes, form a
+// bitonic sequence that five merge steps sort.  More: the products placed
+// one per lane and sorted by the full network.
+constexpr int TINY_ENT = 3;
 
-// Row [a0, a1) of A with at most 32 products.  One entry: its row of B,
-// scaled, is the row of C (already sorted, no duplicates).  Two entries:
-// the two sorted rows of B side by side, the second reversed at the top
-// lanes, form a bitonic sequence that five merge steps sort.  More: the
-// products expanded one per lane and sorted by the full network.
 __device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restrict__ Q, long long a0, long long a1,
-                                         long long out, long long out_end, unsigned long long* err) {
+                                         long long out, long long out_end, const unsigned (&g)[TINY_ENT],
+                                         const int (&n)[TINY_ENT], const float (&x)[TINY_ENT],
+                                         unsigned long long* err) {
     const int lane = lane_id();
     const unsigned W = (unsigned)p.W;
     int key = 0x7FFFFFFF;  // no product: sorts last
     float val = 0.0f;
-    if (a1 - a0 == 1) {
-        unsigned g0;
-        int len;
-        float a;
-        tiny_entry(p, a0, g0, len, a, err);
-        if (lane < len) {
-            const int2 v = __ldg(Q + 2 * (size_t)g0 + lane);
+    const long long na = a1 - a0;
+    if (na == 1) {
+        if (lane < n[0]) {
+            const int2 v = __ldg(Q + 2 * (size_t)g[0] + lane);
             if ((unsigned)v.x < W) {  // a bad column (-1) adds nothing
                 key = v.x;
-                val = a * __int_as_float(v.y);
+                val = x[0] * __int_as_float(v.y);
             }
         }
         tiny_emit(p, key, val, false, 1, out, out_end, err);
         return;
     }
-    if (a1 - a0 == 2) {
-        unsigned g0, g1;
-        int n0, n1;
-        float x0, x1;
-        tiny_entry(p, a0, g0, n0, x0, err);
-        tiny_entry(p, a0 + 1, g1, n1, x1, err);
-        if (n0 + n1 <= 32) {
-            const int j1 = 31 - lane;  // the second row, reversed, at the top lanes
-            int2 v = make_int2(-1, 0);
-            float a = 0.0f;
-            if (lane < n0) {
-                v = __ldg(Q + 2 * (size_t)g0 + lane);
-                a = x0;
-            } else if (j1 < n1) {
-                v = __ldg(Q + 2 * (size_t)g1 + j1);
-                a = x1;
-            }
-            if ((unsigned)v.x < W) {
-                key = v.x;
-                val = a * __int_as_float(v.y);
-            }
-            // bitonic merge: ascending (first row), empty lanes, descending (second row)
-#pragma unroll
-            for (int j = 16; j > 0; j >>= 1) {
-                const int pk = __shfl_xor_sync(FULL, key, j);
-                const float pv = __shfl_xor_sync(FULL, val, j);
-                if (((lane & j) == 0) ? pk < key : pk > key) {
-                    key = pk;
-                    val = pv;
-                }
-            }
-            tiny_emit(p, key, val, true, 2, out, out_end, err);
-            return;
+    if (na == 2 && n[0] + n[1] <= 32) {
+        const int j1 = 31 - lane;  // the second row, reversed, at the top lanes
+        int2 v = make_int2(-1, 0);
+        float a = 0.0f;
+        if (lane < n[0]) {
+            v = __ldg(Q + 2 * (size_t)g[0] + lane);
+            a = x[0];
+        } else if (j1 < n[1]) {
+            v = __ldg(Q + 2 * (size_t)g[1] + j1);
+            a = x[1];
         }
+        if ((unsigned)v.x < W) {
+            key = v.x;
+            val = a * __int_as_float(v.y);
+        }
+        // bitonic merge: ascending (first row), empty lanes, descending (second row)
+#pragma unroll
+        for (int j = 16; j > 0; j >>= 1) {
+            const int pk = __shfl_xor_sync(FULL, key, j);
+            const float pv = __shfl_xor_sync(FULL, val, j);
+            if (((lane & j) == 0) ? pk < key : pk > key) {
+                key = pk;
+                val = pv;
+            }
+        }
+        tiny_emit(p, key, val, true, 2, out, out_end, err);
+        return;
     }
+    if (na <= TINY_ENT && n[0] + n[1] + n[2] <= 32) {
+        int2 v = make_int2(-1, 0);
+        float a = 0.0f;
+        if (lane < n[0]) {
+            v = __ldg(Q + 2 * (size_t)g[0] + lane);
+            a = x[0];
+        } else if (lane < n[0] + n[1]) {
+            v = __ldg(Q + 2 * (size_t)g[1] + (lane - n[0]));
+            a = x[1];
+        } else if (lane < n[0] + n[1] + n[2]) {
+            v = __ldg(Q + 2 * (size_t)g[2] + (lane - n[0] - n[1]));
+            a = x[2];
+        }
+        if ((unsigned)v.x < W) {
+            key = v.x;
+            val = a * __int_as_float(v.y);
+        }
+        warp_sort_kv(key, val);
+        tiny_emit(p, key, val, true, 4, out, out_end, err);
+        return;
+    }
+    // longer runs of entries (rows of B that are empty among them)
     int base = 0;  // products placed so far (warp-uniform)
     for (long long ec = a0; ec < a1 && base < 32; ec += 32) {
         const long long e = ec + lane;
@@ -176,8 +182,11 @@ __device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restr
 // Every light row with 1 .. TINY_MAX products (split rows carry negative
 // marks in the flops array and are never tiny; with a heavy threshold that
 // low, heavy rows stay with the wide kernel's blocks), 32-row chunks dealt
-// to the warps in turn, the bounds of a chunk's tiny rows loaded at once.
-__global__ void __launch_bounds__(256) k_numeric_tiny(NumParams p) {
+// to the warps in turn.  Lane l loads what row l of the chunk needs before
+// its rows of B (bounds in A and C, up to TINY_ENT entries of A and their
+// rows' descriptions), all rows of the chunk at once, so that a row then
+// waits for one round of loads only.
+__global__ void __launch_bounds__(256, 6) k_numeric_tiny(NumParams p) {
     const int lane = lane_id();
     unsigned long long* err = &p.hdr->err;
     const int2* Q = reinterpret_cast<const int2*>(p.Bq);
@@ -195,11 +204,43 @@ __global__ void __launch_bounds__(256) k_numeric_tiny(NumParams p) {
             o0 = clampll(__ldg(p.Cp + r), 0, p.nnzC);
             o1 = clampll(__ldg(p.Cp + r + 1), o0, p.nnzC);
         }
+        unsigned gl[TINY_ENT];
+        int nl[TINY_ENT];
+        float xl[TINY_ENT];
+        int kl[TINY_ENT];
+#pragma unroll
+        for (int u = 0; u < TINY_ENT; ++u) {
+            kl[u] = -1;
+            xl[u] = 0.0f;
+            if (tiny && a0 + u < a1 && a1 - a0 <= TINY_ENT) {
+                kl[u] = __ldg(p.Ai + a0 + u);
+                xl[u] = p.Ax ? __ldg(p.Ax + a0 + u) : 1.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TINY_ENT; ++u) {
+            gl[u] = 0;
+            nl[u] = 0;
+            if (tiny && a0 + u < a1 && a1 - a0 <= TINY_ENT) {
+                long long s;
+                if ((unsigned)kl[u] < (unsigned)p.nB) padded_row<2>(p.Bp, p.nnzB, p.d, kl[u], s, nl[u], gl[u]);
+                else atomicOr(err, ERR_A_COL);
+            }
+        }
         unsigned rows = __ballot_sync(FULL, tiny);
         while (rows) {
             const int src = __ffs(rows) - 1;
             rows &= rows - 1;
-            tiny_row(p, Q, shfl64(a0, src), shfl64(a1, src), shfl64(o0, src), shfl64(o1, src), err);
+            unsigned g[TINY_ENT];
+            int n[TINY_ENT];
+            float x[TINY_ENT];
+#pragma unroll
+            for (int u = 0; u < TINY_ENT; ++u) {
+                g[u] = __shfl_sync(FULL, gl[u], src);
+                n[u] = __shfl_sync(FULL, nl[u], src);
+                x[u] = __shfl_sync(FULL, xl[u], src);
+            }
+            tiny_row(p, Q, shfl64(a0, src), shfl64(a1, src), shfl64(o0, src), shfl64(o1, src), g, n, x, err);
         }
     }
 }
