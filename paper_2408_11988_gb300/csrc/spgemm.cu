@@ -400,7 +400,13 @@ struct SymParams {
     Sched s;
     long long item_cap;
     int skip_light;  // 1: split and heavy rows only (light rows run in k_symbolic_light)
+    int tiny;        // 1: light rows of classes <= SYM_TINY_CLASS are counted by k_symbolic_tiny
 };
+
+// Rows with at most 31 products (flops classes 1 .. 40, eighths of an
+// octave) are the symbolic pass's tiny rows when k_symbolic_tiny runs.
+constexpr int SYM_TINY_CLASS = 40;
+static_assert(SYM_TINY_CLASS < NUM_CLASSES, "tiny classes");
 
 // Count of the marks in words [w0, dw*8 or dw) of a warp's or block's
 // marks, stride `step`, clearing them.
@@ -484,6 +490,110 @@ __device__ __forceinline__ int block_sum(int c, int* s_red) {
     v = warp_sum(v);
     __syncthreads();
     return v;
+}
+
+// Tiny rows (light, at most 31 products) counted in registers: a row of one
+// entry of A has as many columns as its row of B (flops_i itself); a longer
+// one has its rows of B's columns placed one per lane, sorted (two rows: one
+// bitonic merge of the first row and the second reversed at the top lanes;
+// more: the full network) and the distinct ones counted.  32-row chunks are
+// dealt to the warps in turn; the one-entry rows of a chunk are counted lane
+// by lane.  Called when d is too wide for the row-group light kernel, where
+// each light row costs a pass over d/4 words of byte marks.
+__device__ __forceinline__ void warp_sort_keys(int& key) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int pk = __shfl_xor_sync(FULL, key, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            if (keep_min ? pk < key : pk > key) key = pk;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_symbolic_tiny(SymParams p) {
+    const int lane = lane_id();
+    unsigned long long* err = &p.hdr->err;
+    const long long* flops = p.s.flops;
+    const long long nchunks = ((long long)p.nB + 31) / 32;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = gw; c < nchunks; c += nwarps) {
+        const long long r = c * 32 + lane;
+        const long long f = r < p.nB ? __ldg(flops + r) : 0;
+        const int cls = flops_class(f);
+        const bool tiny = f >= 1 && cls <= SYM_TINY_CLASS && cls < p.cta_class;
+        long long a0 = 0, a1 = 0;
+        if (tiny) {
+            a0 = clampll(__ldg(p.Ap + r), 0, p.nnzA);
+            a1 = clampll(__ldg(p.Ap + r + 1), a0, p.nnzA);
+            if (a1 - a0 == 1) p.Cp_next[r] = f;  // one row of B: its columns, all distinct
+        }
+        unsigned rows = __ballot_sync(FULL, tiny && a1 - a0 > 1);
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const long long b0 = shfl64(a0, src), b1 = shfl64(a1, src);
+            int key = 0x7FFFFFFF;  // no column: sorts last
+            if (b1 - b0 == 2) {
+                long long s0, s1;
+                int n0, n1;
+                const int k0 = __ldg(p.Ai + b0), k1 = __ldg(p.Ai + b0 + 1);
+                n0 = n1 = 0;
+                s0 = s1 = 0;
+                if ((unsigned)k0 < (unsigned)p.nB) p.segB(k0, s0, n0);
+                else if (lane == 0) atomicOr(err, ERR_A_COL);
+                if ((unsigned)k1 < (unsigned)p.nB) p.segB(k1, s1, n1);
+                else if (lane == 0) atomicOr(err, ERR_A_COL);
+                if (n0 + n1 <= 32) {
+                    const int j1 = 31 - lane;  // the second row, reversed, at the top lanes
+                    int col = -1;
+                    if (lane < n0) col = __ldg(p.Bi + s0 + lane);
+                    else if (j1 < n1) col = __ldg(p.Bi + s1 + j1);
+                    if ((unsigned)col < (unsigned)p.d) key = col;
+                    else if (col != -1) atomicOr(err, ERR_B_COL);
+#pragma unroll
+                    for (int j = 16; j > 0; j >>= 1) {
+                        const int pk = __shfl_xor_sync(FULL, key, j);
+                        if (((lane & j) == 0) ? pk < key : pk > key) key = pk;
+                    }
+                    const int prev = __shfl_up_sync(FULL, key, 1);
+                    const unsigned heads = __ballot_sync(FULL, key != 0x7FFFFFFF && (lane == 0 || prev != key));
+                    if (lane == 0) p.Cp_next[c * 32 + src] = __popc(heads);
+                    continue;
+                }
+            }
+            int base = 0;  // columns placed so far (warp-uniform)
+            for (long long ec = b0; ec < b1 && base < 32; ec += 32) {
+                const long long e = ec + lane;
+                int len = 0;
+                long long st = 0;
+                if (e < b1) {
+                    const int k = __ldg(p.Ai + e);
+                    if ((unsigned)k < (unsigned)p.nB) p.segB(k, st, len);
+                    else atomicOr(err, ERR_A_COL);
+                }
+                const int incl = warp_incl_scan(len), excl = incl - len;
+                const int tot = __shfl_sync(FULL, incl, 31);
+                const int pj = lane - base;
+                const int q = owner_lane(excl, pj < 0 ? 0 : pj);
+                const long long sq = shfl64(st, q);
+                const int eq = __shfl_sync(FULL, excl, q);
+                if (pj >= 0 && pj < tot) {
+                    const int col = __ldg(p.Bi + sq + (pj - eq));
+                    if ((unsigned)col < (unsigned)p.d) key = col;
+                    else atomicOr(err, ERR_B_COL);
+                }
+                base += tot;
+            }
+            warp_sort_keys(key);
+            const int prev = __shfl_up_sync(FULL, key, 1);
+            const unsigned heads = __ballot_sync(FULL, key != 0x7FFFFFFF && (lane == 0 || prev != key));
+            if (lane == 0) p.Cp_next[c * 32 + src] = __popc(heads);
+        }
+    }
 }
 
 template <int G, bool FL>
@@ -574,11 +684,19 @@ __global__ void __launch_bounds__(256, 8) k_symbolic(SymParams p) {
     }
 
     // light rows: one warp per row, static round robin over the class order
+    // (highest first: the tiny rows, when k_symbolic_tiny counts them, are
+    // the last ones)
     if (p.skip_light) return;
+    long long nlight_end = nrows;
+    if (p.tiny) {
+        long long t = 0;
+        for (int c = 1 + lane; c <= SYM_TINY_CLASS && c < p.cta_class; c += 32) t += p.hdr->hist[c];
+        nlight_end -= warp_sum(t);
+    }
     unsigned* bm = smem_u + warp * p.slot;
     SymRowBody<G, FL> body{p, bm, err};
-    pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
-                   p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body, mark);
+    pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nlight_end, (long long)gridDim.x * nw,
+                   p.Ap, p.nnzA, p.Ai, (const float*)nullptr, p.nB, p.segB, err, body, mark);
 }
 
 
@@ -761,6 +879,7 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     p.s = s;
     p.item_cap = item_cap;
     p.skip_light = 0;
+    p.tiny = 0;
     const int threads = 32 * cfg.warps_per_cta;
     const size_t smem = sizeof(unsigned) * (size_t)p.slot * cfg.warps_per_cta;
     const void* k;
@@ -785,6 +904,15 @@ cudaError_t launch_symbolic(const DevCsr& A, const DevCsr& B, long long d, const
     const size_t lsmem = sizeof(unsigned) * (size_t)8 * p.dw * (32 / SRG) * cfg.warps_per_cta;
     const bool rg_ok = rg && lsmem <= 200 * 1024;
     if (rg_ok) p.skip_light = 1;
+    // without the row-group kernel, tiny light rows are counted in registers
+    // (one warp per light row forced: the classic walk for every row)
+    if (!rg_ok && cfg.row_lanes != 32 && d > 256) {
+        p.tiny = 1;
+        const int tgrid = persistent_grid((const void*)k_symbolic_tiny, 256, 0, cfg.sms);
+        count_launch();
+        k_symbolic_tiny<<<tgrid, 256, 0, st>>>(p);
+        if ((e = cudaGetLastError())) return e;
+    }
     const int grid = persistent_grid(k, threads, smem, cfg.sms);
     void* args[] = {&p};
     count_launch();
