@@ -37,7 +37,12 @@ struct BwdParams {
     Sched s;
     long long item_cap;
     int skip_light;  // 1: split and heavy rows only (light rows run in k_backward_light)
+    int tiny;        // 1: light rows of classes <= BWD_TINY_CLASS run in k_backward_tiny
 };
+
+// Rows with at most 31 products (flops classes 1 .. 40) are the backward's
+// tiny rows when k_backward_tiny runs.
+constexpr int BWD_TINY_CLASS = 40;
 
 // Sum of v over the run of equal keys that starts at this lane (keys are
 // non-decreasing across lanes); only a run's first lane's result is used.
@@ -527,10 +532,120 @@ __global__ void __launch_bounds__(256, HEAVY ? 6 : 5) k_backward(BwdParams p) {
         backward_range_cta<G, BA>(p, ba, row, a0, a1, fsm, sdA);
     }
     if constexpr (!HEAVY) {
+        // light rows in the class order (highest first: the tiny rows, when
+        // k_backward_tiny takes them, are the last ones)
+        long long nlight_end = nrows;
+        if (p.tiny) {
+            long long t = 0;
+            for (int c = 1 + lane_id(); c <= BWD_TINY_CLASS && c < p.cta_class; c += 32) t += p.hdr->hist[c];
+            nlight_end -= warp_sum(t);
+        }
         float* g = fsm + (size_t)warp * p.dpad;
         BwdRowBody<G, BA> body{p, ba, g, sdA, &p.hdr->err, -1, 0, 0, 0, 0};
-        pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nrows, (long long)gridDim.x * nw, p.Ap,
-                       p.nnzA, p.Ai, p.Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, &p.hdr->err, body, mark);
+        pipelined_rows(p.perm, nheavy + (long long)blockIdx.x * nw + warp, nlight_end, (long long)gridDim.x * nw,
+                       p.Ap, p.nnzA, p.Ai, p.Ax, p.nB, SegWhole{p.Bp, p.nnzB, p.d}, &p.hdr->err, body, mark);
+    }
+}
+
+// Tiny light rows (at most 31 products) in registers: lane j holds entry j
+// of row i of C (column and dC value; the row has at most as many entries as
+// products), and the row's products are placed one per lane (lane j: the
+// product of number j over the row's entries of A, like an expansion of
+// Eq. 1).  A product (k, col) finds dC(i, col) by a binary search of the
+// sorted row of C over the lanes; it adds A(i,k) * dC(i, col) to dB with a
+// float atomic and B(k, col) * dC(i, col) to dA(i,k), the products of one
+// entry (neighbouring lanes) summed into their first lane.  32-row chunks
+// are dealt to the warps in turn.  Used where the light rows would each
+// take a warp pass over a dense row of d floats (d above the row-group
+// range).
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_backward_tiny(BwdParams p) {
+    const int lane = lane_id();
+    unsigned long long* err = &p.hdr->err;
+    const long long nchunks = ((long long)p.nB + 31) / 32;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const SegWhole seg{p.Bp, p.nnzB, p.d};
+    for (long long c = gw; c < nchunks; c += nwarps) {
+        const long long r = c * 32 + lane;
+        const long long f = r < p.nB ? __ldg(p.s.flops + r) : 0;
+        const int cls = flops_class(f);
+        const bool tiny = f >= 1 && cls <= BWD_TINY_CLASS && cls < p.cta_class;
+        long long a0 = 0, a1 = 0, o0 = 0, o1 = 0;
+        if (tiny) {
+            a0 = clampll(__ldg(p.Ap + r), 0, p.nnzA);
+            a1 = clampll(__ldg(p.Ap + r + 1), a0, p.nnzA);
+            o0 = clampll(__ldg(p.Cp + r), 0, p.nnzC);
+            o1 = clampll(__ldg(p.Cp + r + 1), o0, p.nnzC);
+        }
+        unsigned rows = __ballot_sync(FULL, tiny);
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const long long b0 = shfl64(a0, src), b1 = shfl64(a1, src);
+            const long long q0 = shfl64(o0, src), q1 = shfl64(o1, src);
+            // the row of C, one entry per lane (sorted columns; none: INT_MAX)
+            int cc = 0x7FFFFFFF;
+            float dv = 0.0f;
+            if (lane < q1 - q0) {
+                cc = __ldg(p.Ci + q0 + lane);
+                dv = __ldg(p.dC + q0 + lane);
+            }
+            if (q1 - q0 > 32 && lane == 0) atomicOr(err, ERR_C_ROW);
+            int base = 0;  // products placed so far (warp-uniform)
+            for (long long ec = b0; ec < b1 && base < 32; ec += 32) {
+                const long long e = ec + lane;
+                int len = 0;
+                long long st = 0;
+                float a = 0.0f;
+                if (e < b1) {
+                    const int k = __ldg(p.Ai + e);
+                    a = __ldg(p.Ax + e);
+                    if ((unsigned)k < (unsigned)p.nB) seg(k, st, len);
+                    else atomicOr(err, ERR_A_COL);
+                }
+                const int incl = warp_incl_scan(len), excl = incl - len;
+                const int tot = __shfl_sync(FULL, incl, 31);
+                const int pj = lane - base;
+                const int q = owner_lane(excl, pj < 0 ? 0 : pj);  // entry ec + q of A
+                const long long sq = shfl64(st, q);
+                const int eq = __shfl_sync(FULL, excl, q);
+                const float aq = __shfl_sync(FULL, a, q);
+                const bool ent = pj >= 0 && pj < tot;
+                int col = 0x7FFFFFFF;
+                float b = 0.0f;
+                const long long j = sq + (pj - eq);  // the product's entry of B
+                if (ent) {
+                    if constexpr (PACKED) {
+                        const int2 v = __ldg(p.Bpk + j);
+                        col = v.x;
+                        b = __int_as_float(v.y);
+                    } else {
+                        col = __ldg(p.Bi + j);
+                        b = __ldg(p.Bx + j);
+                    }
+                }
+                // dC(i, col): the last lane of the row of C whose column is <= col
+                const int at = owner_lane(cc, col);
+                const float g = __shfl_sync(FULL, dv, at);
+                const bool found = __shfl_sync(FULL, cc, at) == col;
+                float part = 0.0f;
+                if (ent) {
+                    if (found && (unsigned)col < (unsigned)p.d) {
+                        if (p.dB) atomicAdd(p.dB + j, aq * g);
+                        part = b * g;
+                    } else {
+                        atomicOr(err, (unsigned)col < (unsigned)p.d ? ERR_C_ROW : ERR_B_COL);
+                    }
+                }
+                // dA of entry ec + q: its products are neighbouring lanes
+                const int key = ent ? q : -1 - lane;
+                part = seg_sum_down(part, key);
+                const int prevq = __shfl_up_sync(FULL, key, 1);
+                if (ent && p.dA && (lane == 0 || prevq != key)) p.dA[ec + q] = part;
+                base += tot;
+            }
+        }
     }
 }
 
@@ -578,6 +693,7 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     p.s = s;
     p.item_cap = split_item_capacity(A.nnz);
     p.skip_light = 0;
+    p.tiny = 0;
     int warps = cfg.warps_per_cta;
     if (warps > 8) return cudaErrorInvalidValue;
     size_t smem = backward_smem(d, warps);
@@ -592,6 +708,16 @@ cudaError_t launch_backward(const DevCsr& A, const DevCsr& B, long long d, const
     const bool rg = cfg.row_lanes != 32 && pk && !(dB && (reinterpret_cast<uintptr_t>(dB) & 15)) && p.dpad <= 512 &&
                     lsmem <= 200 * 1024;
     if (rg) p.skip_light = 1;
+    // without the row-group kernel, tiny light rows run in registers (one
+    // warp per light row forced: the classic walk for every row)
+    if (!rg && cfg.row_lanes != 32 && d > 256) {
+        p.tiny = 1;
+        const void* kt = pk ? (const void*)k_backward_tiny<true> : (const void*)k_backward_tiny<false>;
+        void* targs[] = {&p};
+        count_launch();
+        if ((e = cudaLaunchKernel(kt, dim3(persistent_grid(kt, 256, 0, cfg.sms)), dim3(256), targs, 0, st)))
+            return e;
+    }
     const void* k;
     switch (cfg.group) {
         case 2:  // quads: packed B and a 16-byte aligned dB only
