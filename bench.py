@@ -76,7 +76,8 @@ REL = 1e-5
 def _kernel_sources_hash():
     import hashlib
     h = hashlib.sha1()
-    for f in ("numeric.cu", "numeric.cuh", "common.cuh", "staged.cuh", "layout.h", "wide.cuh", "rowgroup.cuh"):
+    for f in ("numeric.cu", "numeric.cuh", "numeric_tiny.cu", "common.cuh", "staged.cuh", "layout.h", "wide.cuh",
+              "rowgroup.cuh"):
         with open(os.path.join(ROOT, "paper_2408_11988_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
