@@ -251,3 +251,43 @@ def test_backward_deterministic_db(case):
     Cs = plan_s.forward(Ad, Bd)
     _, dBs = plan_s.backward(Ad, Bd, Cs, dC)
     assert np.all(np.abs(dBs.cpu().numpy() - rB) <= REL * bB)
+
+
+def _tiny_rows_case(n=4000, d=700, seed=77):
+    # rows of A with 1-3 entries (and some longer ones) whose rows of B draw
+    # their columns from a few narrow windows, so that the products of a row
+    # share columns often: the duplicate handling of the tiny-row kernels
+    # (merge, sort, runs of equal columns) in every pass
+    rng = np.random.default_rng(seed)
+    windows = np.array([0, 6, 350, d - 16])
+    brow = []
+    for k in range(n):
+        w = windows[rng.integers(0, len(windows))]
+        cols = np.sort(rng.choice(16, size=int(rng.integers(1, 12)), replace=False)) + w
+        brow.append(cols)
+    Bp = np.zeros(n + 1, np.int64)
+    Bp[1:] = np.cumsum([len(c) for c in brow])
+    Bc = np.concatenate(brow).astype(np.int32)
+    Bv = rng.uniform(-1.0, 1.0, size=Bc.size).astype(np.float32)
+    arow = []
+    for i in range(n):
+        r = rng.random()
+        na = 0 if r < 0.1 else (1 if r < 0.45 else (2 if r < 0.7 else (3 if r < 0.9 else int(rng.integers(4, 40)))))
+        arow.append(np.sort(rng.choice(n, size=na, replace=False)))
+    Ap = np.zeros(n + 1, np.int64)
+    Ap[1:] = np.cumsum([len(c) for c in arow])
+    Ac = np.concatenate(arow).astype(np.int32)
+    Av = rng.uniform(0.0, 1.0, size=Ac.size).astype(np.float32)
+    return synth.CSR(n, n, Ap, Ac, Av), synth.CSR(n, d, Bp, Bc, Bv)
+
+
+@pytest.mark.parametrize("d", [700, 1024])
+def test_tiny_rows_with_shared_columns(d):
+    from _cmp import compare_full
+    from paper_2408_11988_gb300 import spgemm
+    A, B = _tiny_rows_case(d=d)
+    compare_full(spgemm(dev(A), dev(B)), A, B)
+    rp, col, dC, dA, dB = _run(A, B)
+    rA, bA, rB, bB = oracle.backward(A, B, rp, col, dC.astype(np.float64))
+    assert np.all(np.abs(dA - rA) <= REL * bA), np.max(np.abs(dA - rA) / np.maximum(bA, 1e-30))
+    assert np.all(np.abs(dB - rB) <= REL * bB), np.max(np.abs(dB - rB) / np.maximum(bB, 1e-30))
