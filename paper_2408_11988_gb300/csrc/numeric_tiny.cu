@@ -1,8 +1,9 @@
 // Tiny rows of the wide numeric pass (plus-times, one column tile of
-// 256 < W <= 1024): rows with 1 .. TINY_MAX products.  In R-MAT products most
-// non-empty rows are of this kind (about two thirds at d = 1024, 1 %), and
-// on the wide kernel's path each costs a whole pass of a warp over a
-// 1024-column accumulator and a bitmap read-out for a few dozen products.
+// 256 < W <= 1024): rows with 1 .. TINY_MAX products.  In R-MAT products
+// about half of the non-empty rows are of this kind (at d = 1024, 1 %; under
+// 5 % of the products), and on the wide kernel's path each costs a whole
+// pass of a warp over a 1024-column accumulator and a bitmap read-out for a
+// few dozen products.
 // Here a row is expanded, sorted and compressed in registers (Eq. 1 written
 // as a sum over the row's products grouped by column): lane j takes the
 // row's j-th product, the warp sorts the (column, value) pairs by column
