@@ -556,6 +556,11 @@ __global__ void __launch_bounds__(256, 5) k_numeric_light(NumParams p) {
     if (tid < 32) {  // one warp; its lanes store the same values
         long long nh, nr;
         sched_counts(p.hdr, p.cta_class, nh, nr);
+        if (p.tiny_max) {  // the tiny rows, last in the class order, run in k_numeric_tiny
+            long long t = 0;
+            for (int c = 1 + lane_id(); c <= TINY_CLASS && c < p.cta_class; c += 32) t += p.hdr->hist[c];
+            nr -= warp_sum(t);
+        }
         s_nheavy = nh;
         s_nrows = nr;
     }
@@ -1181,6 +1186,10 @@ cudaError_t launch_numeric_dense(const DevCsr& A, const DevCsr& B, long long d, 
                 case 16: return launch_light<16>(p, w, cfg.sms, st);
                 default: return cudaErrorInvalidValue;
             }
+        }
+        if (Bq && cfg.row_lanes != 4) {  // one tile, the copy in pairs (E = 2): tiny rows first, in registers
+            if ((e = launch_numeric_tiny(p, cfg.sms, st))) return e;
+            p.tiny_max = TINY_MAX;
         }
         switch (cfg.row_lanes) {
             case 4:

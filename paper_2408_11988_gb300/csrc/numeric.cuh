@@ -39,9 +39,11 @@ struct NumParams {
     int tiny_max;    // wide kernel: light rows with at most this many products run in k_numeric_tiny
 };
 
-// Rows with at most this many products go to the tiny-row kernel on the
-// wide path (one product per lane).
-constexpr int TINY_MAX = 32;
+// Light rows with at most TINY_MAX products go to the tiny-row kernel (one
+// product per lane): exactly the flops classes 1 .. TINY_CLASS, the tail of
+// the class order, which the row-group light kernel then stops short of.
+constexpr int TINY_MAX = 31;
+constexpr int TINY_CLASS = 40;  // flops class of 31 products; 32 start class 41
 
 inline NumParams numeric_params(const DevCsr& A, const DevCsr& B, long long d, int W, int T,
                                 const long long* tp, const int2* Bpk, const Sched& s, const LaunchCfg& cfg,

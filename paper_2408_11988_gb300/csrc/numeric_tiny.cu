@@ -66,40 +66,34 @@ __device__ __forceinline__ void tiny_emit(const NumParams& p, int key, float val
     if (lane == 0 && out + __popc(hb) != out_end) atomicOr(err, ERR_C_ROW);
 }
 
-// Row [a0, a1) of A with at most 32 products.  Rows of up to TINY_ENT
-// entries arrive with their rows of B described (first pair g[u], entries
-// n[u], value x[u], loaded for the whole chunk at once), so only the rows of
-// B themselves remain to be read.  One entry: its row of B, scaled, is the
-// row of C (already sorted, no duplicates).  Two entries: the two sorted
-// rows of B side by side, the second reversed at the top lanes, form a
-// bitonic sequence that five merge steps sort.  More: the products placed
-// one per lane and sorted by the full network.
+// Rows of up to TINY_ENT entries arrive with their rows of B described
+// (first pair g[u], entries n[u], value x[u], loaded for the whole chunk at
+// once), so only the rows of B themselves remain to be read: tiny_fetch
+// issues this lane's load for one row, and the kernel issues the next row's
+// before it processes the current one.
 constexpr int TINY_ENT = 3;
 
-__device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restrict__ Q, long long a0, long long a1,
-                                         long long out, long long out_end, const unsigned (&g)[TINY_ENT],
-                                         const int (&n)[TINY_ENT], const float (&x)[TINY_ENT],
-                                         unsigned long long* err) {
+// A tiny row as the pipeline carries it.
+struct TinyRow {
+    long long a0, a1, out, out_end;
+};
+
+// This lane's product of a row of at most TINY_ENT entries (v.x = -1: none).
+// One entry: lane j takes entry j of the row of B.  Two: the first row of B
+// from lane 0 up, the second reversed from lane 31 down (a bitonic sequence
+// once sorted keys sit in the lanes).  Three: the rows one after another.
+__device__ __forceinline__ void tiny_fetch(const int2* __restrict__ Q, int na, const unsigned (&g)[TINY_ENT],
+                                           const int (&n)[TINY_ENT], const float (&x)[TINY_ENT], int2& v, float& a) {
     const int lane = lane_id();
-    const unsigned W = (unsigned)p.W;
-    int key = 0x7FFFFFFF;  // no product: sorts last
-    float val = 0.0f;
-    const long long na = a1 - a0;
+    v = make_int2(-1, 0);
+    a = 0.0f;
     if (na == 1) {
         if (lane < n[0]) {
-            const int2 v = __ldg(Q + 2 * (size_t)g[0] + lane);
-            if ((unsigned)v.x < W) {  // a bad column (-1) adds nothing
-                key = v.x;
-                val = x[0] * __int_as_float(v.y);
-            }
+            v = __ldg(Q + 2 * (size_t)g[0] + lane);
+            a = x[0];
         }
-        tiny_emit(p, key, val, false, 1, out, out_end, err);
-        return;
-    }
-    if (na == 2 && n[0] + n[1] <= 32) {
-        const int j1 = 31 - lane;  // the second row, reversed, at the top lanes
-        int2 v = make_int2(-1, 0);
-        float a = 0.0f;
+    } else if (na == 2) {
+        const int j1 = 31 - lane;
         if (lane < n[0]) {
             v = __ldg(Q + 2 * (size_t)g[0] + lane);
             a = x[0];
@@ -107,26 +101,7 @@ __device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restr
             v = __ldg(Q + 2 * (size_t)g[1] + j1);
             a = x[1];
         }
-        if ((unsigned)v.x < W) {
-            key = v.x;
-            val = a * __int_as_float(v.y);
-        }
-        // bitonic merge: ascending (first row), empty lanes, descending (second row)
-#pragma unroll
-        for (int j = 16; j > 0; j >>= 1) {
-            const int pk = __shfl_xor_sync(FULL, key, j);
-            const float pv = __shfl_xor_sync(FULL, val, j);
-            if (((lane & j) == 0) ? pk < key : pk > key) {
-                key = pk;
-                val = pv;
-            }
-        }
-        tiny_emit(p, key, val, true, 2, out, out_end, err);
-        return;
-    }
-    if (na <= TINY_ENT && n[0] + n[1] + n[2] <= 32) {
-        int2 v = make_int2(-1, 0);
-        float a = 0.0f;
+    } else if (na == 3) {
         if (lane < n[0]) {
             v = __ldg(Q + 2 * (size_t)g[0] + lane);
             a = x[0];
@@ -137,25 +112,54 @@ __device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restr
             v = __ldg(Q + 2 * (size_t)g[2] + (lane - n[0] - n[1]));
             a = x[2];
         }
-        if ((unsigned)v.x < W) {
+    }
+}
+
+// Row r with its fetched product (v, a): one entry — the scaled row of B is
+// the row of C (sorted, no duplicates); two — five bitonic merge steps;
+// three — the full sorting network; more entries (rows of B that are empty
+// among them) — the products expanded here, round by round, then sorted.
+__device__ __forceinline__ void tiny_process(const NumParams& p, const int2* __restrict__ Q, const TinyRow& r,
+                                             int2 v, float a, unsigned long long* err) {
+    const int lane = lane_id();
+    const unsigned W = (unsigned)p.W;
+    const long long na = r.a1 - r.a0;
+    int key = 0x7FFFFFFF;  // no product: sorts last
+    float val = 0.0f;
+    if (na <= TINY_ENT) {
+        if ((unsigned)v.x < W) {  // pads and bad columns (-1) add nothing
             key = v.x;
             val = a * __int_as_float(v.y);
         }
-        warp_sort_kv(key, val);
-        tiny_emit(p, key, val, true, 4, out, out_end, err);
+        if (na == 1) {
+            tiny_emit(p, key, val, false, 1, r.out, r.out_end, err);
+        } else if (na == 2) {
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+                const int pk = __shfl_xor_sync(FULL, key, j);
+                const float pv = __shfl_xor_sync(FULL, val, j);
+                if (((lane & j) == 0) ? pk < key : pk > key) {
+                    key = pk;
+                    val = pv;
+                }
+            }
+            tiny_emit(p, key, val, true, 2, r.out, r.out_end, err);
+        } else {
+            warp_sort_kv(key, val);
+            tiny_emit(p, key, val, true, 4, r.out, r.out_end, err);
+        }
         return;
     }
-    // longer runs of entries (rows of B that are empty among them)
     int base = 0;  // products placed so far (warp-uniform)
-    for (long long ec = a0; ec < a1 && base < 32; ec += 32) {
+    for (long long ec = r.a0; ec < r.a1 && base < 32; ec += 32) {
         const long long e = ec + lane;
         int len = 0;
         long long s = 0;
         unsigned g0 = 0;
-        float a = 0.0f;
-        if (e < a1) {
+        float x = 0.0f;
+        if (e < r.a1) {
             const int k = __ldg(p.Ai + e);
-            a = p.Ax ? __ldg(p.Ax + e) : 1.0f;
+            x = p.Ax ? __ldg(p.Ax + e) : 1.0f;
             if ((unsigned)k < (unsigned)p.nB) padded_row<2>(p.Bp, p.nnzB, p.d, k, s, len, g0);
             else atomicOr(err, ERR_A_COL);
         }
@@ -166,28 +170,29 @@ __device__ __forceinline__ void tiny_row(const NumParams& p, const int2* __restr
         const int q = owner_lane(excl, pj < 0 ? 0 : pj);
         const unsigned gq = __shfl_sync(FULL, g0, q);
         const int eq = __shfl_sync(FULL, excl, q);
-        const float aq = __shfl_sync(FULL, a, q);
+        const float aq = __shfl_sync(FULL, x, q);
         if (pj >= 0 && pj < tot) {
-            const int2 v = __ldg(Q + 2 * (size_t)gq + (pj - eq));
-            if ((unsigned)v.x < W) {
-                key = v.x;
-                val = aq * __int_as_float(v.y);
+            const int2 w = __ldg(Q + 2 * (size_t)gq + (pj - eq));
+            if ((unsigned)w.x < W) {
+                key = w.x;
+                val = aq * __int_as_float(w.y);
             }
         }
         base += tot;
     }
     warp_sort_kv(key, val);
-    tiny_emit(p, key, val, true, 32, out, out_end, err);
+    tiny_emit(p, key, val, true, 32, r.out, r.out_end, err);
 }
 
 // Every light row with 1 .. TINY_MAX products (split rows carry negative
 // marks in the flops array and are never tiny; with a heavy threshold that
-// low, heavy rows stay with the wide kernel's blocks), 32-row chunks dealt
+// low, heavy rows stay with the other kernels' blocks), 32-row chunks dealt
 // to the warps in turn.  Lane l loads what row l of the chunk needs before
 // its rows of B (bounds in A and C, up to TINY_ENT entries of A and their
-// rows' descriptions), all rows of the chunk at once, so that a row then
-// waits for one round of loads only.
-__global__ void __launch_bounds__(256, 6) k_numeric_tiny(NumParams p) {
+// rows' descriptions), all rows of the chunk at once; then the chunk's tiny
+// rows go through a two-stage pipeline: the next row's gathers are issued
+// before the current row is sorted and written.
+__global__ void __launch_bounds__(256, 4) k_numeric_tiny(NumParams p) {
     const int lane = lane_id();
     unsigned long long* err = &p.hdr->err;
     const int2* Q = reinterpret_cast<const int2*>(p.Bq);
@@ -228,10 +233,12 @@ __global__ void __launch_bounds__(256, 6) k_numeric_tiny(NumParams p) {
                 else atomicOr(err, ERR_A_COL);
             }
         }
-        unsigned rows = __ballot_sync(FULL, tiny);
-        while (rows) {
-            const int src = __ffs(rows) - 1;
-            rows &= rows - 1;
+        // row of chunk lane src, and this lane's product of it
+        auto take = [&](int src, TinyRow& t, int2& v, float& a) {
+            t.a0 = shfl64(a0, src);
+            t.a1 = shfl64(a1, src);
+            t.out = shfl64(o0, src);
+            t.out_end = shfl64(o1, src);
             unsigned g[TINY_ENT];
             int n[TINY_ENT];
             float x[TINY_ENT];
@@ -241,11 +248,36 @@ __global__ void __launch_bounds__(256, 6) k_numeric_tiny(NumParams p) {
                 n[u] = __shfl_sync(FULL, nl[u], src);
                 x[u] = __shfl_sync(FULL, xl[u], src);
             }
-            tiny_row(p, Q, shfl64(a0, src), shfl64(a1, src), shfl64(o0, src), shfl64(o1, src), g, n, x, err);
+            tiny_fetch(Q, (int)(t.a1 - t.a0), g, n, x, v, a);
+        };
+        unsigned rows = __ballot_sync(FULL, tiny);
+        if (!rows) continue;
+        TinyRow cur;
+        int2 v;
+        float a;
+        take(__ffs(rows) - 1, cur, v, a);
+        rows &= rows - 1;
+        for (;;) {
+            const bool more = rows != 0;  // warp-uniform
+            TinyRow nxt{0, 0, 0, 0};
+            int2 nv = make_int2(-1, 0);
+            float nx = 0.0f;
+            if (more) {
+                take(__ffs(rows) - 1, nxt, nv, nx);
+                rows &= rows - 1;
+            }
+            tiny_process(p, Q, cur, v, a, err);
+            if (!more) break;
+            cur = nxt;
+            v = nv;
+            a = nx;
         }
     }
 }
 
+// p.Bq must be the row-aligned copy in pairs (E = 2: rows start at even
+// entries), as the wide kernel and the row-group kernels of eight or more
+// lanes use it.
 cudaError_t launch_numeric_tiny(const NumParams& p, int sms, cudaStream_t st) {
     if (p.nB == 0 || !p.Bq) return cudaSuccess;
     const int grid = persistent_grid((const void*)k_numeric_tiny, 256, 0, sms);
