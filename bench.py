@@ -226,6 +226,25 @@ def products_per_row(A, B):
     return cs[A.rowptr[1:]] - cs[A.rowptr[:-1]]
 
 
+def cpu_plain_record(A, B, F, reps=2):
+    """The forward on all host cores (cpu_plain: the paper's local kernel,
+    Sec. III-C, OpenMP with a dense SPA per thread, FP32), full size, best of
+    `reps` after one warm-up: a plain multi-core baseline beside the FP64
+    single-thread oracle."""
+    import cpu_plain
+    threads = cpu_plain.max_threads()
+    cpu_plain.spgemm(A, B, threads)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        cpu_plain.spgemm(A, B, threads)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": round(2.0 * F / best / 1e9, 3), "unit": "GFLOP/s", "ms": round(best * 1e3, 2),
+            "threads": threads, "host": host_info(),
+            "what": "forward (row counts + values) of the whole product, FP32, rows of A over all host cores "
+                    "(OpenMP) with a dense accumulator per thread; a plain baseline, not the oracle"}
+
+
 def cpu_baseline(A, B, want_bwd, target_s=12.0, gpu=None):
     """The FP64 oracle on the first m rows of A (rows are randomly labelled by
     the R-MAT permutation, so a prefix is a uniform sample), sized to about
@@ -361,6 +380,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
         Cl = last["C"]
         cpu = cpu_baseline(A, B, want_bwd, target_s=8.0 if nested else 12.0,
                            gpu=(Cl.rowptr, Cl.col, Cl.val, last["dA"], dC_host))
+    plain = cpu_plain_record(A, B, F) if (rank == 0 and want_cpu and not args.no_cpu_baseline and not nested) else None
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     l0 = N.lib().ts_kernel_launches()
     if dist:
@@ -438,6 +458,7 @@ def measure_product(args, name, ws, rank, local, dist, tuning_json=None, steps=N
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "verified": cpu.pop("verified") if cpu else None,
+        "cpu_plain": plain,
     }
     if not want_bwd:
         rec["graph_forward"] = graph_forward(plan, Ad, Bd, C, F, steps, warmup, dist)
